@@ -1,0 +1,132 @@
+"""ORACLE — test infrastructure only.
+
+A plain, slow, single-threaded CPU Brandes BC in FP64 (``brandes.c``), written
+from the paper's ComputeBC program (Section 2, Fig. 1).  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package; the library under ``paper_2401_02472_gb300`` never does and
+shares no code with it.
+
+Functions
+---------
+bfs(g, src)          -> int32 dist[n] (-1 unreachable), FIFO BFS.
+sigma(g, src, mode)  -> (mant, exp2, dist, stats): path counts mant * 2**exp2.
+bc(g, sources, mode) -> (bc[n], per-source stats).
+
+Modes: PLAIN (doubles; overflow reported as inf), XFLOAT (sigma with a 64-bit
+exponent), AUTO (PLAIN per source, rerun in XFLOAT when sigma overflows).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+PLAIN, XFLOAT, AUTO = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "brandes.c")
+_SO = os.path.join(_HERE, "_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# -ffp-contract=off: no fused multiply-add, the arithmetic runs exactly as written.
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+class SrcStats(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int64),
+        ("reached", ctypes.c_int64),
+        ("arcs", ctypes.c_int64),
+        ("used_xfloat", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("max_level_spread_log2", ctypes.c_double),
+    ]
+
+
+STATS_DTYPE = np.dtype(
+    [("levels", np.int64), ("reached", np.int64), ("arcs", np.int64), ("used_xfloat", np.int32),
+     ("pad", np.int32), ("max_level_spread_log2", np.float64)]
+)
+
+
+def build(force: bool = False, src: str = _SRC, out: str = _SO) -> str:
+    """Compile the oracle into a shared library (also used on tampered copies in tests)."""
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *CFLAGS, src, "-o", tmp, "-lm"], check=True, capture_output=True)
+    os.replace(tmp, out)
+    return out
+
+
+def load(path: str | None = None):
+    """ctypes handle of the oracle library (the default build unless `path` names another)."""
+    global _lib
+    if path is None:
+        with _lock:
+            if _lib is None:
+                _lib = _declare(ctypes.CDLL(build()))
+        return _lib
+    return _declare(ctypes.CDLL(path))
+
+
+def _declare(lib):
+    i32, p = ctypes.c_int32, ctypes.c_void_p
+    lib.oracle_bfs.argtypes = [i32, p, p, i32, p]
+    lib.oracle_bfs.restype = ctypes.c_int
+    lib.oracle_bc.argtypes = [i32, p, p, p, i32, ctypes.c_int, p, p]
+    lib.oracle_bc.restype = ctypes.c_int
+    lib.oracle_sigma.argtypes = [i32, p, p, i32, ctypes.c_int, p, p, p, p]
+    lib.oracle_sigma.restype = ctypes.c_int
+    return lib
+
+
+def _csr(g):
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(g.col_idx, dtype=np.int32)
+    if ci.size == 0:
+        ci = np.zeros(1, np.int32)
+    return rp, ci
+
+
+def bfs(g, src: int, lib=None) -> np.ndarray:
+    lib = lib or load()
+    rp, ci = _csr(g)
+    dist = np.empty(max(g.n, 1), np.int32)
+    rc = lib.oracle_bfs(g.n, rp.ctypes.data, ci.ctypes.data, int(src), dist.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_bfs rc={rc}")
+    return dist[: g.n]
+
+
+def sigma(g, src: int, mode: int = AUTO, lib=None):
+    lib = lib or load()
+    rp, ci = _csr(g)
+    mant = np.empty(g.n, np.float64)
+    exp2 = np.empty(g.n, np.int64)
+    dist = np.empty(g.n, np.int32)
+    st = np.zeros(1, STATS_DTYPE)
+    rc = lib.oracle_sigma(g.n, rp.ctypes.data, ci.ctypes.data, int(src), mode, mant.ctypes.data,
+                          exp2.ctypes.data, dist.ctypes.data, st.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_sigma rc={rc}")
+    return mant, exp2, dist, st[0]
+
+
+def bc(g, sources, mode: int = AUTO, lib=None):
+    lib = lib or load()
+    rp, ci = _csr(g)
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1))
+    out = np.empty(max(g.n, 1), np.float64)
+    st = np.zeros(max(src.size, 1), STATS_DTYPE)
+    nsrc = int(src.size)
+    buf = src if nsrc else np.zeros(1, np.int32)
+    rc = lib.oracle_bc(g.n, rp.ctypes.data, ci.ctypes.data, buf.ctypes.data, nsrc, mode, out.ctypes.data,
+                       st.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_bc rc={rc}")
+    return out[: g.n], st[:nsrc]
