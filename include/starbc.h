@@ -1,0 +1,201 @@
+/*
+ * starbc — Brandes betweenness centrality (BC) on one GB300 GPU (sm_103a).
+ *
+ * The operation (paper Section 2, Fig. 1, the ComputeBC program, which follows
+ * Brandes' algorithm): for a multiset S of source vertices of an unweighted
+ * undirected graph G,
+ *
+ *     BC(v) = sum_{s in S, s != v} delta_s(v),
+ *     delta_s(v) = sum over BFS children w of v (dist_s(w) = dist_s(v) + 1) of
+ *                  (sigma_s(v) / sigma_s(w)) * (1 + delta_s(w)),
+ *
+ * where sigma_s(v) counts shortest s-v paths, built in a forward BFS by adding
+ * sigma over BFS parents (Fig. 1, the iterateInBFS loop) and delta in a
+ * reverse-level sweep (Fig. 1, the iterateInReverse loop).  Ordered (s, t)
+ * pairs are counted: no halving.  Duplicated sources count once per
+ * occurrence.  Vertices not reached from s receive nothing from s.
+ *
+ * Graph input: int32 CSR, row_ptr[n+1] and col_idx[nnz], both directions of
+ * every undirected edge stored (the paper's CSR offset array and edge list,
+ * Section 3.1).  Rows need not be sorted; a repeated arc counts as a parallel
+ * edge and a self-loop is never on a shortest path.
+ *
+ * Pointers: every array argument may be host memory or device memory of the
+ * current device; the library tells them apart with cudaPointerGetAttributes.
+ * Calls whose outputs are in host memory return after the result is there;
+ * calls whose outputs are in device memory are asynchronous on `stream` (a
+ * cudaStream_t; NULL is the legacy default stream).
+ *
+ * Errors: every entry point returns an sp_status.  Argument errors, allocation
+ * failures and CUDA launch errors are returned at once.  Errors found by the
+ * GPU while an asynchronous call runs (a path count out of range, a barrier
+ * wait that timed out) are latched in the graph and returned by
+ * sp_graph_check() once the stream has been synchronised, and by any later
+ * synchronous call on the same graph.  sp_last_error() gives a one-line
+ * description of the last failure on the calling thread.  Nothing here ever
+ * aborts or traps the GPU.
+ */
+#ifndef STARBC_H
+#define STARBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SP_API __attribute__((visibility("default")))
+#else
+#define SP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* sp_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    SP_OK = 0,
+    SP_NOT_READY = 1,        /* request still running (sp_bc_poll) */
+    SP_ERR_INVALID_ARG = -1, /* bad pointer, size, source id or option */
+    SP_ERR_OOM = -2,         /* device or pinned host memory exhausted */
+    SP_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    SP_ERR_TOO_LARGE = -4,   /* nnz >= 2^31, or a limit of the chosen form exceeded */
+    SP_ERR_RANGE = -5,       /* a path count or dependency left the representable range */
+    SP_ERR_TIMEOUT = -6,     /* a device-side wait gave up (the launch stopped cleanly) */
+    SP_ERR_CANCELLED = -7,   /* request cancelled */
+    SP_ERR_BAD_GRAPH = -8,   /* CSR failed validation (row_ptr not monotone, id out of range, ...) */
+    SP_ERR_NO_DEVICE = -9    /* no CUDA device of compute capability 10.3 */
+} sp_status;
+
+typedef struct sp_graph_s* sp_graph;
+typedef struct sp_server_s* sp_server;
+typedef int64_t sp_request;
+
+/* ------------------------------------------------------------------------ */
+/* Graphs                                                                    */
+
+/* Flags for sp_graph_create. */
+#define SP_GRAPH_CHECK_SYMMETRIC 0x1u /* also verify every arc (u,v) has its reverse (v,u) */
+
+typedef struct {
+    int32_t n;
+    int32_t max_degree;
+    int64_t nnz;
+    int64_t isolated;       /* vertices of degree 0 */
+    int32_t sorted_rows;    /* 1 when every row is strictly increasing */
+    int32_t has_self_loops; /* 1 when some arc (v,v) exists */
+    int32_t has_duplicates; /* 1 when some arc appears twice in a row (only detected on sorted rows) */
+    int32_t symmetric;      /* 1 yes, 0 no, -1 not checked */
+} sp_graph_info;
+
+/*
+ * Copy a CSR graph into device memory and validate it on the GPU: row_ptr[0]
+ * == 0, row_ptr non-decreasing, row_ptr[n] == nnz, every col_idx in [0, n).
+ * The inputs are copied before return (the caller may free them); the graph
+ * owns its device memory until sp_graph_destroy.  Blocks until done.
+ * n >= 0; nnz < 2^31.  Returns SP_ERR_BAD_GRAPH on a CSR that fails, with the
+ * first offending index in sp_last_error().
+ */
+SP_API sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
+                          uint32_t flags, sp_stream stream, sp_graph* out);
+SP_API sp_status sp_graph_destroy(sp_graph g);
+SP_API sp_status sp_graph_get_info(sp_graph g, sp_graph_info* out);
+/* Return (and clear) a device-side error latched by an earlier asynchronous
+   call on this graph; synchronise the stream of that call first. */
+SP_API sp_status sp_graph_check(sp_graph g);
+
+/* ------------------------------------------------------------------------ */
+/* Betweenness centrality                                                   */
+
+enum { SP_FP64 = 0, SP_FP32_DELTA = 1 };
+enum { SP_FORM_AUTO = 0, SP_FORM_PLAIN = 1, SP_FORM_BATCHED = 2 };
+
+typedef struct {
+    int32_t precision;          /* SP_FP64 (delta in FP64) or SP_FP32_DELTA (delta stored in FP32) */
+    int32_t form;               /* SP_FORM_AUTO, SP_FORM_PLAIN (one source at a time) or SP_FORM_BATCHED */
+    int32_t batch;              /* batched form: sources per batch, 32, 64, 128 or 256; 0 = autotuned */
+    int32_t max_ctas;           /* cap on the persistent grid (0 = every co-resident CTA) */
+    int64_t barrier_timeout_ns; /* per device-side wait; 0 = 20 s */
+    int32_t debug_flags;        /* SP_DEBUG_* (tests only) */
+    int32_t reserved[3];
+} sp_bc_opts;
+
+/* debug_flags: block 0 leaves at one grid barrier without arriving, so the
+   other blocks' waits run out and the call returns SP_ERR_TIMEOUT. */
+#define SP_DEBUG_SKIP_BARRIER 0x1
+
+typedef struct {
+    int64_t traversed_arcs; /* sum over sources s of A_s = sum of degrees of vertices reached from s */
+    int64_t reached;        /* sum over sources of |R_s| (including s) */
+    int64_t entries;        /* (vertex, level) work entries over all batches (batched form) */
+    int64_t scanned_arcs;   /* adjacency entries read, forward + backward */
+    int32_t max_levels;     /* max over sources of L = 1 + eccentricity of s */
+    int32_t batches;        /* launches' batches (plain form: one per source) */
+    int32_t batch;          /* sources per batch used (1 for the plain form) */
+    int32_t form;           /* SP_FORM_PLAIN or SP_FORM_BATCHED */
+    int32_t promoted;       /* FP32_DELTA batches rerun with FP64 delta (range) */
+    int32_t sigma_float;    /* batches whose path counts needed FP64 with rescaling */
+    int32_t pad[2];
+} sp_bc_stats;
+
+SP_API void sp_bc_opts_default(sp_bc_opts* o);
+
+/*
+ * BC over sources[0..nsrc) into bc_out[n] (FP64, overwritten, not accumulated:
+ * the paper's attachNodeProperty(BC = 0) then the per-source sums).
+ * sources: int32, host or device; each in [0, n).  nsrc == 0 gives all zeros.
+ * bc_out: host or device.  Device outputs: asynchronous on `stream`.
+ */
+SP_API sp_status sp_bc(sp_graph g, const int32_t* sources, int32_t nsrc, double* bc_out, sp_stream stream);
+
+/* As sp_bc with options; `stats` (host, may be NULL) makes the call synchronous. */
+SP_API sp_status sp_bc_ex(sp_graph g, const int32_t* sources, int32_t nsrc, const sp_bc_opts* opts, double* bc_out,
+                   sp_bc_stats* stats, sp_stream stream);
+
+/*
+ * Hop distances of the forward BFS (Fig. 1, iterateInBFS; Section 3.3 BFS
+ * traversal): dist_out[i * n + v] = dist(sources[i], v), -1 when unreachable.
+ * dist_out: int32 [nsrc][n], host or device.
+ */
+SP_API sp_status sp_bfs(sp_graph g, const int32_t* sources, int32_t nsrc, int32_t* dist_out, sp_stream stream);
+
+/*
+ * Shortest-path counts from one source (Fig. 1, the sigma sums of the forward
+ * pass) as mant_out[v] * 2^exp2_out[v], mant in [1, 2), 0 when unreachable.
+ * mant_out: double[n]; exp2_out: int64[n]; host or device.
+ */
+SP_API sp_status sp_sigma(sp_graph g, int32_t src, double* mant_out, int64_t* exp2_out, sp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of BC requests over resident graphs          */
+
+/*
+ * A server owns a host scheduler thread and `max_slots` CUDA streams.  Graphs
+ * added to it stay resident.  A request is admitted when its device footprint
+ * fits in what is left of `hbm_budget_bytes`; admitted requests are split into
+ * source batches that run concurrently on free slots, so requests that arrive
+ * while others run start as soon as a slot and memory free up.  A request's
+ * result does not depend on what else runs: its batches and their order are
+ * fixed by the request alone.
+ */
+SP_API sp_status sp_server_create(size_t hbm_budget_bytes, int32_t max_slots, sp_server* out);
+SP_API sp_status sp_server_add_graph(sp_server s, sp_graph g, int32_t* graph_id);
+/* bc_out: device double[n] (n of the graph); sources copied before return. */
+SP_API sp_status sp_bc_submit(sp_server s, int32_t graph_id, const int32_t* sources, int32_t nsrc,
+                       const sp_bc_opts* opts, double* bc_out, sp_request* req);
+SP_API sp_status sp_bc_poll(sp_server s, sp_request req);                     /* SP_OK, SP_NOT_READY or the error */
+SP_API sp_status sp_bc_wait(sp_server s, sp_request req, int64_t timeout_ns); /* SP_NOT_READY on timeout */
+SP_API sp_status sp_bc_cancel(sp_server s, sp_request req);
+/* Host steady-clock times in ns: submission, first batch start, completion (0 if not yet). */
+SP_API sp_status sp_request_times(sp_server s, sp_request req, int64_t* submit_ns, int64_t* start_ns, int64_t* done_ns);
+SP_API sp_status sp_server_destroy(sp_server s); /* waits for running requests */
+
+/* ------------------------------------------------------------------------ */
+SP_API const char* sp_status_string(sp_status st);
+SP_API const char* sp_last_error(void); /* thread-local; "" when none */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STARBC_H */

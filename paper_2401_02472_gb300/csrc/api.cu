@@ -1,0 +1,494 @@
+// The C ABI: argument checks, host/device staging, choice of form, and the
+// reruns that keep results exact when a representation runs out of range.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdlib>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sp {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+sp_status fail(sp_status st, const std::string& what) {
+    set_last_error(std::string(sp_status_string(st)) + ": " + what);
+    return st;
+}
+
+sp_status cuda_fail(cudaError_t e, const char* what) {
+    std::string s = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(SP_ERR_OOM, s);
+    return fail(SP_ERR_CUDA, s);
+}
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static sp_status check_device() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SP_ERR_NO_DEVICE, "no CUDA device");
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3)
+        return fail(SP_ERR_NO_DEVICE, "this build targets compute capability 10.3 (sm_103a); device " +
+                                          std::to_string(dev) + " is " + std::to_string(major) + "." +
+                                          std::to_string(minor));
+    static bool pool_set[64] = {false};
+    if (dev >= 0 && dev < 64 && !pool_set[dev]) {
+        // Keep freed workspace in the stream-ordered pool between calls.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool_set[dev] = true;
+    }
+    return SP_OK;
+}
+
+// A device copy of `count` int32 from host or device memory (freed by the caller).
+static sp_status stage_in(const int32_t* src, int64_t count, cudaStream_t st, int32_t** out) {
+    *out = nullptr;
+    if (count <= 0) return SP_OK;
+    SP_CUDA(cudaMallocAsync((void**)out, sizeof(int32_t) * (size_t)count, st));
+    cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(*out, src, sizeof(int32_t) * (size_t)count, kind, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(*out, st);
+        *out = nullptr;
+        return cuda_fail(e, "copying input");
+    }
+    return SP_OK;
+}
+
+__global__ void check_sources_kernel(const int32_t* s, int32_t nsrc, int32_t n, int* bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsrc; i += gridDim.x * blockDim.x)
+        if (s[i] < 0 || s[i] >= n) atomicMin(bad, i);
+}
+
+static sp_status check_sources(const int32_t* d_src, int32_t nsrc, int32_t n, cudaStream_t st) {
+    if (nsrc <= 0) return SP_OK;
+    int* d_bad = nullptr;
+    SP_CUDA(cudaMallocAsync((void**)&d_bad, sizeof(int), st));
+    int h_bad = INT32_MAX;
+    cudaError_t e = cudaMemcpyAsync(d_bad, &h_bad, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        check_sources_kernel<<<std::min(1024, (nsrc + 255) / 256), 256, 0, st>>>(d_src, nsrc, n, d_bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d_bad, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "checking sources");
+    if (h_bad != INT32_MAX)
+        return fail(SP_ERR_INVALID_ARG, "source " + std::to_string(h_bad) + " is not a vertex id in [0, n)");
+    return SP_OK;
+}
+
+std::string barrier_diagnostic(const Ctl& h, int grid) {
+    int lo = INT32_MAX, hi = INT32_MIN, nlo = 0;
+    for (int b = 0; b < grid && b < 1024; ++b) {
+        int p = h.block_phase[b];
+        if (p < lo) { lo = p; nlo = 0; }
+        if (p == lo) ++nlo;
+        hi = std::max(hi, p);
+    }
+    return " (timed out at barrier " + std::to_string(h.err_where) + " with " + std::to_string(h.timeout_count) +
+           " of " + std::to_string(grid) + " blocks arrived; blocks' last barriers " + std::to_string(lo) + ".." +
+           std::to_string(hi) + ", " + std::to_string(nlo) + " at the lowest)";
+}
+
+static sp_status map_device_error(int err, const char* form, const std::string& diag = "") {
+    if (err == 0) return SP_OK;
+    std::string f = std::string(form) + diag;
+    switch (err) {
+        case SP_ERR_RANGE: return fail(SP_ERR_RANGE, f + ": a path count or dependency left the FP64 range");
+        case SP_ERR_TIMEOUT: return fail(SP_ERR_TIMEOUT, f + ": a grid barrier wait timed out");
+        case kErrCapacity:
+        case kErrCapEntries:
+        case kErrCapHubs:
+        case kErrCapLevels: return fail(SP_ERR_TOO_LARGE, f + ": workspace capacity exceeded");
+        case kErrSigmaOverflow: return fail(SP_ERR_RANGE, f + ": path counts overflowed");
+        case kErrThetaRange32: return fail(SP_ERR_RANGE, f + ": FP32 dependency out of range");
+        case kErrCorrupt: return fail(SP_ERR_CUDA, f + ": device state out of range (internal error)");
+        default: return fail(SP_ERR_CUDA, f + ": device error " + std::to_string(err));
+    }
+}
+
+static uint64_t bfs_timeout_ns() {
+    const char* e = getenv("SP_BARRIER_TIMEOUT_NS");
+    return e ? strtoull(e, nullptr, 10) : 20000000000ull;
+}
+
+static uint64_t timeout_of(const sp_bc_opts& o) {
+    return o.barrier_timeout_ns > 0 ? (uint64_t)o.barrier_timeout_ns : bfs_timeout_ns();
+}
+
+int default_batch_width(int32_t nsrc) { return nsrc > 32 ? 64 : 32; }
+
+// Device bytes one batched launch of this width allocates (default capacities).
+size_t batched_workspace_bytes(const Graph* g, int width, bool theta_f32) {
+    const size_t n = (size_t)g->n, W = (size_t)width / 32, B = (size_t)width;
+    const size_t lcap = std::min<size_t>(n + 2, 16384);
+    const size_t ecap = std::min<size_t>(std::max<size_t>(8 * n, 1 << 16), n * std::min(B, lcap));
+    const size_t hcap = (size_t)g->nnz / 512 * 8 + 1024, segcap = (size_t)g->nnz / 1024 + (size_t)g->nnz / 512 + 2;
+    return 4 * 4 * n * W + 4 * n * W + 4 * n + 8 * n * B + (theta_f32 ? 4 : 8) * n * B + ecap * (4 + 4 * W) +
+           hcap * 24 + segcap * B * 8 + 2 * lcap * B * 4 + 3 * (lcap + 2) * 8 + (1 << 20);
+}
+
+// Batch width when the caller leaves it open: the autotuned value for the
+// graph if there is one, else by source count.
+static int choose_width(Graph* g, const sp_bc_opts& o, int32_t nsrc) {
+    if (o.batch > 0) return o.batch;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        auto it = g->tuned_batch.find(o.precision);
+        if (it != g->tuned_batch.end()) return it->second;
+    }
+    return default_batch_width(nsrc);
+}
+
+// Run BC on device buffers, rerunning with a wider representation or more
+// workspace when the device reports that it ran out of one.
+static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
+                           sp_bc_stats* stats, cudaStream_t st) {
+    bool sigma_float;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        sigma_float = g->sigma_float;
+    }
+    bool theta_f32 = o.precision == SP_FP32_DELTA;
+    int form = o.form;
+    if (form == SP_FORM_AUTO) form = nsrc >= 16 ? SP_FORM_BATCHED : SP_FORM_PLAIN;
+    int width = form == SP_FORM_BATCHED ? choose_width(g, o, nsrc) : 1;
+    int promoted = 0, sigma_batches = 0;
+    int64_t ecap = 0, hcap = 0, lcap = 0;
+    LaunchResult r;
+    for (int attempt = 0; attempt < 16; ++attempt) {
+        r = LaunchResult{};
+        sp_status rc;
+        if (form == SP_FORM_PLAIN) {
+            PlainLaunch L{};
+            L.g = g;
+            L.d_sources = d_src;
+            L.nsrc = nsrc;
+            L.d_bc = d_bc;
+            L.mode = PlainMode::BC;
+            L.sigma_float = sigma_float;
+            L.theta_f32 = theta_f32;
+            L.max_ctas = o.max_ctas;
+            L.timeout_ns = timeout_of(o);
+            L.debug_flags = o.debug_flags;
+            L.stream = st;
+            rc = run_plain(L, &r);
+        } else {
+            BatchedLaunch L{};
+            L.g = g;
+            L.d_sources = d_src;
+            L.nsrc = nsrc;
+            L.d_bc = d_bc;
+            L.width = width;
+            L.sigma_float = sigma_float;
+            L.theta_f32 = theta_f32;
+            L.max_ctas = o.max_ctas;
+            L.timeout_ns = timeout_of(o);
+            L.debug_flags = o.debug_flags;
+            L.stream = st;
+            L.entry_cap = ecap;
+            L.hub_cap = hcap;
+            L.level_cap = lcap;
+            rc = run_batched(L, &r);
+        }
+        if (rc != SP_OK) return rc;
+        if (r.err == kErrSigmaOverflow && !sigma_float) {
+            sigma_float = true;
+            sigma_batches = 1;
+            std::lock_guard<std::mutex> lk(g->mu);
+            g->sigma_float = true;
+            continue;
+        }
+        if (r.err == kErrThetaRange32 && theta_f32) {
+            theta_f32 = false;
+            promoted = 1;
+            continue;
+        }
+        if (form == SP_FORM_BATCHED) {
+            if (r.err == kErrCapEntries) { ecap = 2 * r.ecap; continue; }
+            if (r.err == kErrCapHubs) { hcap = 2 * r.hcap; continue; }
+            if (r.err == kErrCapLevels && r.lcap < (int64_t)g->n + 2) { lcap = (int64_t)g->n + 2; continue; }
+        }
+        break;
+    }
+    sp_status rc = map_device_error(r.err, form == SP_FORM_PLAIN ? "plain form" : "batched form", r.diag);
+    if (rc != SP_OK) return rc;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->traversed_arcs = (int64_t)r.traversed_arcs;
+        stats->reached = (int64_t)r.reached;
+        stats->entries = (int64_t)r.entries;
+        stats->scanned_arcs = (int64_t)r.scanned_arcs;
+        stats->max_levels = r.levels;
+        stats->batch = width;
+        stats->batches = form == SP_FORM_PLAIN ? nsrc : (nsrc + width - 1) / width;
+        stats->form = form;
+        stats->promoted = promoted;
+        stats->sigma_float = sigma_float ? 1 : sigma_batches;
+    }
+    return SP_OK;
+}
+
+sp_status bc_device_entry(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
+                          sp_bc_stats* stats, cudaStream_t st) {
+    return bc_device(g, d_src, nsrc, o, d_bc, stats, st);
+}
+
+}  // namespace sp
+
+using namespace sp;
+
+extern "C" {
+
+const char* sp_status_string(sp_status st) {
+    switch (st) {
+        case SP_OK: return "SP_OK";
+        case SP_NOT_READY: return "SP_NOT_READY";
+        case SP_ERR_INVALID_ARG: return "SP_ERR_INVALID_ARG";
+        case SP_ERR_OOM: return "SP_ERR_OOM";
+        case SP_ERR_CUDA: return "SP_ERR_CUDA";
+        case SP_ERR_TOO_LARGE: return "SP_ERR_TOO_LARGE";
+        case SP_ERR_RANGE: return "SP_ERR_RANGE";
+        case SP_ERR_TIMEOUT: return "SP_ERR_TIMEOUT";
+        case SP_ERR_CANCELLED: return "SP_ERR_CANCELLED";
+        case SP_ERR_BAD_GRAPH: return "SP_ERR_BAD_GRAPH";
+        case SP_ERR_NO_DEVICE: return "SP_ERR_NO_DEVICE";
+    }
+    return "SP_ERR_UNKNOWN";
+}
+
+const char* sp_last_error(void) { return g_last_error.c_str(); }
+
+void sp_bc_opts_default(sp_bc_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = SP_FP64;
+    o->form = SP_FORM_AUTO;
+}
+
+sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz, uint32_t flags,
+                          sp_stream stream, sp_graph* out) {
+    set_last_error("");
+    if (!out) return fail(SP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || nnz < 0) return fail(SP_ERR_INVALID_ARG, "negative size");
+    if (nnz >= (int64_t)INT32_MAX) return fail(SP_ERR_TOO_LARGE, "nnz must be below 2^31 (int32 row_ptr)");
+    if (!row_ptr) return fail(SP_ERR_INVALID_ARG, "row_ptr is NULL");
+    if (nnz > 0 && !col_idx) return fail(SP_ERR_INVALID_ARG, "col_idx is NULL");
+    if (flags & ~(uint32_t)SP_GRAPH_CHECK_SYMMETRIC) return fail(SP_ERR_INVALID_ARG, "unknown flag");
+    sp_status rc = check_device();
+    if (rc != SP_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Graph* g = new Graph();
+    cudaGetDevice(&g->device);
+    g->n = n;
+    g->nnz = nnz;
+    auto cleanup = [&](sp_status s) {
+        if (g->d_rp) cudaFree(g->d_rp);
+        if (g->d_ci) cudaFree(g->d_ci);
+        delete g;
+        return s;
+    };
+    if (cudaMalloc((void**)&g->d_rp, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&g->d_ci, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(SP_ERR_OOM, "graph arrays"));
+    }
+    cudaError_t e = cudaMemcpyAsync(g->d_rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1),
+                                    is_device_ptr(row_ptr) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(g->d_ci, col_idx, sizeof(int32_t) * (size_t)nnz,
+                            is_device_ptr(col_idx) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "copying the graph"));
+    std::string detail;
+    rc = validate_graph(g, flags, st, &detail);
+    if (rc == SP_ERR_BAD_GRAPH) return cleanup(fail(rc, detail));
+    if (rc != SP_OK) return cleanup(rc);
+    *out = reinterpret_cast<sp_graph>(g);
+    return SP_OK;
+}
+
+sp_status sp_graph_destroy(sp_graph gh) {
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    cudaFree(g->d_rp);
+    cudaFree(g->d_ci);
+    delete g;
+    return SP_OK;
+}
+
+sp_status sp_graph_get_info(sp_graph gh, sp_graph_info* out) {
+    if (!gh || !out) return fail(SP_ERR_INVALID_ARG, "NULL argument");
+    *out = reinterpret_cast<Graph*>(gh)->info;
+    return SP_OK;
+}
+
+sp_status sp_graph_check(sp_graph gh) {
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    return SP_OK;
+}
+
+sp_status sp_bc_ex(sp_graph gh, const int32_t* sources, int32_t nsrc, const sp_bc_opts* opts, double* bc_out,
+                   sp_bc_stats* stats, sp_stream stream) {
+    set_last_error("");
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    if (nsrc < 0) return fail(SP_ERR_INVALID_ARG, "nsrc < 0");
+    if (nsrc > 0 && !sources) return fail(SP_ERR_INVALID_ARG, "sources is NULL");
+    if (g->n > 0 && !bc_out) return fail(SP_ERR_INVALID_ARG, "bc_out is NULL");
+    sp_bc_opts o;
+    sp_bc_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision != SP_FP64 && o.precision != SP_FP32_DELTA) return fail(SP_ERR_INVALID_ARG, "precision");
+    if (o.form < SP_FORM_AUTO || o.form > SP_FORM_BATCHED) return fail(SP_ERR_INVALID_ARG, "form");
+    if (o.batch != 0 && o.batch != 32 && o.batch != 64 && o.batch != 128 && o.batch != 256)
+        return fail(SP_ERR_INVALID_ARG, "batch must be 0, 32, 64, 128 or 256");
+    if (o.max_ctas < 0 || o.barrier_timeout_ns < 0) return fail(SP_ERR_INVALID_ARG, "negative option");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (g->n == 0) return SP_OK;
+    const bool host_out = !is_device_ptr(bc_out);
+    double* d_bc = bc_out;
+    if (host_out) SP_CUDA(cudaMallocAsync((void**)&d_bc, sizeof(double) * (size_t)g->n, st));
+    int32_t* d_src = nullptr;
+    sp_status rc = stage_in(sources, nsrc, st, &d_src);
+    if (rc == SP_OK) rc = check_sources(d_src, nsrc, g->n, st);
+    if (rc == SP_OK) {
+        if (nsrc == 0) {
+            cudaError_t e = cudaMemsetAsync(d_bc, 0, sizeof(double) * (size_t)g->n, st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "zeroing bc_out");
+        } else {
+            rc = bc_device(g, d_src, nsrc, o, d_bc, stats, st);
+        }
+    }
+    if (rc == SP_OK && host_out) {
+        cudaError_t e = cudaMemcpyAsync(bc_out, d_bc, sizeof(double) * (size_t)g->n, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copying bc_out");
+    }
+    if (d_src) cudaFreeAsync(d_src, st);
+    if (host_out) cudaFreeAsync(d_bc, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == SP_OK && e != cudaSuccess) rc = cuda_fail(e, "sp_bc");
+    return rc;
+}
+
+sp_status sp_bc(sp_graph g, const int32_t* sources, int32_t nsrc, double* bc_out, sp_stream stream) {
+    return sp_bc_ex(g, sources, nsrc, nullptr, bc_out, nullptr, stream);
+}
+
+sp_status sp_bfs(sp_graph gh, const int32_t* sources, int32_t nsrc, int32_t* dist_out, sp_stream stream) {
+    set_last_error("");
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    if (nsrc < 0) return fail(SP_ERR_INVALID_ARG, "nsrc < 0");
+    if (nsrc == 0 || g->n == 0) return SP_OK;
+    if (!sources || !dist_out) return fail(SP_ERR_INVALID_ARG, "NULL pointer");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t count = (size_t)nsrc * (size_t)g->n;
+    const bool host_out = !is_device_ptr(dist_out);
+    int32_t* d_dist = dist_out;
+    if (host_out) SP_CUDA(cudaMallocAsync((void**)&d_dist, sizeof(int32_t) * count, st));
+    int32_t* d_src = nullptr;
+    sp_status rc = stage_in(sources, nsrc, st, &d_src);
+    if (rc == SP_OK) rc = check_sources(d_src, nsrc, g->n, st);
+    if (rc == SP_OK) {
+        PlainLaunch L{};
+        L.g = g;
+        L.d_sources = d_src;
+        L.nsrc = nsrc;
+        L.d_dist = d_dist;
+        L.mode = PlainMode::BFS;
+        L.sigma_float = false;
+        L.theta_f32 = false;
+        L.timeout_ns = bfs_timeout_ns();
+        L.stream = st;
+        LaunchResult r;
+        rc = run_plain(L, &r);
+        if (rc == SP_OK) rc = map_device_error(r.err, "bfs", r.diag);
+    }
+    if (rc == SP_OK && host_out) {
+        cudaError_t e = cudaMemcpyAsync(dist_out, d_dist, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copying dist_out");
+    }
+    if (d_src) cudaFreeAsync(d_src, st);
+    if (host_out) cudaFreeAsync(d_dist, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == SP_OK && e != cudaSuccess) rc = cuda_fail(e, "sp_bfs");
+    return rc;
+}
+
+sp_status sp_sigma(sp_graph gh, int32_t src, double* mant_out, int64_t* exp2_out, sp_stream stream) {
+    set_last_error("");
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    if (src < 0 || src >= g->n) return fail(SP_ERR_INVALID_ARG, "source out of range");
+    if (!mant_out || !exp2_out) return fail(SP_ERR_INVALID_ARG, "NULL pointer");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)g->n;
+    const bool host_m = !is_device_ptr(mant_out), host_e = !is_device_ptr(exp2_out);
+    double* d_m = mant_out;
+    long long* d_e = reinterpret_cast<long long*>(exp2_out);
+    if (host_m) SP_CUDA(cudaMallocAsync((void**)&d_m, sizeof(double) * n, st));
+    if (host_e) SP_CUDA(cudaMallocAsync((void**)&d_e, sizeof(long long) * n, st));
+    int32_t* d_src = nullptr;
+    sp_status rc = stage_in(&src, 1, st, &d_src);
+    if (rc == SP_OK) {
+        PlainLaunch L{};
+        L.g = g;
+        L.d_sources = d_src;
+        L.nsrc = 1;
+        L.d_mant = d_m;
+        L.d_exp = d_e;
+        L.mode = PlainMode::SIGMA;
+        L.sigma_float = true;
+        L.theta_f32 = false;
+        L.timeout_ns = 20000000000ull;
+        L.stream = st;
+        LaunchResult r;
+        rc = run_plain(L, &r);
+        if (rc == SP_OK) rc = map_device_error(r.err, "sigma", r.diag);
+    }
+    cudaError_t e = cudaSuccess;
+    if (rc == SP_OK && host_m) e = cudaMemcpyAsync(mant_out, d_m, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    if (rc == SP_OK && e == cudaSuccess && host_e)
+        e = cudaMemcpyAsync(exp2_out, d_e, sizeof(long long) * n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copying sigma");
+    if (d_src) cudaFreeAsync(d_src, st);
+    if (host_m) cudaFreeAsync(d_m, st);
+    if (host_e) cudaFreeAsync(d_e, st);
+    e = cudaStreamSynchronize(st);
+    if (rc == SP_OK && e != cudaSuccess) rc = cuda_fail(e, "sp_sigma");
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,846 @@
+// Batched form: B = 32*W sources per batch traverse the graph together.
+//
+// Same method as the plain form (paper Section 2, Fig. 1, ComputeBC; level-
+// synchronous BFS of Section 3.3), with many sources sharing each adjacency
+// scan (the sourceSet loop of Fig. 1 run in parallel instead of in sequence):
+//
+//   per vertex v:          seen[v]    B-bit mask of sources that reached v
+//   per level d:           F_d[v]     B-bit mask of sources with dist_s(v) = d
+//                          (dense copies for the levels in use, a ring of 4)
+//   per (vertex, source):  sig[v][s]  path counts, row-major so that a warp
+//                          whose lane k*32+l is source k*32+l reads a row with
+//                          coalesced loads
+//                          th[v][s]   (1 + delta_s(v)) / sigma_s(v)
+//   level stack:           entries (v, F_d[v]) for every vertex active at d
+//
+// Forward level d, for each entry (v, F) and each neighbour u of v:
+//   sigma pull:   m = F & F_{d-1}[u];  sig[v][s] += sig[u][s] for s in m
+//   discovery:    new = F & ~seen[u];  seen[u] |= new (atomic OR, the old value
+//                 tells which bits are really new), F_{d+1}[u] |= new, and the
+//                 first thread to give u bits at this level appends u
+// Backward level d (L-1 .. 1), for each entry (v, F):
+//   m = F & F_{d+1}[w] over neighbours w;  acc[s] += th[w][s] for s in m
+//   delta_s(v) = sigma_s(v) * acc[s];  th[v][s] = (1 + delta) / sigma;
+//   BC[v] += sum_s delta_s(v)
+// The per-(vertex, source) sums walk v's row in CSR order (hubs: in segment
+// order), so results are bit-identical from run to run.
+#pragma once
+
+#include <climits>
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sp {
+
+constexpr int kBatchThreads = 256;
+
+struct BatchArgs {
+    const int32_t* rp;
+    const int32_t* ci;
+    int32_t n;
+    const int32_t* sources;
+    int32_t nsrc;
+    double* bc;
+    uint32_t* dense;          // [4][n][W]
+    uint32_t* seen;           // [n][W]
+    int32_t* ptag;            // [n] level stamp of the last append
+    void* sig;                // [n][B]
+    void* th;                 // [n][B]
+    int32_t* ent;             // [ecap] level stack (vertex | hub flag)
+    uint32_t* emask;          // [ecap][W]
+    long long ecap;
+    int32_t* eoff;            // [lcap+2]
+    HubRec* hubs;
+    int32_t hcap;
+    int32_t* hoff;            // [lcap+2]
+    unsigned long long* hcnt; // [lcap+2]
+    int32_t* hdone;           // [2*hcap]
+    void* part;               // [segcap][B] 8-byte slots
+    int32_t segcap;
+    int32_t* emax;            // [lcap][B]
+    int32_t* emin;            // [lcap][B]
+    int32_t lcap;
+    Ctl* ctl;
+    int* err_latch;
+    int debug_flags;
+    unsigned long long timeout_ns;
+    int t_hub, seg;
+};
+
+template <int W>
+__device__ __forceinline__ void load_mask(const uint32_t* p, uint32_t (&m)[W]) {
+    if constexpr (W == 1) {
+        m[0] = __ldcg(p);
+    } else if constexpr (W == 2) {
+        uint2 x = __ldcg(reinterpret_cast<const uint2*>(p));
+        m[0] = x.x; m[1] = x.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < W; k += 4) {
+            uint4 x = __ldcg(reinterpret_cast<const uint4*>(p + k));
+            m[k] = x.x; m[k + 1] = x.y; m[k + 2] = x.z; m[k + 3] = x.w;
+        }
+    }
+}
+template <int W>
+__device__ __forceinline__ void store_mask(uint32_t* p, const uint32_t (&m)[W]) {
+    if constexpr (W == 1) {
+        p[0] = m[0];
+    } else if constexpr (W == 2) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(m[0], m[1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < W; k += 4) *reinterpret_cast<uint4*>(p + k) = make_uint4(m[k], m[k + 1], m[k + 2], m[k + 3]);
+    }
+}
+template <int W>
+__device__ __forceinline__ void zero_mask(uint32_t* p) {
+    uint32_t z[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) z[k] = 0u;
+    store_mask<W>(p, z);
+}
+
+template <int W, typename SigT, typename ThT>
+struct BatchKernel {
+    static constexpr int B = 32 * W;
+    static constexpr bool kFloatSig = !std::is_integral<SigT>::value;
+    static constexpr bool kTh32 = sizeof(ThT) == 4;
+    // dependency accumulator: FP32 for FP32 dependencies, FP64 otherwise
+    using AccT = typename std::conditional<kTh32, float, double>::type;
+
+    const BatchArgs& a;
+    Ctl* ctl;
+    int lane;
+    int d = 0;
+    int hoff_d = 0, nrec_d = 0, nseg_d = 0, hoff_next = 0;
+    int stamp_next = 0;
+    uint32_t* prev = nullptr;  // dense F_{d-1}
+    uint32_t* cur = nullptr;   // dense F_d
+    uint32_t* next = nullptr;  // dense F_{d+1}
+    int cshift[W];             // per-source shift between level d-1 and d (forward) / d and d+1 (backward)
+    int my_emax[W], my_emin[W];
+    bool ovf = false;
+    unsigned long long st_arcs = 0, st_reached = 0, st_entries = 0, st_scanned = 0;
+
+    __device__ BatchKernel(const BatchArgs& args) : a(args), ctl(args.ctl), lane(lane_id()) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) { cshift[k] = 0; my_emax[k] = INT_MIN; my_emin[k] = INT_MAX; }
+    }
+    __device__ __forceinline__ SigT* sig() const { return reinterpret_cast<SigT*>(a.sig); }
+    __device__ __forceinline__ ThT* th() const { return reinterpret_cast<ThT*>(a.th); }
+    __device__ __forceinline__ uint32_t* ring(int r) const { return a.dense + (size_t)(r & 3) * (size_t)a.n * W; }
+
+    // Append vertex u to level nl of the stack (and to the hub list).
+    __device__ void push(int u, int nl) {
+        int du = __ldg(&a.rp[u + 1]) - __ldg(&a.rp[u]);
+        bool hub = du > a.t_hub;
+        int pos = aggregated_slot(&ctl->qtail);
+        if ((long long)pos >= a.ecap) { set_error(ctl, kErrCapEntries); return; }
+        a.ent[pos] = hub ? (int)((unsigned)u | kHubFlag) : u;
+        if (hub) {
+            int nseg = (du + a.seg - 1) / a.seg;
+            unsigned long long old = atomicAdd(&a.hcnt[nl], (1ull << 32) | (unsigned long long)(unsigned)nseg);
+            int rec = hoff_next + (int)(old >> 32);
+            int sb = (int)(old & 0xFFFFFFFFull);
+            if (rec >= a.hcap || sb + nseg > a.segcap) { set_error(ctl, kErrCapHubs); return; }
+            HubRec h;
+            h.v = u; h.qpos = pos; h.nseg = nseg; h.seg_base = sb;
+            a.hubs[rec] = h;
+            a.hdone[rec] = 0;
+            a.hdone[a.hcap + rec] = 0;
+        }
+    }
+
+    // Discovery of neighbour u by sources F (one lane, one arc).
+    __device__ __forceinline__ void discover(int u, const uint32_t (&F)[W]) {
+        uint32_t s[W];
+        load_mask<W>(a.seen + (size_t)u * W, s);
+        uint32_t any = 0;
+        uint32_t nw[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) { nw[k] = F[k] & ~s[k]; any |= nw[k]; }
+        if (!any) return;
+        uint32_t anynew = 0;
+        uint32_t* nx = next + (size_t)u * W;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            if (nw[k]) {
+                uint32_t old = atomicOr(&a.seen[(size_t)u * W + k], nw[k]);
+                uint32_t nb = nw[k] & ~old;
+                if (nb) { atomicOr(&nx[k], nb); anynew |= nb; }
+            }
+        }
+        if (anynew) {
+            if (atomicMax(&a.ptag[u], stamp_next) < stamp_next) push(u, d + 1);
+        }
+    }
+
+    // Store the new path counts of entry (v, F) from the per-lane sums.
+    __device__ __forceinline__ void sigma_flush(int v, const uint32_t (&F)[W], const SigT (&acc)[W]) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            if ((F[k] >> lane) & 1u) {
+                size_t idx = (size_t)v * B + k * 32 + lane;
+                if constexpr (kFloatSig) {
+                    double val = scale2((double)acc[k], -cshift[k]);
+                    if (!normal_finite(val)) set_error(ctl, SP_ERR_RANGE);
+                    sig()[idx] = (SigT)val;
+                    int e = exp_field(val) - 1023;
+                    my_emax[k] = max(my_emax[k], e);
+                    my_emin[k] = min(my_emin[k], e);
+                } else {
+                    sig()[idx] = acc[k];
+                }
+            }
+        }
+    }
+
+    // Backward: from the per-lane sums of theta over children, delta, theta(v), BC.
+    __device__ __forceinline__ void delta_flush(int v, const uint32_t (&F)[W], const AccT (&acc)[W]) {
+        AccT bcsum = 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            if ((F[k] >> lane) & 1u) {
+                size_t idx = (size_t)v * B + k * 32 + lane;
+                SigT sv = __ldcg(&sig()[idx]);
+                if constexpr (kTh32) {
+                    float sf;
+                    if constexpr (kFloatSig) {
+                        sf = (float)sv;
+                    } else {
+                        sf = u64_to_f32(sv);
+                    }
+                    float delta = sf * acc[k];
+                    if constexpr (kFloatSig) delta = (float)scale2((double)delta, -cshift[k]);
+                    float t = (1.0f + delta) / sf;
+                    if (!normal_finite_f(t) || !normal_finite_f(sf)) set_error(ctl, kErrThetaRange32);
+                    th()[idx] = t;
+                    bcsum += delta;
+                } else {
+                    double s = (double)sv;
+                    double delta = s * acc[k];
+                    if constexpr (kFloatSig) delta = scale2(delta, -cshift[k]);
+                    double t = (1.0 + delta) / s;
+                    if (!normal_finite(t)) set_error(ctl, SP_ERR_RANGE);
+                    th()[idx] = t;
+                    bcsum += delta;
+                }
+            }
+        }
+        // fixed-order reduction over the sources of this entry
+        for (int o = 16; o > 0; o >>= 1) bcsum += __shfl_xor_sync(kFull, bcsum, o);
+        if (lane == 0) a.bc[v] = __ldcg(&a.bc[v]) + (double)bcsum;
+    }
+
+    // ---------------- forward ----------------
+    // Chunk of up to 32 level-stack entries [e0, min(e0+32, qe)).
+    __device__ void fwd_chunk(int e0, int qe) {
+        const int e = e0 + lane;
+        bool valid = e < qe;
+        unsigned qv = valid ? (unsigned)__ldcg(&a.ent[e]) : kHubFlag;
+        bool hubent = (qv & kHubFlag) != 0;
+        int v = (int)(qv & kVertexMask);
+        if (valid && v >= a.n) { set_error(ctl, kErrCorrupt); valid = false; hubent = true; v = 0; }
+        uint32_t F[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) F[k] = 0u;
+        int beg = 0, deg = 0;
+        if (valid) {
+            load_mask<W>(cur + (size_t)v * W, F);
+            store_mask<W>(a.emask + (size_t)e * W, F);
+            if (!hubent) {
+                beg = __ldg(&a.rp[v]);
+                deg = __ldg(&a.rp[v + 1]) - beg;
+                int pc = 0;
+#pragma unroll
+                for (int k = 0; k < W; ++k) pc += __popc(F[k]);
+                st_arcs += (unsigned long long)deg * (unsigned long long)pc;
+                st_reached += (unsigned long long)pc;
+                st_entries += 1;
+                st_scanned += (unsigned long long)deg;
+            } else {
+                st_entries += 1;
+            }
+        }
+        const int incl = warp_incl_scan(deg);
+        const int excl = incl - deg;
+        const int total = __shfl_sync(kFull, incl, 31);
+        SigT acc[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] = 0;
+        int cur_e = -1;  // lane index of the entry whose sums are in acc
+        for (int cb = 0; cb < total; cb += kWarp) {
+            const int ai = cb + lane;
+            const bool has = ai < total;
+            // owner lane: the largest j with excl_j <= ai
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                int ex = __shfl_sync(kFull, excl, j + step < 32 ? j + step : 31);
+                if (j + step < 32 && ex <= ai) j += step;
+            }
+            const int bj = __shfl_sync(kFull, beg, j);
+            const int exj = __shfl_sync(kFull, excl, j);
+            uint32_t Fj[W], m[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) { Fj[k] = __shfl_sync(kFull, F[k], j); m[k] = 0u; }
+            int u = 0;
+            if (has) {
+                u = __ldg(&a.ci[bj + (ai - exj)]);
+                if (d > 0) {
+                    uint32_t p[W];
+                    load_mask<W>(prev + (size_t)u * W, p);
+#pragma unroll
+                    for (int k = 0; k < W; ++k) m[k] = Fj[k] & p[k];
+                }
+                discover(u, Fj);
+            }
+            if (d > 0) {
+                uint32_t anym = 0;
+#pragma unroll
+                for (int k = 0; k < W; ++k) anym |= m[k];
+                unsigned pend = __ballot_sync(kFull, anym != 0u);
+                while (pend) {
+                    const int jj = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    const int uj = __shfl_sync(kFull, u, jj);
+                    const int ej = __shfl_sync(kFull, j, jj);
+                    if (ej != cur_e) {
+                        if (cur_e >= 0) {
+                            uint32_t Fc[W];
+#pragma unroll
+                            for (int k = 0; k < W; ++k) Fc[k] = __shfl_sync(kFull, F[k], cur_e);
+                            sigma_flush(__shfl_sync(kFull, v, cur_e), Fc, acc);
+                        }
+                        cur_e = ej;
+#pragma unroll
+                        for (int k = 0; k < W; ++k) acc[k] = 0;
+                    }
+                    const SigT* row = sig() + (size_t)uj * B + lane;
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        uint32_t mk = __shfl_sync(kFull, m[k], jj);
+                        if ((mk >> lane) & 1u) {
+                            SigT x = __ldcg(row + k * 32);
+                            if constexpr (kFloatSig) {
+                                acc[k] += x;
+                            } else {
+                                SigT s2 = acc[k] + x;
+                                ovf |= s2 < x;
+                                acc[k] = s2;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (cur_e >= 0) {
+            uint32_t Fc[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) Fc[k] = __shfl_sync(kFull, F[k], cur_e);
+            sigma_flush(__shfl_sync(kFull, v, cur_e), Fc, acc);
+        }
+    }
+
+    // Segment g of this level's hubs (forward).
+    __device__ void fwd_hub_segment(int g) {
+        const int r = find_hub(a.hubs, hoff_d, hoff_d + nrec_d, g);
+        const int hv = __ldcg(&a.hubs[r].v);
+        const int nseg = __ldcg(&a.hubs[r].nseg);
+        const int sb = __ldcg(&a.hubs[r].seg_base);
+        if (hv < 0 || hv >= a.n || nseg < 1 || sb < 0 || sb + nseg > a.segcap) {
+            if (lane == 0) set_error(ctl, kErrCorrupt);
+            return;
+        }
+        const int s = g - sb;
+        const int rb = __ldg(&a.rp[hv]), re = __ldg(&a.rp[hv + 1]);
+        const int beg = rb + s * a.seg;
+        const int end = min(re, beg + a.seg);
+        uint32_t F[W];
+        load_mask<W>(cur + (size_t)hv * W, F);
+        SigT acc[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] = 0;
+        for (int cb = beg; cb < end; cb += kWarp) {
+            const int ai = cb + lane;
+            const bool has = ai < end;
+            uint32_t m[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) m[k] = 0u;
+            int u = 0;
+            if (has) {
+                u = __ldg(&a.ci[ai]);
+                if (d > 0) {
+                    uint32_t p[W];
+                    load_mask<W>(prev + (size_t)u * W, p);
+#pragma unroll
+                    for (int k = 0; k < W; ++k) m[k] = F[k] & p[k];
+                }
+                discover(u, F);
+            }
+            if (d > 0) {
+                uint32_t anym = 0;
+#pragma unroll
+                for (int k = 0; k < W; ++k) anym |= m[k];
+                unsigned pend = __ballot_sync(kFull, anym != 0u);
+                while (pend) {
+                    const int jj = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    const int uj = __shfl_sync(kFull, u, jj);
+                    const SigT* row = sig() + (size_t)uj * B + lane;
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        uint32_t mk = __shfl_sync(kFull, m[k], jj);
+                        if ((mk >> lane) & 1u) {
+                            SigT x = __ldcg(row + k * 32);
+                            if constexpr (kFloatSig) {
+                                acc[k] += x;
+                            } else {
+                                SigT s2 = acc[k] + x;
+                                ovf |= s2 < x;
+                                acc[k] = s2;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (lane == 0) st_scanned += (unsigned long long)(end - beg);
+        SigT* prow = reinterpret_cast<SigT*>(a.part) + (size_t)g * B + lane;
+#pragma unroll
+        for (int k = 0; k < W; ++k) prow[k * 32] = acc[k];
+        int old = 0;
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            old = atomicAdd(&a.hdone[r], 1);
+        }
+        old = __shfl_sync(kFull, old, 0);
+        if (old != nseg - 1) return;
+        __threadfence();
+        // last segment: sum partial rows in segment order
+        SigT tot[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) tot[k] = 0;
+        for (int q = 0; q < nseg; ++q) {
+            const SigT* pr = reinterpret_cast<const SigT*>(a.part) + (size_t)(sb + q) * B + lane;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                SigT x = __ldcg(pr + k * 32);
+                if constexpr (kFloatSig) {
+                    tot[k] += x;
+                } else {
+                    SigT s2 = tot[k] + x;
+                    ovf |= s2 < x;
+                    tot[k] = s2;
+                }
+            }
+        }
+        if (lane == 0) {
+            int pc = 0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) pc += __popc(F[k]);
+            st_arcs += (unsigned long long)(re - rb) * (unsigned long long)pc;
+            st_reached += (unsigned long long)pc;
+        }
+        if (d > 0) sigma_flush(hv, F, tot);
+    }
+
+    // ---------------- backward ----------------
+    __device__ void bwd_chunk(int e0, int qe, bool skip_arcs) {
+        const int e = e0 + lane;
+        bool valid = e < qe;
+        unsigned qv = valid ? (unsigned)__ldcg(&a.ent[e]) : kHubFlag;
+        bool hubent = (qv & kHubFlag) != 0;
+        int v = (int)(qv & kVertexMask);
+        if (valid && v >= a.n) { set_error(ctl, kErrCorrupt); valid = false; hubent = true; v = 0; }
+        uint32_t F[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) F[k] = 0u;
+        int beg = 0, deg = 0;
+        if (valid && !hubent) {
+            load_mask<W>(a.emask + (size_t)e * W, F);
+            beg = __ldg(&a.rp[v]);
+            deg = skip_arcs ? 0 : __ldg(&a.rp[v + 1]) - beg;
+            st_scanned += (unsigned long long)deg;
+        }
+        const int incl = warp_incl_scan(deg);
+        const int excl = incl - deg;
+        const int total = __shfl_sync(kFull, incl, 31);
+        AccT acc[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] = 0;
+        // Entries are flushed in lane order; entries with no child arcs get acc = 0.
+        int next_flush = 0;  // lanes below this index are flushed
+        auto flush_upto = [&](int upto) {  // flush entries next_flush .. upto-1
+            for (; next_flush < upto; ++next_flush) {
+                const int c = next_flush;
+                const bool cv = __shfl_sync(kFull, (int)(valid && !hubent), c) != 0;
+                if (!cv) continue;
+                uint32_t Fc[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) Fc[k] = __shfl_sync(kFull, F[k], c);
+                delta_flush(__shfl_sync(kFull, v, c), Fc, acc);
+#pragma unroll
+                for (int k = 0; k < W; ++k) acc[k] = 0;
+            }
+        };
+        for (int cb = 0; cb < total; cb += kWarp) {
+            const int ai = cb + lane;
+            const bool has = ai < total;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                int ex = __shfl_sync(kFull, excl, j + step < 32 ? j + step : 31);
+                if (j + step < 32 && ex <= ai) j += step;
+            }
+            const int bj = __shfl_sync(kFull, beg, j);
+            const int exj = __shfl_sync(kFull, excl, j);
+            uint32_t m[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) m[k] = 0u;
+            int w = 0;
+            if (has) {
+                w = __ldg(&a.ci[bj + (ai - exj)]);
+                uint32_t c[W];
+                load_mask<W>(next + (size_t)w * W, c);
+#pragma unroll
+                for (int k = 0; k < W; ++k) m[k] = c[k];
+            }
+            // masks of the owners are needed lane-wise: AND after the shuffle below
+            uint32_t anym = 0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                uint32_t Fj = __shfl_sync(kFull, F[k], j);
+                m[k] &= Fj;
+                anym |= m[k];
+            }
+            unsigned pend = __ballot_sync(kFull, has && anym != 0u);
+            while (pend) {
+                const int jj = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const int wj = __shfl_sync(kFull, w, jj);
+                const int ej = __shfl_sync(kFull, j, jj);
+                if (ej > next_flush) flush_upto(ej);
+                const ThT* row = th() + (size_t)wj * B + lane;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    uint32_t mk = __shfl_sync(kFull, m[k], jj);
+                    if ((mk >> lane) & 1u) acc[k] += (AccT)__ldcg(row + k * 32);
+                }
+            }
+        }
+        flush_upto(32);
+    }
+
+    __device__ void bwd_hub_segment(int g, bool skip_arcs) {
+        const int r = find_hub(a.hubs, hoff_d, hoff_d + nrec_d, g);
+        const int hv = __ldcg(&a.hubs[r].v);
+        const int qpos = __ldcg(&a.hubs[r].qpos);
+        const int nseg = __ldcg(&a.hubs[r].nseg);
+        const int sb = __ldcg(&a.hubs[r].seg_base);
+        if (hv < 0 || hv >= a.n || nseg < 1 || sb < 0 || sb + nseg > a.segcap || qpos < 0 || qpos >= a.ecap) {
+            if (lane == 0) set_error(ctl, kErrCorrupt);
+            return;
+        }
+        const int s = g - sb;
+        const int rb = __ldg(&a.rp[hv]), re = __ldg(&a.rp[hv + 1]);
+        const int beg = rb + s * a.seg;
+        const int end = skip_arcs ? beg : min(re, beg + a.seg);
+        uint32_t F[W];
+        load_mask<W>(a.emask + (size_t)qpos * W, F);
+        AccT acc[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] = 0;
+        for (int cb = beg; cb < end; cb += kWarp) {
+            const int ai = cb + lane;
+            const bool has = ai < end;
+            uint32_t m[W];
+            uint32_t anym = 0;
+            int w = 0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) m[k] = 0u;
+            if (has) {
+                w = __ldg(&a.ci[ai]);
+                uint32_t c[W];
+                load_mask<W>(next + (size_t)w * W, c);
+#pragma unroll
+                for (int k = 0; k < W; ++k) { m[k] = c[k] & F[k]; anym |= m[k]; }
+            }
+            unsigned pend = __ballot_sync(kFull, anym != 0u);
+            while (pend) {
+                const int jj = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const int wj = __shfl_sync(kFull, w, jj);
+                const ThT* row = th() + (size_t)wj * B + lane;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    uint32_t mk = __shfl_sync(kFull, m[k], jj);
+                    if ((mk >> lane) & 1u) acc[k] += (AccT)__ldcg(row + k * 32);
+                }
+            }
+        }
+        if (lane == 0) st_scanned += (unsigned long long)(end - beg);
+        AccT* prow = reinterpret_cast<AccT*>(a.part) + (size_t)g * B + lane;
+#pragma unroll
+        for (int k = 0; k < W; ++k) prow[k * 32] = acc[k];
+        int old = 0;
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            old = atomicAdd(&a.hdone[a.hcap + r], 1);
+        }
+        old = __shfl_sync(kFull, old, 0);
+        if (old != nseg - 1) return;
+        __threadfence();
+        AccT tot[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) tot[k] = 0;
+        for (int q = 0; q < nseg; ++q) {
+            const AccT* pr = reinterpret_cast<const AccT*>(a.part) + (size_t)(sb + q) * B + lane;
+#pragma unroll
+            for (int k = 0; k < W; ++k) tot[k] += __ldcg(pr + k * 32);
+        }
+        delta_flush(hv, F, tot);
+    }
+
+    // Per-block reduction of the level's sigma exponent range, then one
+    // global atomic per source and block.
+    __device__ void flush_exponents(int level) {
+        if constexpr (kFloatSig) {
+            __shared__ int s_max[B], s_min[B];
+            for (int i = threadIdx.x; i < B; i += blockDim.x) { s_max[i] = INT_MIN; s_min[i] = INT_MAX; }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (my_emax[k] >= my_emin[k]) {
+                    atomicMax(&s_max[k * 32 + lane], my_emax[k]);
+                    atomicMin(&s_min[k * 32 + lane], my_emin[k]);
+                }
+                my_emax[k] = INT_MIN;
+                my_emin[k] = INT_MAX;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < B; i += blockDim.x) {
+                if (s_max[i] >= s_min[i]) {
+                    atomicMax(&a.emax[(size_t)level * B + i], s_max[i]);
+                    atomicMin(&a.emin[(size_t)level * B + i], s_min[i]);
+                }
+            }
+        }
+    }
+};
+
+template <int W, typename SigT, typename ThT>
+__global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs a) {
+    using K_t = BatchKernel<W, SigT, ThT>;
+    constexpr int B = K_t::B;
+    constexpr bool kFloatSig = K_t::kFloatSig;
+    K_t K(a);
+    Ctl* ctl = a.ctl;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    const int lane = K.lane;
+    const int n = a.n;
+    int phase = 0;
+    int qsnap = 0;  // level-stack fill at the last barrier
+    int levels_max = 0;
+    int stamp_base = 1;
+    auto sync = [&]() -> bool {
+        bool skip = (a.debug_flags & SP_DEBUG_SKIP_BARRIER) && blockIdx.x == 0 && phase == 1;
+        bool ok = grid_sync(ctl, gridDim.x, a.timeout_ns, phase++, skip, &qsnap);
+        if (tid == 0) ctl->work[(phase + 2) & 3] = 0u;
+        return ok;
+    };
+    // Work loop of one level: hub segments first, then chunks of 32 entries.
+    auto work = [&](int nitems_hub, int qb, int qe, auto&& on_hub, auto&& on_chunk) {
+        const int nchunks = (qe - qb + kWarp - 1) / kWarp;
+        const int total = nitems_hub + nchunks;
+        while (true) {
+            int item = 0;
+            if (lane == 0) item = (int)atomicAdd(&ctl->work[phase & 3], 1u);
+            item = __shfl_sync(kFull, item, 0);
+            if (item >= total) break;
+            if (item < nitems_hub) on_hub(item);
+            else on_chunk(qb + (item - nitems_hub) * kWarp);
+        }
+    };
+
+    for (int i = tid; i < n; i += nthr) a.bc[i] = 0.0;
+    if (!sync()) goto out;
+
+    for (int b0 = 0; b0 < a.nsrc; b0 += B) {
+        const int nb = min(B, a.nsrc - b0);
+        // ---- init: sources of this batch at level 0 ----
+        K.hoff_next = 0;
+        K.stamp_next = stamp_base;
+        K.d = -1;
+        if (tid == 0) {
+            a.hcnt[1] = 0ull;
+            a.eoff[0] = 0;
+            a.hoff[0] = 0;
+        }
+        if constexpr (kFloatSig) {
+            for (int i = tid; i < B; i += nthr) {
+                a.emax[i] = 0;
+                a.emin[i] = 0;
+                a.emax[B + i] = INT_MIN;
+                a.emin[B + i] = INT_MAX;
+            }
+        }
+        if (tid < nb) {
+            const int s = tid;
+            const int x = __ldg(&a.sources[b0 + s]);
+            const uint32_t bit = 1u << (s & 31);
+            atomicOr(&a.seen[(size_t)x * W + (s >> 5)], bit);
+            atomicOr(&a.dense[(size_t)x * W + (s >> 5)], bit);  // ring 0 = F_0
+            K.sig()[(size_t)x * B + s] = (SigT)1;
+            if (atomicMax(&a.ptag[x], stamp_base) < stamp_base) K.push(x, 0);
+        }
+        if (!sync()) goto out;
+
+        // ---- forward ----
+        int qb = 0, qe = qsnap;
+        int hoff_d = 0;
+        int d = 0;
+        while (true) {
+            K.d = d;
+            K.prev = a.dense + (size_t)((d + 3) & 3) * n * W;
+            K.cur = a.dense + (size_t)(d & 3) * n * W;
+            K.next = a.dense + (size_t)((d + 1) & 3) * n * W;
+            K.stamp_next = stamp_base + d + 1;
+            unsigned long long hc = ld_volatile(&a.hcnt[d]);
+            K.hoff_d = hoff_d;
+            K.nrec_d = (int)(hc >> 32);
+            K.nseg_d = (int)(hc & 0xFFFFFFFFull);
+            K.hoff_next = hoff_d + K.nrec_d;
+            if (d + 2 >= a.lcap) { set_error(ctl, kErrCapLevels); }
+            if constexpr (kFloatSig) {
+#pragma unroll
+                for (int k = 0; k < W; ++k)
+                    K.cshift[k] = d > 0 ? centre_shift(ld_volatile(&a.emax[(size_t)(d - 1) * B + k * 32 + lane]),
+                                                       ld_volatile(&a.emin[(size_t)(d - 1) * B + k * 32 + lane]))
+                                        : 0;
+                if (d + 1 < a.lcap)
+                    for (int i = tid; i < B; i += nthr) {
+                        a.emax[(size_t)(d + 1) * B + i] = INT_MIN;
+                        a.emin[(size_t)(d + 1) * B + i] = INT_MAX;
+                    }
+            }
+            if (tid == 0) {
+                a.eoff[d + 1] = qe;
+                a.hoff[d] = hoff_d;
+                if (d + 2 < a.lcap + 2) a.hcnt[d + 2] = 0ull;
+            }
+            // clear dense F_{d-2}
+            if (d >= 2) {
+                const int cb = ld_volatile(&a.eoff[d - 2]), ce = ld_volatile(&a.eoff[d - 1]);
+                uint32_t* clr = a.dense + (size_t)((d + 2) & 3) * n * W;
+                for (int i = cb + tid; i < ce; i += nthr) {
+                    int v = (int)((unsigned)__ldcg(&a.ent[i]) & kVertexMask);
+                    zero_mask<W>(clr + (size_t)v * W);
+                }
+            }
+            work(K.nseg_d, qb, qe, [&](int g) { K.fwd_hub_segment(g); }, [&](int e0) { K.fwd_chunk(e0, qe); });
+            K.flush_exponents(d);
+            if (K.ovf) set_error(ctl, kErrSigmaOverflow);
+            if (!sync()) goto out;
+            const int nq = qsnap;
+            hoff_d = K.hoff_next;
+            if (nq == qe) break;
+            qb = qe;
+            qe = nq;
+            ++d;
+        }
+        const int L = d + 1;
+        levels_max = max(levels_max, L);
+
+        // ---- backward ----
+        for (int dd = L - 1; dd >= 1; --dd) {
+            K.d = dd;
+            K.next = a.dense + (size_t)((dd + 1) & 3) * n * W;  // dense F_{dd+1}
+            const int qbd = ld_volatile(&a.eoff[dd]), qed = ld_volatile(&a.eoff[dd + 1]);
+            unsigned long long hc = ld_volatile(&a.hcnt[dd]);
+            K.hoff_d = ld_volatile(&a.hoff[dd]);
+            K.nrec_d = (int)(hc >> 32);
+            K.nseg_d = (int)(hc & 0xFFFFFFFFull);
+            if constexpr (kFloatSig) {
+#pragma unroll
+                for (int k = 0; k < W; ++k)
+                    K.cshift[k] = centre_shift(ld_volatile(&a.emax[(size_t)dd * B + k * 32 + lane]),
+                                               ld_volatile(&a.emin[(size_t)dd * B + k * 32 + lane]));
+            }
+            // scatter F_dd into its dense ring slot (read by level dd-1), clear F_{dd+2},
+            // and clear seen of this level's vertices
+            {
+                uint32_t* dst = a.dense + (size_t)(dd & 3) * n * W;
+                for (int i = qbd + tid; i < qed; i += nthr) {
+                    int v = (int)((unsigned)__ldcg(&a.ent[i]) & kVertexMask);
+                    uint32_t msk[W];
+                    load_mask<W>(a.emask + (size_t)i * W, msk);
+                    store_mask<W>(dst + (size_t)v * W, msk);
+                    zero_mask<W>(a.seen + (size_t)v * W);
+                }
+                if (dd + 2 <= L - 1) {
+                    const int cb = ld_volatile(&a.eoff[dd + 2]), ce = ld_volatile(&a.eoff[dd + 3]);
+                    uint32_t* clr = a.dense + (size_t)((dd + 2) & 3) * n * W;
+                    for (int i = cb + tid; i < ce; i += nthr) {
+                        int v = (int)((unsigned)__ldcg(&a.ent[i]) & kVertexMask);
+                        zero_mask<W>(clr + (size_t)v * W);
+                    }
+                }
+            }
+            const bool skip = dd == L - 1;
+            work(K.nseg_d, qbd, qed, [&](int g) { K.bwd_hub_segment(g, skip); },
+                 [&](int e0) { K.bwd_chunk(e0, qed, skip); });
+            if (!sync()) goto out;
+        }
+
+        // ---- cleanup: dense levels 0..2, seen of the sources; reset the stack ----
+        for (int j = 0; j < 3 && j < L; ++j) {
+            const int cb = ld_volatile(&a.eoff[j]), ce = ld_volatile(&a.eoff[j + 1]);
+            uint32_t* clr = a.dense + (size_t)(j & 3) * n * W;
+            for (int i = cb + tid; i < ce; i += nthr) {
+                int v = (int)((unsigned)__ldcg(&a.ent[i]) & kVertexMask);
+                zero_mask<W>(clr + (size_t)v * W);
+                if (j == 0) zero_mask<W>(a.seen + (size_t)v * W);
+            }
+        }
+        if (tid == 0) {
+            ctl->qtail = 0;
+            a.hcnt[0] = 0ull;
+        }
+        stamp_base += L + 1;
+        if (!sync()) goto out;
+    }
+
+out:
+    {
+        __shared__ unsigned long long s_st[4];
+        if (threadIdx.x == 0) { s_st[0] = 0; s_st[1] = 0; s_st[2] = 0; s_st[3] = 0; }
+        __syncthreads();
+        atomicAdd(&s_st[0], K.st_arcs);
+        atomicAdd(&s_st[1], K.st_reached);
+        atomicAdd(&s_st[2], K.st_entries);
+        atomicAdd(&s_st[3], K.st_scanned);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicAdd(&ctl->traversed_arcs, s_st[0]);
+            atomicAdd(&ctl->reached, s_st[1]);
+            atomicAdd(&ctl->entries, s_st[2]);
+            atomicAdd(&ctl->scanned_arcs, s_st[3]);
+            atomicMax(&ctl->max_levels, levels_max);
+            int e = ld_volatile(&ctl->err);
+            if (e != 0 && a.err_latch) *(volatile int*)a.err_latch = e;
+        }
+    }
+}
+
+// Host side: workspace layout and launch for one width.
+template <int W>
+sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result);
+
+}  // namespace sp

@@ -1,0 +1,127 @@
+// Host side of the batched form for one width: workspace layout and launch.
+#pragma once
+
+#include <cstring>
+#include <string>
+
+#include "bc_batched.cuh"
+
+namespace sp {
+
+template <int W>
+sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
+    constexpr int B = 32 * W;
+    const Graph* g = L.g;
+    const int64_t n = g->n;
+    cudaStream_t st = L.stream;
+    const int t_hub = 512, seg = 1024;
+
+    const void* fn;
+    if (L.sigma_float)
+        fn = L.theta_f32 ? (const void*)&batched_kernel<W, double, float> : (const void*)&batched_kernel<W, double, double>;
+    else
+        fn = L.theta_f32 ? (const void*)&batched_kernel<W, unsigned long long, float>
+                         : (const void*)&batched_kernel<W, unsigned long long, double>;
+    int per_sm = 0;
+    SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, 0));
+    if (per_sm < 1) return fail(SP_ERR_CUDA, "batched kernel cannot be resident");
+    int grid = per_sm * device_sm_count(g->device);
+    if (L.max_ctas > 0 && L.max_ctas < grid) grid = L.max_ctas;
+
+    int64_t lcap = std::min<int64_t>(n + 2, L.level_cap > 0 ? L.level_cap : 16384);
+    int64_t ecap_max = n * std::min<int64_t>(B, lcap);
+    int64_t ecap = L.entry_cap > 0 ? L.entry_cap : std::max<int64_t>(8 * n, 1 << 16);
+    ecap = std::max<int64_t>(1, std::min(ecap, ecap_max));
+    int64_t hcap = L.hub_cap > 0 ? L.hub_cap : (g->nnz / t_hub) * 8 + 1024;
+    int64_t segcap = g->nnz / seg + g->nnz / t_hub + 2;
+    if (hcap > INT32_MAX || segcap > INT32_MAX || ecap > INT32_MAX) return fail(SP_ERR_TOO_LARGE, "batched workspace");
+    const size_t th_size = L.theta_f32 ? 4 : 8;
+
+    size_t bytes = 0;
+    auto take = [&](size_t b) { size_t o = bytes; bytes += (b + 255) & ~(size_t)255; return o; };
+    size_t o_ctl = take(sizeof(Ctl));
+    size_t o_dense = take(sizeof(uint32_t) * 4 * (size_t)n * W);
+    size_t o_seen = take(sizeof(uint32_t) * (size_t)n * W);
+    size_t o_ptag = take(sizeof(int32_t) * (size_t)n);
+    size_t zero_end = bytes;  // everything above starts at zero
+    size_t o_sig = take(8 * (size_t)n * B);
+    size_t o_th = take(th_size * (size_t)n * B);
+    size_t o_ent = take(sizeof(int32_t) * (size_t)ecap);
+    size_t o_emask = take(sizeof(uint32_t) * (size_t)ecap * W);
+    size_t o_eoff = take(sizeof(int32_t) * (size_t)(lcap + 2));
+    size_t o_hoff = take(sizeof(int32_t) * (size_t)(lcap + 2));
+    size_t o_hcnt = take(sizeof(unsigned long long) * (size_t)(lcap + 2));
+    size_t o_hubs = take(sizeof(HubRec) * (size_t)hcap);
+    size_t o_hdone = take(sizeof(int32_t) * 2 * (size_t)hcap);
+    size_t o_part = take(8 * (size_t)segcap * B);
+    size_t o_emax = take(sizeof(int32_t) * (size_t)lcap * B);
+    size_t o_emin = take(sizeof(int32_t) * (size_t)lcap * B);
+
+    char* ws = nullptr;
+    if (cudaMallocAsync((void**)&ws, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SP_ERR_OOM, "workspace allocation (batched form, " + std::to_string(bytes >> 20) + " MiB)");
+    }
+    cudaError_t ce = cudaMemsetAsync(ws, 0, zero_end, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(ws + o_hcnt, 0, sizeof(unsigned long long) * (size_t)(lcap + 2), st);
+    if (ce != cudaSuccess) { cudaFreeAsync(ws, st); return cuda_fail(ce, "cudaMemsetAsync"); }
+
+    BatchArgs a{};
+    a.rp = g->d_rp;
+    a.ci = g->d_ci;
+    a.n = (int32_t)n;
+    a.sources = L.d_sources;
+    a.nsrc = L.nsrc;
+    a.bc = L.d_bc;
+    a.dense = reinterpret_cast<uint32_t*>(ws + o_dense);
+    a.seen = reinterpret_cast<uint32_t*>(ws + o_seen);
+    a.ptag = reinterpret_cast<int32_t*>(ws + o_ptag);
+    a.sig = ws + o_sig;
+    a.th = ws + o_th;
+    a.ent = reinterpret_cast<int32_t*>(ws + o_ent);
+    a.emask = reinterpret_cast<uint32_t*>(ws + o_emask);
+    a.ecap = ecap;
+    a.eoff = reinterpret_cast<int32_t*>(ws + o_eoff);
+    a.hubs = reinterpret_cast<HubRec*>(ws + o_hubs);
+    a.hcap = (int32_t)hcap;
+    a.hoff = reinterpret_cast<int32_t*>(ws + o_hoff);
+    a.hcnt = reinterpret_cast<unsigned long long*>(ws + o_hcnt);
+    a.hdone = reinterpret_cast<int32_t*>(ws + o_hdone);
+    a.part = ws + o_part;
+    a.segcap = (int32_t)segcap;
+    a.emax = reinterpret_cast<int32_t*>(ws + o_emax);
+    a.emin = reinterpret_cast<int32_t*>(ws + o_emin);
+    a.lcap = (int32_t)lcap;
+    a.ctl = reinterpret_cast<Ctl*>(ws + o_ctl);
+    a.err_latch = nullptr;
+    a.debug_flags = L.debug_flags;
+    a.timeout_ns = L.timeout_ns;
+    a.t_hub = t_hub;
+    a.seg = seg;
+
+    void* args[] = {&a};
+    ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBatchThreads), args, 0, st);
+    if (ce != cudaSuccess) {
+        cudaFreeAsync(ws, st);
+        return cuda_fail(ce, "cudaLaunchCooperativeKernel (batched form)");
+    }
+    static thread_local Ctl h;
+    std::memset(&h, 0, sizeof(h));
+    ce = cudaMemcpyAsync(&h, ws + o_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(ws, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "reading the batched-form result");
+    result->err = h.err;
+    result->levels = h.max_levels;
+    result->traversed_arcs = h.traversed_arcs;
+    result->reached = h.reached;
+    result->entries = h.entries;
+    result->scanned_arcs = h.scanned_arcs;
+    if (h.err == SP_ERR_TIMEOUT) result->diag = barrier_diagnostic(h, grid);
+    result->ecap = ecap;
+    result->hcap = hcap;
+    result->lcap = lcap;
+    return SP_OK;
+}
+
+}  // namespace sp

@@ -1,0 +1,6 @@
+// Batched-form kernels for 64 sources per batch.
+#include "bc_batched_launch.cuh"
+
+namespace sp {
+template sp_status launch_batched_w<2>(const BatchedLaunch& L, LaunchResult* result);
+}  // namespace sp

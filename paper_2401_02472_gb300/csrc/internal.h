@@ -1,0 +1,113 @@
+// Host-side declarations shared by the starbc translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "starbc.h"
+
+namespace sp {
+
+struct Ctl;
+struct HubRec;
+
+struct Graph {
+    int device = 0;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t* d_rp = nullptr;  // [n+1]
+    int32_t* d_ci = nullptr;  // [max(nnz,1)]
+    sp_graph_info info{};
+    int* err_latch_host = nullptr;  // mapped pinned int: device-side errors of asynchronous calls
+    int* err_latch_dev = nullptr;
+    std::mutex mu;
+    bool sigma_float = false;  // path counts of this graph overflowed 64-bit integers before
+    std::map<int, int> tuned_batch;  // precision -> batch width chosen by the autotuner
+};
+
+// Thread-local error text.
+void set_last_error(const std::string& s);
+sp_status fail(sp_status st, const std::string& what);
+sp_status cuda_fail(cudaError_t e, const char* what);
+
+#define SP_CUDA(call)                                           \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return ::sp::cuda_fail(e_, #call); \
+    } while (0)
+
+// Kernel tiers (entries of the level stack by degree).
+struct Tiers {
+    int t_thread;  // degree <= t_thread: one lane walks the row
+    int t_hub;     // degree > t_hub: the row is split into segments of `seg` arcs
+    int seg;
+};
+
+enum class PlainMode : int { BC = 0, BFS = 1, SIGMA = 2 };
+
+struct PlainLaunch {
+    const Graph* g;
+    const int32_t* d_sources;
+    int32_t nsrc;
+    double* d_bc;           // BC mode
+    int32_t* d_dist;        // BFS mode: [nsrc][n]
+    double* d_mant;         // SIGMA mode
+    long long* d_exp;       // SIGMA mode
+    PlainMode mode;
+    bool sigma_float;       // double path counts with per-level rescaling
+    bool theta_f32;         // 1/sigma-scaled dependencies stored in FP32
+    int max_ctas;
+    uint64_t timeout_ns;
+    int debug_flags;
+    cudaStream_t stream;
+};
+
+struct LaunchResult {
+    int err = 0;             // device error code (0, sp_status or internal)
+    int levels = 0;
+    unsigned long long traversed_arcs = 0, reached = 0, entries = 0, scanned_arcs = 0;
+    int64_t ecap = 0, hcap = 0, lcap = 0;  // capacities used (batched form)
+    std::string diag;                      // barrier state when a wait timed out
+};
+
+// Summary of where the blocks of a launch stood when a barrier wait timed out.
+std::string barrier_diagnostic(const Ctl& h, int grid);
+
+// Run the plain form on L.stream and wait for it; `result` receives the
+// device-side error code and statistics.
+sp_status run_plain(const PlainLaunch& L, LaunchResult* result);
+
+struct BatchedLaunch {
+    const Graph* g;
+    const int32_t* d_sources;
+    int32_t nsrc;
+    double* d_bc;
+    int width;              // sources per batch: 32, 64, 128 or 256
+    bool sigma_float;
+    bool theta_f32;
+    int max_ctas;
+    uint64_t timeout_ns;
+    int debug_flags;
+    cudaStream_t stream;
+    int64_t entry_cap;      // level-stack capacity (entries); 0 = default estimate
+    int64_t hub_cap;        // hub records; 0 = default estimate
+    int64_t level_cap;      // BFS levels per batch; 0 = default (16384)
+};
+
+sp_status run_batched(const BatchedLaunch& L, LaunchResult* result);
+template <int W>
+sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result);
+
+// Graph validation kernels.
+sp_status validate_graph(Graph* g, uint32_t flags, cudaStream_t stream, std::string* detail);
+
+int device_sm_count(int device);
+int default_batch_width(int32_t nsrc);
+size_t batched_workspace_bytes(const Graph* g, int width, bool theta_f32);
+
+}  // namespace sp

@@ -1,0 +1,270 @@
+"""CUDA path against the CPU oracle, through the C ABI.
+
+Levels must match bit for bit; path counts exactly while below 2^53; BC
+within rtol 1e-9 (FP64 dependencies) or 1e-4 (FP32 dependencies) per vertex,
+|gpu - oracle| <= rtol * max(|oracle|, 1), and exactly 0 where the oracle has
+an exact 0.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2401_02472_gb300 as sp
+
+pytestmark = pytest.mark.gpu
+
+RTOL = {sp.SP_FP64: 1e-9, sp.SP_FP32_DELTA: 1e-4}
+DEV = "cuda:0"
+
+
+def assert_bc_close(got, want, rtol, what=""):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    assert got.shape == want.shape
+    assert np.all(np.isfinite(got)), what
+    err = np.abs(got - want)
+    bound = rtol * np.maximum(np.abs(want), 1.0)
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, f"{what}: {bad.size} vertices off, first {bad[:5]} got {got[bad[:5]]} want {want[bad[:5]]}"
+    assert np.all(got[want == 0.0] == 0.0), f"{what}: nonzero where the oracle has exact 0"
+
+
+def device_graph(g, flags=0):
+    return sp.Graph(g.row_ptr, g.col_idx, flags=flags)
+
+
+def gpu_bc(G, sources, precision=sp.SP_FP64, form=sp.SP_FORM_AUTO, batch=0, device_out=True, **kw):
+    src = torch.as_tensor(np.asarray(sources, np.int32), device=DEV)
+    out = torch.empty(G.n, dtype=torch.float64, device=DEV) if device_out else np.empty(G.n, np.float64)
+    st = sp.sp_bc_ex(G.handle, src, out, sp.make_opts(precision=precision, form=form, batch=batch, **kw))
+    torch.cuda.synchronize()
+    return (out.cpu().numpy() if device_out else out), st
+
+
+# ---------------------------------------------------------------------------
+GRAPHS = {
+    "er2000": lambda: gen.er(2000, 10000, 1),
+    "rmat12": lambda: gen.rmat(12, 16, 2),
+    "knn5000": lambda: gen.knn2d(5000, 4, 3),
+    "grid30x41": lambda: gen.grid(30, 41),
+    "path300": lambda: gen.path(300),
+    "mixed": lambda: gen.disjoint_union(gen.star(40), gen.cycle(9), gen.from_edges(5, []), gen.path(17),
+                                        gen.complete(6)),
+}
+_cache = {}
+
+
+def graph(name):
+    if name not in _cache:
+        g = GRAPHS[name]()
+        _cache[name] = (g, device_graph(g))
+    return _cache[name]
+
+
+def hub_graph():
+    """A graph with rows far above both hub thresholds (segments in both forms)."""
+    if "hub" not in _cache:
+        base = gen.rmat(13, 8, 5)
+        n = base.n
+        extra = [(0, v) for v in range(1, n, 1)] + [(1, v) for v in range(2, n, 2)]
+        rp, ci = base.row_ptr, base.col_idx
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        edges = np.concatenate([np.stack([rows, ci], 1), np.asarray(extra)], 0)
+        g = gen.from_edges(n, edges, "hub")
+        _cache["hub"] = (g, device_graph(g))
+    return _cache["hub"]
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_bfs_levels_bit_exact(name):
+    g, G = graph(name)
+    srcs = np.unique(np.array([0, g.n // 3, g.n - 1, g.n // 2], np.int32))
+    dist = torch.empty((len(srcs), g.n), dtype=torch.int32, device=DEV)
+    sp.sp_bfs(G.handle, torch.as_tensor(srcs, device=DEV), dist)
+    got = dist.cpu().numpy()
+    for i, s in enumerate(srcs):
+        assert np.array_equal(got[i], oracle.bfs(g, int(s))), (name, s)
+
+
+def test_bfs_host_buffers_and_hubs():
+    g, G = hub_graph()
+    srcs = np.array([0, 1, 77, 4095], np.int32)
+    dist = np.empty((4, g.n), np.int32)
+    sp.sp_bfs(G.handle, srcs, dist)
+    for i, s in enumerate(srcs):
+        assert np.array_equal(dist[i], oracle.bfs(g, int(s)))
+
+
+@pytest.mark.parametrize("name", ["er2000", "rmat12", "grid30x41", "mixed"])
+def test_sigma_exact(name):
+    g, G = graph(name)
+    for s in [0, g.n - 1]:
+        mant = np.empty(g.n, np.float64)
+        e2 = np.empty(g.n, np.int64)
+        sp.sp_sigma(G.handle, s, mant, e2)
+        om, oe, od, _ = oracle.sigma(g, s)
+        assert np.array_equal(mant, om) and np.array_equal(e2, oe), (name, s)
+
+
+def test_sigma_beyond_double_range():
+    # Path counts up to C(1198, 599) ~ 2^1193: the per-level rescaled FP64 path.
+    g = gen.grid(600, 600)
+    G = device_graph(g)
+    mant = np.empty(g.n, np.float64)
+    e2 = np.empty(g.n, np.int64)
+    sp.sp_sigma(G.handle, 0, mant, e2)
+    for (i, j) in [(599, 599), (0, 599), (300, 299), (599, 1), (450, 512), (10, 10)]:
+        v = i * 600 + j
+        want = math.comb(i + j, i)
+        shift = max(want.bit_length() - 64, 0)
+        log2_want = shift + math.log2(want >> shift)
+        assert abs(math.log2(mant[v]) + int(e2[v]) - log2_want) <= 1e-12 * max(1.0, log2_want)
+    om, oe, _, _ = oracle.sigma(g, 0)
+    lg = np.log2(mant) + e2
+    lo = np.log2(om) + oe
+    assert np.max(np.abs(lg - lo) / np.maximum(lo, 1)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_bc_plain(name, precision):
+    g, G = graph(name)
+    srcs = gen.sources(g, min(12, int((g.degrees() > 0).sum())), 7)
+    got, st = gpu_bc(G, srcs, precision, sp.SP_FORM_PLAIN)
+    want, ost = oracle.bc(g, srcs)
+    assert_bc_close(got, want, RTOL[precision], f"{name} plain")
+    assert st["traversed_arcs"] == int(ost["arcs"].sum())
+    assert st["max_levels"] == int(ost["levels"].max())
+
+
+@pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
+@pytest.mark.parametrize("batch", [32, 64, 128, 256])
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_bc_batched(name, batch, precision):
+    g, G = graph(name)
+    k = min(batch + 37, int((g.degrees() > 0).sum()))  # a ragged last batch
+    srcs = gen.sources(g, k, 11)
+    got, st = gpu_bc(G, srcs, precision, sp.SP_FORM_BATCHED, batch)
+    want, ost = oracle.bc(g, srcs)
+    assert_bc_close(got, want, RTOL[precision], f"{name} B={batch}")
+    assert st["traversed_arcs"] == int(ost["arcs"].sum())
+    assert st["reached"] == int(ost["reached"].sum())
+    assert st["max_levels"] == int(ost["levels"].max())
+
+
+def test_er2000_all_sources_both_forms():
+    g, G = graph("er2000")
+    srcs = np.arange(g.n, dtype=np.int32)
+    want, _ = oracle.bc(g, srcs)
+    for form, batch in [(sp.SP_FORM_PLAIN, 0), (sp.SP_FORM_BATCHED, 64)]:
+        got, _ = gpu_bc(G, srcs, sp.SP_FP64, form, batch)
+        assert_bc_close(got, want, 1e-9, f"er2000 all sources form={form}")
+    # the invariant: sum of BC = sum over reached ordered pairs of (d - 1)
+    from tests import bruteforce as bf
+
+    assert abs(got.sum() - bf.pair_distance_excess(g, srcs)) <= 1e-9 * got.sum()
+
+
+@pytest.mark.parametrize("form", [sp.SP_FORM_PLAIN, sp.SP_FORM_BATCHED])
+@pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
+def test_hubs_split_into_segments(form, precision):
+    g, G = hub_graph()
+    srcs = np.array([0, 1, 2, 3, 4095, 17, 0, 1000] * 5, np.int32)
+    got, _ = gpu_bc(G, srcs, precision, form, 32)
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(got, want, RTOL[precision], "hub graph")
+
+
+# ---------------------------------------------------------------------------
+def test_edge_cases():
+    g, G = graph("mixed")
+    z, _ = gpu_bc(G, [], sp.SP_FP64)
+    assert np.array_equal(z, np.zeros(g.n))
+    iso = [int(v) for v in np.nonzero(g.degrees() == 0)[0][:3]]
+    z, _ = gpu_bc(G, iso * 20, sp.SP_FP64, sp.SP_FORM_BATCHED, 32)
+    assert np.array_equal(z, np.zeros(g.n))
+    dup = [0, 0, 0, 41, 41, 50] * 7
+    for form in (sp.SP_FORM_PLAIN, sp.SP_FORM_BATCHED):
+        got, _ = gpu_bc(G, dup, sp.SP_FP64, form, 32)
+        want, _ = oracle.bc(g, dup)
+        assert_bc_close(got, want, 1e-9, "duplicates")
+    one = gen.from_edges(1, [])
+    G1 = device_graph(one)
+    got, _ = gpu_bc(G1, [0, 0], sp.SP_FP64)
+    assert np.array_equal(got, np.zeros(1))
+    two = gen.path(2)
+    G2 = device_graph(two)
+    got, _ = gpu_bc(G2, [0, 1] * 20, sp.SP_FP64, sp.SP_FORM_BATCHED, 32)
+    assert np.array_equal(got, np.zeros(2))
+
+
+def test_host_output_buffer_matches_device():
+    g, G = graph("rmat12")
+    srcs = gen.sources(g, 50, 3)
+    a, _ = gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_BATCHED, 64, device_out=True)
+    b, _ = gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_BATCHED, 64, device_out=False)
+    assert np.array_equal(a, b)
+    hb = np.empty(g.n, np.float64)
+    sp.sp_bc(G.handle, srcs, hb)  # host sources, host output
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(hb, want, 1e-9)
+
+
+@pytest.mark.parametrize("form,batch", [(sp.SP_FORM_PLAIN, 0), (sp.SP_FORM_BATCHED, 64), (sp.SP_FORM_BATCHED, 128)])
+def test_run_to_run_bit_identical(form, batch):
+    g, G = hub_graph()
+    srcs = gen.sources(g, 150, 9)
+    a, _ = gpu_bc(G, srcs, sp.SP_FP32_DELTA, form, batch)
+    for _ in range(3):
+        b, _ = gpu_bc(G, srcs, sp.SP_FP32_DELTA, form, batch)
+        assert np.array_equal(a, b)
+
+
+def test_linearity_over_calls():
+    g, G = graph("knn5000")
+    s1, s2 = gen.sources(g, 40, 1), gen.sources(g, 70, 2)
+    a, _ = gpu_bc(G, s1, sp.SP_FP64, sp.SP_FORM_BATCHED, 32)
+    b, _ = gpu_bc(G, s2, sp.SP_FP64, sp.SP_FORM_BATCHED, 32)
+    c, _ = gpu_bc(G, np.concatenate([s1, s2]), sp.SP_FP64, sp.SP_FORM_BATCHED, 32)
+    assert_bc_close(c, a + b, 1e-12)
+
+
+def test_bad_graphs_are_rejected():
+    with pytest.raises(sp.StarbcError) as e:
+        sp.sp_graph_create(np.array([0, 2, 1, 3], np.int32), np.array([1, 2, 0], np.int32))
+    assert e.value.status == sp.SP_ERR_BAD_GRAPH
+    with pytest.raises(sp.StarbcError) as e:
+        sp.sp_graph_create(np.array([0, 1, 2], np.int32), np.array([1, 5], np.int32))
+    assert e.value.status == sp.SP_ERR_BAD_GRAPH
+    with pytest.raises(sp.StarbcError) as e:
+        sp.sp_graph_create(np.array([0, 1, 1], np.int32), np.array([1], np.int32), flags=sp.SP_GRAPH_CHECK_SYMMETRIC)
+    assert e.value.status == sp.SP_ERR_BAD_GRAPH
+    g = gen.rmat(10, 8, 1)
+    G = device_graph(g, sp.SP_GRAPH_CHECK_SYMMETRIC)
+    assert G.info["symmetric"] == 1 and G.info["sorted_rows"] == 1
+    assert G.info["max_degree"] == int(g.degrees().max())
+    assert G.info["isolated"] == int((g.degrees() == 0).sum())
+    _, G = graph("er2000")
+    with pytest.raises(sp.StarbcError) as e:
+        gpu_bc(G, [0, 2000])
+    assert e.value.status == sp.SP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("form", [sp.SP_FORM_PLAIN, sp.SP_FORM_BATCHED])
+def test_barrier_timeout_returns_status(form):
+    # One block skips a barrier on purpose; the others give up after 50 ms and
+    # the launch ends with SP_ERR_TIMEOUT instead of hanging.
+    g, G = graph("er2000")
+    with pytest.raises(sp.StarbcError) as e:
+        gpu_bc(G, list(range(40)), sp.SP_FP64, form, 32, barrier_timeout_ns=50_000_000,
+               debug_flags=sp.SP_DEBUG_SKIP_BARRIER)
+    assert e.value.status == sp.SP_ERR_TIMEOUT
+    got, _ = gpu_bc(G, list(range(40)), sp.SP_FP64, form, 32)  # the context is still usable
+    want, _ = oracle.bc(g, list(range(40)))
+    assert_bc_close(got, want, 1e-9)
