@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Betweenness-centrality throughput on GB300, one JSON line on stdout.
+
+A step is one pass of the whole hot path over one synthetic input: create the
+resident graph from a device CSR (copy + validation on the GPU), run BC over
+the workload's source set (batched persistent kernel, autotuned width), and
+destroy the graph.  The metric is traversed edges per second,
+GTEPS = sum over sources s of A_s / step time, A_s = sum of degrees of the
+vertices reached from s (forward + backward both counted once per arc).
+
+Default workload: RMAT scale 22 (4,194,304 vertices, edge factor 16,
+a,b,c,d = 0.57,0.19,0.19,0.05, symmetrised, deduplicated, seeded relabelling),
+1,024 seeded sources among vertices of degree >= 1, FP32 dependencies,
+FP64 BC.  Inputs (512 MB CSR + GBs of state) are far larger than the 129 MB L2.
+
+  python bench.py [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Under torchrun every rank runs its own source set on its own GPU (sources
+are independent; no collective on the data path) and rank 0 prints the
+aggregate: scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+WORKLOADS = {
+    # name: graph, sources, source seed, precision, form
+    "rmat22_1024src_batched": dict(graph="rmat22", nsrc=1024, seed=14, precision="fp32_delta", form="batched",
+                                   desc="RMAT scale 22, edge factor 16, 1,024 sources, autotuned batches"),
+    "rmat20_64src_batched": dict(graph="rmat20", nsrc=64, seed=12, precision="fp32_delta", form="batched",
+                                 desc="RMAT scale 20, edge factor 16, 64 sources"),
+    "knn4_1m_256src_batched": dict(graph="knn4_1m", nsrc=256, seed=13, precision="fp32_delta", form="batched",
+                                   desc="2-D 4-NN graph of 10^6 uniform points, 256 sources"),
+    "er2000_all_plain": dict(graph="er2000", nsrc=2000, seed=None, precision="fp64", form="plain",
+                             desc="Erdos-Renyi n=2,000 m=10,000, all 2,000 sources"),
+}
+DEFAULT_WORKLOAD = "rmat22_1024src_batched"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload_inputs(name, rank=0):
+    w = WORKLOADS[name]
+    g = gen.workload_graph(w["graph"])
+    if w["seed"] is None:
+        srcs = np.arange(min(w["nsrc"], g.n), dtype=np.int32)
+    else:
+        srcs = gen.sources(g, w["nsrc"], w["seed"] + 1000 * rank)
+    return w, g, srcs
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(st: dict, n: int, form: str, theta_bytes: int, width: int) -> int:
+    """HBM bytes the method must move for one launch, from the launch's own counts.
+
+    adjacency   4 B per scanned arc (forward + backward) + row_ptr pair per entry and pass
+    masks       batched: W words per entry, read in the forward, stored, read again backward
+    DAG state   per (arc, source) on a shortest-path DAG: the parent's sigma (8 B) in the
+                forward pull and the child's theta in the backward pull
+    per (v, s)  sigma written and re-read (8 + 8 B), theta written
+    BC          zeroed once (8 B per vertex), read-modify-write per entry (16 B)
+    """
+    words = max(width // 32, 0)
+    b = 4 * st["scanned_arcs"] + 16 * st["entries"]
+    b += 3 * 4 * words * st["entries"]
+    b += st["dag_arcs"] * (8 + theta_bytes)
+    b += st["reached"] * (8 + 8 + theta_bytes)
+    b += 8 * n + 16 * st["entries"]
+    return int(b)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(g, srcs, budget_s=15.0):
+    """The oracle as it stands (single thread) on a bounded prefix of the sources."""
+    import oracle
+
+    t0 = time.perf_counter()
+    _, st = oracle.bc(g, srcs[:1])
+    t1 = time.perf_counter() - t0
+    k = int(max(1, min(len(srcs), budget_s / max(t1, 1e-6))))
+    if k > 1:
+        t0 = time.perf_counter()
+        _, st = oracle.bc(g, srcs[:k])
+        t1 = time.perf_counter() - t0
+    arcs = int(st["arcs"].sum())
+    return {"value": arcs / t1 / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"first {k} of {len(srcs)} sources, {arcs} traversed arcs, {t1:.2f} s"}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle, on a bounded sample of the workload per step."""
+    w, g, srcs = workload_inputs(args.workload, rank)
+    if rank != 0:
+        return
+    import oracle
+
+    per_step = max(1, args.ref_sources)
+    for i in range(args.warmup):
+        oracle.bc(g, srcs[i % len(srcs):i % len(srcs) + 1])
+    times, arcs = [], 0
+    for i in range(args.steps):
+        s = srcs[(i * per_step) % len(srcs):(i * per_step) % len(srcs) + per_step]
+        t0 = time.perf_counter()
+        _, st = oracle.bc(g, s)
+        times.append(time.perf_counter() - t0)
+        arcs += int(st["arcs"].sum())
+    tot = sum(times)
+    value = arcs / tot / 1e9
+    line = {
+        "impl": "reference", "metric": "BC GTEPS (fwd+bwd)", "value": value, "unit": "GTEPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "sources_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} source(s) per step of {args.workload}"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    import paper_2401_02472_gb300 as sp
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    w, g, srcs = workload_inputs(args.workload, rank)
+    prec = sp.SP_FP32_DELTA if w["precision"] == "fp32_delta" else sp.SP_FP64
+    form = sp.SP_FORM_BATCHED if w["form"] == "batched" else sp.SP_FORM_PLAIN
+    opts = sp.make_opts(precision=prec, form=form, batch=args.batch)
+    theta_bytes = 4 if prec == sp.SP_FP32_DELTA else 8
+
+    d_rp = torch.as_tensor(g.row_ptr, device=dev)
+    d_ci = torch.as_tensor(g.col_idx, device=dev)
+    d_src = torch.as_tensor(srcs, device=dev)
+    d_bc = torch.empty(g.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(rp, ci, s, out):
+        G = sp.sp_graph_create(rp, ci, n=g.n, nnz=g.nnz)
+        try:
+            st = sp.sp_bc_ex(G, s, out, opts)
+        finally:
+            sp.sp_graph_destroy(G)
+        return st
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(d_rp, d_ci, d_src, d_bc)
+    torch.cuda.synchronize()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    torch.cuda.synchronize()
+    barrier()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        stats.append(step(d_rp, d_ci, d_src, d_bc))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+
+    # end to end through the public API with host buffers (pinned)
+    h_rp = torch.as_tensor(g.row_ptr).pin_memory()
+    h_ci = torch.as_tensor(g.col_idx).pin_memory()
+    h_src = torch.as_tensor(srcs).pin_memory()
+    h_bc = torch.empty(g.n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st_e = step(h_rp, h_ci, h_src, h_bc)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    arcs = stats[-1]["traversed_arcs"]
+    gteps_rank = arcs / (total_ms / args.steps / 1e3) / 1e9
+    e2e_rank = st_e["traversed_arcs"] / e2e_s / 1e9
+    # aggregate: units over all ranks / max time over ranks
+    if dist is not None:
+        t = torch.tensor([total_ms, float(arcs), e2e_s, float(st_e["traversed_arcs"])], dtype=torch.float64,
+                         device=dev)
+        allt = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(allt, t)
+        allt = torch.stack(allt).cpu().numpy()
+        total_ms_max = allt[:, 0].max()
+        value = allt[:, 1].sum() / (total_ms_max / args.steps / 1e3) / 1e9
+        e2e_value = allt[:, 3].sum() / allt[:, 2].max() / 1e9
+    else:
+        total_ms_max = total_ms
+        value = gteps_rank
+        e2e_value = e2e_rank
+    if rank != 0:
+        return
+
+    s = stats[-1]
+    peak, peak_kind = load_peaks()
+    kernel_ms = s["kernel_ms"]
+    alg = algorithmic_bytes(s, g.n, w["form"], theta_bytes, s["batch"] if s["form"] == sp.SP_FORM_BATCHED else 0)
+    achieved = alg / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0
+    launches_per_step = s["launches"] + 2  # + graph validation (row_ptr, rows)
+    base = cpu_baseline(g, srcs, args.cpu_budget) if not args.no_cpu_baseline else None
+    line = {
+        "metric": "BC GTEPS (fwd+bwd)",
+        "value": value,
+        "unit": "GTEPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64-sigma/f32-delta/f64-bc" if prec == sp.SP_FP32_DELTA else "u64-sigma/f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "n": g.n, "arcs": g.nnz,
+                   "sources": int(len(srcs)), "batch": s["batch"], "form": w["form"], "max_levels": s["max_levels"],
+                   "l2": "inputs larger than L2 (no flush)"},
+        "e2e": {"value": e2e_value, "unit": "GTEPS",
+                "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col_idx.nbytes + srcs.nbytes),
+                "d2h_bytes_per_step": int(g.n * 8)},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": args.traffic,
+                     "peak_kind": peak_kind, "kernel_ms": kernel_ms, "algorithmic_bytes": alg},
+        "cpu_baseline": base,
+        "clocks": clk,
+        "detail": {"traversed_arcs_per_step": arcs, "dag_arcs": s["dag_arcs"], "entries": s["entries"],
+                   "scanned_arcs": s["scanned_arcs"], "reached": s["reached"], "step_ms": step_ms,
+                   "wall_s": t_wall, "tuned_batch": s["batch"], "promoted": s["promoted"],
+                   "sigma_float": s["sigma_float"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="fixed batch width (0 = autotuned)")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sources", type=int, default=1, help="reference arm: oracle sources per step")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("note: fewer than 3 warm-up steps")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group(backend)
+        dist = tdist
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

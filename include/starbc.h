@@ -130,13 +130,16 @@ typedef struct {
     int64_t reached;        /* sum over sources of |R_s| (including s) */
     int64_t entries;        /* (vertex, level) work entries over all batches (batched form) */
     int64_t scanned_arcs;   /* adjacency entries read, forward + backward */
+    int64_t dag_arcs;       /* (arc, source) pairs with the arc on a shortest path from the source */
+    double kernel_ms;       /* device time of the BC kernel launches (CUDA events), summed */
     int32_t max_levels;     /* max over sources of L = 1 + eccentricity of s */
-    int32_t batches;        /* launches' batches (plain form: one per source) */
+    int32_t batches;        /* batches (plain form: one per source) */
     int32_t batch;          /* sources per batch used (1 for the plain form) */
     int32_t form;           /* SP_FORM_PLAIN or SP_FORM_BATCHED */
-    int32_t promoted;       /* FP32_DELTA batches rerun with FP64 delta (range) */
-    int32_t sigma_float;    /* batches whose path counts needed FP64 with rescaling */
-    int32_t pad[2];
+    int32_t promoted;       /* 1 when FP32 dependencies left the FP32 range and the call reran with FP64 */
+    int32_t sigma_float;    /* 1 when path counts needed FP64 with per-level rescaling (above 2^64) */
+    int32_t launches;       /* kernel launches of the call, including reruns and autotuning trials */
+    int32_t tuned;          /* 1 when this call ran the batch-width autotuner */
 } sp_bc_stats;
 
 SP_API void sp_bc_opts_default(sp_bc_opts* o);

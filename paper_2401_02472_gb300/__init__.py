@@ -36,9 +36,10 @@ class sp_bc_opts(ctypes.Structure):
 
 class sp_bc_stats(ctypes.Structure):
     _fields_ = [("traversed_arcs", ctypes.c_int64), ("reached", ctypes.c_int64), ("entries", ctypes.c_int64),
-                ("scanned_arcs", ctypes.c_int64), ("max_levels", ctypes.c_int32), ("batches", ctypes.c_int32),
-                ("batch", ctypes.c_int32), ("form", ctypes.c_int32), ("promoted", ctypes.c_int32),
-                ("sigma_float", ctypes.c_int32), ("pad", ctypes.c_int32 * 2)]
+                ("scanned_arcs", ctypes.c_int64), ("dag_arcs", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
+                ("max_levels", ctypes.c_int32), ("batches", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("form", ctypes.c_int32), ("promoted", ctypes.c_int32), ("sigma_float", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("tuned", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}

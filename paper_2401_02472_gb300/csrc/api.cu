@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -146,8 +148,6 @@ static uint64_t timeout_of(const sp_bc_opts& o) {
     return o.barrier_timeout_ns > 0 ? (uint64_t)o.barrier_timeout_ns : bfs_timeout_ns();
 }
 
-int default_batch_width(int32_t nsrc) { return nsrc > 32 ? 64 : 32; }
-
 // Device bytes one batched launch of this width allocates (default capacities).
 size_t batched_workspace_bytes(const Graph* g, int width, bool theta_f32) {
     const size_t n = (size_t)g->n, W = (size_t)width / 32, B = (size_t)width;
@@ -158,17 +158,50 @@ size_t batched_workspace_bytes(const Graph* g, int width, bool theta_f32) {
            hcap * 24 + segcap * B * 8 + 2 * lcap * B * 4 + 3 * (lcap + 2) * 8 + (1 << 20);
 }
 
-// Batch width when the caller leaves it open: the autotuned value for the
-// graph if there is one, else by source count.
-static int choose_width(Graph* g, const sp_bc_opts& o, int32_t nsrc) {
-    if (o.batch > 0) return o.batch;
-    {
-        std::lock_guard<std::mutex> lk(g->mu);
-        auto it = g->tuned_batch.find(o.precision);
-        if (it != g->tuned_batch.end()) return it->second;
-    }
-    return default_batch_width(nsrc);
+// Autotuned batch widths, keyed by graph signature (n, nnz, max degree) and
+// precision, so that a graph re-created from the same CSR reuses the choice.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int32_t, int64_t, int32_t, int32_t>, int> g_tuned;
+
+static std::tuple<int32_t, int64_t, int32_t, int32_t> tune_key(const Graph* g, int precision) {
+    return std::make_tuple(g->n, g->nnz, g->info.max_degree, (int32_t)precision);
 }
+
+static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
+                           sp_bc_stats* stats, cudaStream_t st);
+
+// Time one batch at each width on the call's own first sources and keep the
+// width with the most traversed arcs per second of kernel time.
+static sp_status autotune_width(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, cudaStream_t st,
+                                int* width, int* launches) {
+    double* scratch = nullptr;
+    SP_CUDA(cudaMallocAsync((void**)&scratch, sizeof(double) * (size_t)g->n, st));
+    double best_rate = -1.0;
+    int best = default_batch_width(nsrc);
+    for (int w : {32, 64, 128, 256}) {
+        if (w > nsrc) break;
+        sp_bc_opts t = o;
+        t.form = SP_FORM_BATCHED;
+        t.batch = w;
+        sp_bc_stats ts;
+        sp_status rc = bc_device(g, d_src, w, t, scratch, &ts, st);
+        *launches += ts.launches;
+        if (rc != SP_OK) {
+            cudaFreeAsync(scratch, st);
+            return rc;
+        }
+        double rate = ts.kernel_ms > 0 ? (double)ts.traversed_arcs / ts.kernel_ms : 0.0;
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = w;
+        }
+    }
+    cudaFreeAsync(scratch, st);
+    *width = best;
+    return SP_OK;
+}
+
+int default_batch_width(int32_t nsrc) { return nsrc > 32 ? 64 : 32; }
 
 // Run BC on device buffers, rerunning with a wider representation or more
 // workspace when the device reports that it ran out of one.
@@ -182,9 +215,30 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
     bool theta_f32 = o.precision == SP_FP32_DELTA;
     int form = o.form;
     if (form == SP_FORM_AUTO) form = nsrc >= 16 ? SP_FORM_BATCHED : SP_FORM_PLAIN;
-    int width = form == SP_FORM_BATCHED ? choose_width(g, o, nsrc) : 1;
+    int width = 1, launches = 0, tuned = 0;
+    if (form == SP_FORM_BATCHED) {
+        if (o.batch > 0) {
+            width = o.batch;
+        } else {
+            auto key = tune_key(g, o.precision);
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tuned.find(key);
+                if (it != g_tuned.end()) width = it->second;
+            }
+            if (width == 1 && nsrc >= 128) {
+                sp_status trc = autotune_width(g, d_src, nsrc, o, st, &width, &launches);
+                if (trc != SP_OK) return trc;
+                tuned = 1;
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tuned[key] = width;
+            }
+            if (width == 1) width = default_batch_width(nsrc);
+        }
+    }
     int promoted = 0, sigma_batches = 0;
     int64_t ecap = 0, hcap = 0, lcap = 0;
+    double kernel_ms = 0.0;
     LaunchResult r;
     for (int attempt = 0; attempt < 16; ++attempt) {
         r = LaunchResult{};
@@ -222,6 +276,8 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             rc = run_batched(L, &r);
         }
         if (rc != SP_OK) return rc;
+        kernel_ms += r.kernel_ms;
+        launches += r.launches;
         if (r.err == kErrSigmaOverflow && !sigma_float) {
             sigma_float = true;
             sigma_batches = 1;
@@ -255,6 +311,10 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         stats->form = form;
         stats->promoted = promoted;
         stats->sigma_float = sigma_float ? 1 : sigma_batches;
+        stats->dag_arcs = (int64_t)r.dag_arcs;
+        stats->kernel_ms = kernel_ms;
+        stats->launches = launches;
+        stats->tuned = tuned;
     }
     return SP_OK;
 }
@@ -389,6 +449,7 @@ sp_status sp_bc_ex(sp_graph gh, const int32_t* sources, int32_t nsrc, const sp_b
             if (e != cudaSuccess) rc = cuda_fail(e, "zeroing bc_out");
         } else {
             rc = bc_device(g, d_src, nsrc, o, d_bc, stats, st);
+            if (stats) stats->launches += 1;  // the source check
         }
     }
     if (rc == SP_OK && host_out) {

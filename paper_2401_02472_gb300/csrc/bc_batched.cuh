@@ -123,7 +123,7 @@ struct BatchKernel {
     int cshift[W];             // per-source shift between level d-1 and d (forward) / d and d+1 (backward)
     int my_emax[W], my_emin[W];
     bool ovf = false;
-    unsigned long long st_arcs = 0, st_reached = 0, st_entries = 0, st_scanned = 0;
+    unsigned long long st_arcs = 0, st_reached = 0, st_entries = 0, st_scanned = 0, st_dag = 0;
 
     __device__ BatchKernel(const BatchArgs& args) : a(args), ctl(args.ctl), lane(lane_id()) {
 #pragma unroll
@@ -294,7 +294,7 @@ struct BatchKernel {
                     uint32_t p[W];
                     load_mask<W>(prev + (size_t)u * W, p);
 #pragma unroll
-                    for (int k = 0; k < W; ++k) m[k] = Fj[k] & p[k];
+                    for (int k = 0; k < W; ++k) { m[k] = Fj[k] & p[k]; st_dag += __popc(m[k]); }
                 }
                 discover(u, Fj);
             }
@@ -377,7 +377,7 @@ struct BatchKernel {
                     uint32_t p[W];
                     load_mask<W>(prev + (size_t)u * W, p);
 #pragma unroll
-                    for (int k = 0; k < W; ++k) m[k] = F[k] & p[k];
+                    for (int k = 0; k < W; ++k) { m[k] = F[k] & p[k]; st_dag += __popc(m[k]); }
                 }
                 discover(u, F);
             }
@@ -819,9 +819,10 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs a) {
 
 out:
     {
-        __shared__ unsigned long long s_st[4];
-        if (threadIdx.x == 0) { s_st[0] = 0; s_st[1] = 0; s_st[2] = 0; s_st[3] = 0; }
+        __shared__ unsigned long long s_st[5];
+        if (threadIdx.x == 0) { s_st[0] = 0; s_st[1] = 0; s_st[2] = 0; s_st[3] = 0; s_st[4] = 0; }
         __syncthreads();
+        atomicAdd(&s_st[4], K.st_dag);
         atomicAdd(&s_st[0], K.st_arcs);
         atomicAdd(&s_st[1], K.st_reached);
         atomicAdd(&s_st[2], K.st_entries);
@@ -832,6 +833,7 @@ out:
             atomicAdd(&ctl->reached, s_st[1]);
             atomicAdd(&ctl->entries, s_st[2]);
             atomicAdd(&ctl->scanned_arcs, s_st[3]);
+            atomicAdd(&ctl->dag_arcs, s_st[4]);
             atomicMax(&ctl->max_levels, levels_max);
             int e = ld_volatile(&ctl->err);
             if (e != 0 && a.err_latch) *(volatile int*)a.err_latch = e;

@@ -100,7 +100,12 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.seg = seg;
 
     void* args[] = {&a};
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, st);
     ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBatchThreads), args, 0, st);
+    cudaEventRecord(ev1, st);
     if (ce != cudaSuccess) {
         cudaFreeAsync(ws, st);
         return cuda_fail(ce, "cudaLaunchCooperativeKernel (batched form)");
@@ -117,6 +122,13 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     result->reached = h.reached;
     result->entries = h.entries;
     result->scanned_arcs = h.scanned_arcs;
+    result->dag_arcs = h.dag_arcs;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) result->kernel_ms = ms;
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    result->launches = 1;
+    result->grid = grid;
     if (h.err == SP_ERR_TIMEOUT) result->diag = barrier_diagnostic(h, grid);
     result->ecap = ecap;
     result->hcap = hcap;

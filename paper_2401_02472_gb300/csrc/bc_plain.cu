@@ -112,7 +112,7 @@ struct PlainKernel {
     // per-thread accumulators
     int my_emax = INT_MIN, my_emin = INT_MAX;
     bool ovf = false;
-    unsigned long long st_arcs = 0, st_reached = 0, st_scanned = 0;
+    unsigned long long st_arcs = 0, st_reached = 0, st_scanned = 0, st_dag = 0;
 
     __device__ PlainKernel(const PlainArgs& args) : a(args), ctl(args.ctl), lane(lane_id()) {}
 
@@ -148,6 +148,7 @@ struct PlainKernel {
             if (atomicCAS(&a.lvl[u], -1, d + 1) == -1) push(u, d + 1);
         } else if (lu == d - 1) {
             c = __ldcg(&sig()[u]);
+            st_dag += 1;
         }
         return c;
     }
@@ -464,17 +465,19 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
 out:
     {
         // statistics: block-level then one atomic per block
-        __shared__ unsigned long long s_st[3];
-        if (threadIdx.x == 0) { s_st[0] = 0; s_st[1] = 0; s_st[2] = 0; }
+        __shared__ unsigned long long s_st[4];
+        if (threadIdx.x == 0) { s_st[0] = 0; s_st[1] = 0; s_st[2] = 0; s_st[3] = 0; }
         __syncthreads();
         atomicAdd(&s_st[0], K.st_arcs);
         atomicAdd(&s_st[1], K.st_reached);
         atomicAdd(&s_st[2], K.st_scanned);
+        atomicAdd(&s_st[3], K.st_dag);
         __syncthreads();
         if (threadIdx.x == 0) {
             atomicAdd(&ctl->traversed_arcs, s_st[0]);
             atomicAdd(&ctl->reached, s_st[1]);
             atomicAdd(&ctl->scanned_arcs, s_st[2]);
+            atomicAdd(&ctl->dag_arcs, s_st[3]);
             atomicMax(&ctl->max_levels, levels_max);
             int e = ld_volatile(&ctl->err);
             if (e != 0 && a.err_latch) *(volatile int*)a.err_latch = e;
@@ -567,7 +570,12 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     cudaMemsetAsync(a.trace, 0, sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32), st);
 
     void* args[] = {&a};
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, st);
     ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPlainThreads), args, 0, st);
+    cudaEventRecord(ev1, st);
     if (ce != cudaSuccess) {
         cudaFreeAsync(ws, st);
         return cuda_fail(ce, "cudaLaunchCooperativeKernel (plain form)");
@@ -583,6 +591,12 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     result->reached = h.reached;
     result->entries = h.reached;
     result->scanned_arcs = h.scanned_arcs;
+    result->dag_arcs = h.dag_arcs;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) result->kernel_ms = ms;
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    result->launches = 1;
     if (h.err == SP_ERR_TIMEOUT) result->diag = barrier_diagnostic(h, grid);
 #ifdef SP_TRACE
     if (h.err == SP_ERR_TIMEOUT) {

@@ -41,6 +41,7 @@ struct Ctl {
     unsigned long long reached;
     unsigned long long entries;
     unsigned long long scanned_arcs;
+    unsigned long long dag_arcs;     // (arc, source) pairs on shortest-path DAGs
     int max_levels;
     unsigned int timeout_count;      // arrivals seen by the first wait that timed out
     int snap[2];                     // qtail as the last block found it, per barrier parity

@@ -27,7 +27,6 @@ struct Graph {
     int* err_latch_dev = nullptr;
     std::mutex mu;
     bool sigma_float = false;  // path counts of this graph overflowed 64-bit integers before
-    std::map<int, int> tuned_batch;  // precision -> batch width chosen by the autotuner
 };
 
 // Thread-local error text.
@@ -72,6 +71,10 @@ struct LaunchResult {
     int levels = 0;
     unsigned long long traversed_arcs = 0, reached = 0, entries = 0, scanned_arcs = 0;
     int64_t ecap = 0, hcap = 0, lcap = 0;  // capacities used (batched form)
+    unsigned long long dag_arcs = 0;
+    double kernel_ms = 0.0;                // CUDA-event time of the launch
+    int launches = 0;
+    int grid = 0;
     std::string diag;                      // barrier state when a wait timed out
 };
 
