@@ -41,6 +41,8 @@ WORKLOADS = {
     # name: graph, sources, source seed, precision, form
     "rmat22_1024src_batched": dict(graph="rmat22", nsrc=1024, seed=14, precision="fp32_delta", form="batched",
                                    desc="RMAT scale 22, edge factor 16, 1,024 sources, autotuned batches"),
+    "rmat22_128src_batched": dict(graph="rmat22", nsrc=128, seed=14, precision="fp32_delta", form="batched",
+                                  desc="RMAT scale 22, edge factor 16, 128 sources (one batch; profiling case)"),
     "rmat20_64src_batched": dict(graph="rmat20", nsrc=64, seed=12, precision="fp32_delta", form="batched",
                                  desc="RMAT scale 20, edge factor 16, 64 sources"),
     "knn4_1m_256src_batched": dict(graph="knn4_1m", nsrc=256, seed=13, precision="fp32_delta", form="batched",

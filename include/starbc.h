@@ -118,8 +118,15 @@ typedef struct {
     int32_t max_ctas;           /* cap on the persistent grid (0 = every co-resident CTA) */
     int64_t barrier_timeout_ns; /* per device-side wait; 0 = 20 s */
     int32_t debug_flags;        /* SP_DEBUG_* (tests only) */
-    int32_t reserved[3];
+    int32_t flags;              /* SP_BC_* */
+    int32_t reserved[2];
 } sp_bc_opts;
+
+/* flags: run the batched form's sources in the caller's order.  By default
+   they are regrouped so that sources at similar distance from a maximum-degree
+   vertex share batches and adjacent lanes (BC is a sum over sources, so only
+   the rounding order changes). */
+#define SP_BC_KEEP_ORDER 0x1
 
 /* debug_flags: block 0 leaves at one grid barrier without arriving, so the
    other blocks' waits run out and the call returns SP_ERR_TIMEOUT. */

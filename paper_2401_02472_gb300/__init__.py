@@ -26,12 +26,13 @@ SP_FP64, SP_FP32_DELTA = 0, 1
 SP_FORM_AUTO, SP_FORM_PLAIN, SP_FORM_BATCHED = 0, 1, 2
 SP_GRAPH_CHECK_SYMMETRIC = 0x1
 SP_DEBUG_SKIP_BARRIER = 0x1
+SP_BC_KEEP_ORDER = 0x1
 
 
 class sp_bc_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("form", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("max_ctas", ctypes.c_int32), ("barrier_timeout_ns", ctypes.c_int64),
-                ("debug_flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("debug_flags", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class sp_bc_stats(ctypes.Structure):
@@ -179,11 +180,11 @@ def sp_graph_check(g: int):
 
 
 def make_opts(precision=SP_FP64, form=SP_FORM_AUTO, batch=0, max_ctas=0, barrier_timeout_ns=0,
-              debug_flags=0) -> sp_bc_opts:
+              debug_flags=0, flags=0) -> sp_bc_opts:
     o = sp_bc_opts()
     lib.sp_bc_opts_default(ctypes.byref(o))
     o.precision, o.form, o.batch, o.max_ctas = precision, form, batch, max_ctas
-    o.barrier_timeout_ns, o.debug_flags = barrier_timeout_ns, debug_flags
+    o.barrier_timeout_ns, o.debug_flags, o.flags = barrier_timeout_ns, debug_flags, flags
     return o
 
 

@@ -203,6 +203,94 @@ static sp_status autotune_width(Graph* g, const int32_t* d_src, int32_t nsrc, co
 
 int default_batch_width(int32_t nsrc) { return nsrc > 32 ? 64 : 32; }
 
+// Sort key of each source: (hop distance from a maximum-degree vertex, the
+// smallest neighbour one hop closer to it).  Sources with equal keys tend to
+// sit at the same BFS level for most vertices, so batching them in adjacent
+// bit positions packs the per-(vertex, source) rows the kernels gather.
+__global__ void source_keys_kernel(const int32_t* __restrict__ src, int32_t nsrc, const int32_t* __restrict__ rp,
+                                   const int32_t* __restrict__ ci, const int32_t* __restrict__ dist,
+                                   unsigned long long* __restrict__ keys) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < nsrc; i += nwarp) {
+        const int s = src[i];
+        const int ds = dist[s];
+        int best = INT_MAX;
+        if (ds > 0)
+            for (int e = rp[s] + lane; e < rp[s + 1]; e += 32) {
+                int u = ci[e];
+                if (dist[u] == ds - 1) best = min(best, u);
+            }
+        best = warp_min_i32(best);
+        if (lane == 0) {
+            unsigned dk = ds < 0 ? 0xFFFFFFFFu : (unsigned)ds;
+            keys[i] = ((unsigned long long)dk << 32) | (unsigned)(best == INT_MAX ? s : best);
+        }
+    }
+}
+
+// A copy of the call's sources in key order (stable), or nullptr to keep the
+// caller's order (a single source, or the plain form).
+static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cudaStream_t st, int32_t** out) {
+    *out = nullptr;
+    if (nsrc < 2 || g->n == 0) return SP_OK;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (!g->d_top_dist) {
+            int32_t* d_dist = nullptr;
+            int32_t* d_one = nullptr;
+            SP_CUDA(cudaMalloc((void**)&d_dist, sizeof(int32_t) * (size_t)g->n));
+            SP_CUDA(cudaMallocAsync((void**)&d_one, sizeof(int32_t), st));
+            SP_CUDA(cudaMemcpyAsync(d_one, &g->top_vertex, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            PlainLaunch L{};
+            L.g = g;
+            L.d_sources = d_one;
+            L.nsrc = 1;
+            L.d_dist = d_dist;
+            L.mode = PlainMode::BFS;
+            L.timeout_ns = bfs_timeout_ns();
+            L.stream = st;
+            LaunchResult r;
+            sp_status rc = run_plain(L, &r);
+            cudaFreeAsync(d_one, st);
+            if (rc == SP_OK) rc = map_device_error(r.err, "source ordering", r.diag);
+            if (rc != SP_OK) {
+                cudaFree(d_dist);
+                return rc;
+            }
+            g->d_top_dist = d_dist;
+        }
+    }
+    unsigned long long* d_keys = nullptr;
+    SP_CUDA(cudaMallocAsync((void**)&d_keys, sizeof(unsigned long long) * (size_t)nsrc, st));
+    source_keys_kernel<<<std::min(1024, (nsrc + 7) / 8), 256, 0, st>>>(d_src, nsrc, g->d_rp, g->d_ci, g->d_top_dist,
+                                                                          d_keys);
+    std::vector<unsigned long long> keys(nsrc);
+    std::vector<int32_t> srcs(nsrc);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned long long) * nsrc, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(srcs.data(), d_src, sizeof(int32_t) * nsrc, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d_keys, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "source ordering");
+    std::vector<int32_t> idx(nsrc);
+    for (int32_t i = 0; i < nsrc; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return keys[x] < keys[y]; });
+    std::vector<int32_t> sorted(nsrc);
+    for (int32_t i = 0; i < nsrc; ++i) sorted[i] = srcs[idx[i]];
+    SP_CUDA(cudaMallocAsync((void**)out, sizeof(int32_t) * (size_t)nsrc, st));
+    e = cudaMemcpyAsync(*out, sorted.data(), sizeof(int32_t) * nsrc, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(*out, st);
+        *out = nullptr;
+        return cuda_fail(e, "source ordering");
+    }
+    return SP_OK;
+}
+
 // Run BC on device buffers, rerunning with a wider representation or more
 // workspace when the device reports that it ran out of one.
 static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
@@ -236,6 +324,20 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             if (width == 1) width = default_batch_width(nsrc);
         }
     }
+    int32_t* d_sorted = nullptr;
+    if (form == SP_FORM_BATCHED && !(o.flags & SP_BC_KEEP_ORDER)) {
+        sp_status orc = order_sources(g, d_src, nsrc, st, &d_sorted);
+        if (orc != SP_OK) return orc;
+        if (d_sorted) {
+            d_src = d_sorted;
+            launches += 1;
+        }
+    }
+    struct FreeSorted {
+        int32_t* p;
+        cudaStream_t s;
+        ~FreeSorted() { if (p) cudaFreeAsync(p, s); }
+    } free_sorted{d_sorted, st};
     int promoted = 0, sigma_batches = 0;
     int64_t ecap = 0, hcap = 0, lcap = 0;
     double kernel_ms = 0.0;
@@ -401,6 +503,7 @@ sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_
 sp_status sp_graph_destroy(sp_graph gh) {
     if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
     Graph* g = reinterpret_cast<Graph*>(gh);
+    if (g->d_top_dist) cudaFree(g->d_top_dist);
     cudaFree(g->d_rp);
     cudaFree(g->d_ci);
     delete g;
@@ -434,6 +537,7 @@ sp_status sp_bc_ex(sp_graph gh, const int32_t* sources, int32_t nsrc, const sp_b
     if (o.batch != 0 && o.batch != 32 && o.batch != 64 && o.batch != 128 && o.batch != 256)
         return fail(SP_ERR_INVALID_ARG, "batch must be 0, 32, 64, 128 or 256");
     if (o.max_ctas < 0 || o.barrier_timeout_ns < 0) return fail(SP_ERR_INVALID_ARG, "negative option");
+    if (o.flags & ~(int32_t)SP_BC_KEEP_ORDER) return fail(SP_ERR_INVALID_ARG, "unknown flag");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (g->n == 0) return SP_OK;

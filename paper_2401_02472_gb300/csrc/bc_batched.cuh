@@ -35,6 +35,9 @@
 namespace sp {
 
 constexpr int kBatchThreads = 256;
+#ifndef SP_BATCH_MINB
+#define SP_BATCH_MINB 4  // resident blocks per SM the register budget is sized for
+#endif
 
 struct BatchArgs {
     const int32_t* rp;
@@ -54,8 +57,11 @@ struct BatchArgs {
     int32_t* eoff;            // [lcap+2]
     HubRec* hubs;
     int32_t hcap;
-    int32_t* hoff;            // [lcap+2]
-    unsigned long long* hcnt; // [lcap+2]
+    int32_t* hoff;            // [lcap+2] first hub record of each level
+    int32_t* soff;            // [lcap+2] first segment of each level in segrec
+    int32_t* segrec;          // [scap] hub record of each segment
+    int32_t scap;
+    unsigned long long* hcnt; // [lcap+2] records << 32 | segments, per level
     int32_t* hdone;           // [2*hcap]
     void* part;               // [segcap][B] 8-byte slots
     int32_t segcap;
@@ -115,7 +121,8 @@ struct BatchKernel {
     Ctl* ctl;
     int lane;
     int d = 0;
-    int hoff_d = 0, nrec_d = 0, nseg_d = 0, hoff_next = 0;
+    int hoff_d = 0, nrec_d = 0, nseg_d = 0, hoff_next = 0;  // hub records of level d / d+1
+    int soff_d = 0, soff_next = 0;                            // segments of level d / d+1
     int stamp_next = 0;
     uint32_t* prev = nullptr;  // dense F_{d-1}
     uint32_t* cur = nullptr;   // dense F_d
@@ -131,9 +138,9 @@ struct BatchKernel {
     }
     __device__ __forceinline__ SigT* sig() const { return reinterpret_cast<SigT*>(a.sig); }
     __device__ __forceinline__ ThT* th() const { return reinterpret_cast<ThT*>(a.th); }
-    __device__ __forceinline__ uint32_t* ring(int r) const { return a.dense + (size_t)(r & 3) * (size_t)a.n * W; }
 
-    // Append vertex u to level nl of the stack (and to the hub list).
+    // Append vertex u to level nl of the stack; rows longer than t_hub also get
+    // a hub record and one work item per segment of `seg` arcs.
     __device__ void push(int u, int nl) {
         int du = __ldg(&a.rp[u + 1]) - __ldg(&a.rp[u]);
         bool hub = du > a.t_hub;
@@ -145,12 +152,16 @@ struct BatchKernel {
             unsigned long long old = atomicAdd(&a.hcnt[nl], (1ull << 32) | (unsigned long long)(unsigned)nseg);
             int rec = hoff_next + (int)(old >> 32);
             int sb = (int)(old & 0xFFFFFFFFull);
-            if (rec >= a.hcap || sb + nseg > a.segcap) { set_error(ctl, kErrCapHubs); return; }
+            if (rec >= a.hcap || sb + nseg > a.segcap || (long long)soff_next + sb + nseg > a.scap) {
+                set_error(ctl, kErrCapHubs);
+                return;
+            }
             HubRec h;
             h.v = u; h.qpos = pos; h.nseg = nseg; h.seg_base = sb;
             a.hubs[rec] = h;
             a.hdone[rec] = 0;
             a.hdone[a.hcap + rec] = 0;
+            for (int q = 0; q < nseg; ++q) a.segrec[soff_next + sb + q] = rec;
         }
     }
 
@@ -175,6 +186,54 @@ struct BatchKernel {
         }
         if (anynew) {
             if (atomicMax(&a.ptag[u], stamp_next) < stamp_next) push(u, d + 1);
+        }
+    }
+
+    // Pull over the pending arcs of one window, in lane (= CSR) order: for
+    // pending lane j, every lane s with bit s of m_j set adds row[u_j][s].
+    // Loads of G arcs are issued before any of them is added, so that a warp
+    // keeps G*W row loads in flight.  on_owner(o) runs before the arcs of
+    // entry o are added.
+    template <bool CHECK_OVF, typename RowT, typename AccType, typename OnOwner>
+    __device__ __forceinline__ void pull_window(const RowT* base, int u, int owner, const uint32_t (&m)[W],
+                                                unsigned pend, AccType (&acc)[W], OnOwner&& on_owner) {
+        constexpr int G = W >= 8 ? 1 : 8 / W;
+        while (pend) {
+            int jj[G];
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                jj[i] = pend ? __ffs(pend) - 1 : -1;
+                pend &= pend - 1;
+            }
+            AccType x[G][W];
+            int oi[G];
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                const int srcl = jj[i] >= 0 ? jj[i] : 0;
+                const int ui = __shfl_sync(kFull, u, srcl);
+                oi[i] = __shfl_sync(kFull, owner, srcl);
+                const RowT* row = base + (size_t)ui * B + lane;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    const uint32_t mk = __shfl_sync(kFull, m[k], srcl);
+                    x[i][k] = (jj[i] >= 0 && ((mk >> lane) & 1u)) ? (AccType)__ldcg(row + k * 32) : (AccType)0;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                if (jj[i] < 0) break;
+                on_owner(oi[i]);
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    if constexpr (CHECK_OVF) {
+                        AccType s2 = acc[k] + x[i][k];
+                        ovf |= s2 < x[i][k];
+                        acc[k] = s2;
+                    } else {
+                        acc[k] += x[i][k];
+                    }
+                }
+            }
         }
     }
 
@@ -235,15 +294,34 @@ struct BatchKernel {
         if (lane == 0) a.bc[v] = __ldcg(&a.bc[v]) + (double)bcsum;
     }
 
+    // Owner lane of window position ai: the largest j with excl_j <= ai.
+    __device__ __forceinline__ int owner_of(int excl, int ai) const {
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            int ex = __shfl_sync(kFull, excl, j + step < 32 ? j + step : 31);
+            if (j + step < 32 && ex <= ai) j += step;
+        }
+        return j;
+    }
+
+    // Entry of lane (e0 + lane) if e0 + lane < qe; hub entries and entries
+    // past the level come back with deg = 0.
+    __device__ __forceinline__ void load_entry(int e, int qe, bool& valid, bool& hubent, int& v) const {
+        valid = e < qe;
+        unsigned qv = valid ? (unsigned)__ldcg(&a.ent[e]) : kHubFlag;
+        hubent = (qv & kHubFlag) != 0;
+        v = (int)(qv & kVertexMask);
+        if (valid && v >= a.n) { set_error(ctl, kErrCorrupt); valid = false; hubent = true; v = 0; }
+    }
+
     // ---------------- forward ----------------
     // Chunk of up to 32 level-stack entries [e0, min(e0+32, qe)).
     __device__ void fwd_chunk(int e0, int qe) {
         const int e = e0 + lane;
-        bool valid = e < qe;
-        unsigned qv = valid ? (unsigned)__ldcg(&a.ent[e]) : kHubFlag;
-        bool hubent = (qv & kHubFlag) != 0;
-        int v = (int)(qv & kVertexMask);
-        if (valid && v >= a.n) { set_error(ctl, kErrCorrupt); valid = false; hubent = true; v = 0; }
+        bool valid, hubent;
+        int v;
+        load_entry(e, qe, valid, hubent, v);
         uint32_t F[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) F[k] = 0u;
@@ -251,6 +329,7 @@ struct BatchKernel {
         if (valid) {
             load_mask<W>(cur + (size_t)v * W, F);
             store_mask<W>(a.emask + (size_t)e * W, F);
+            st_entries += 1;
             if (!hubent) {
                 beg = __ldg(&a.rp[v]);
                 deg = __ldg(&a.rp[v + 1]) - beg;
@@ -259,10 +338,7 @@ struct BatchKernel {
                 for (int k = 0; k < W; ++k) pc += __popc(F[k]);
                 st_arcs += (unsigned long long)deg * (unsigned long long)pc;
                 st_reached += (unsigned long long)pc;
-                st_entries += 1;
                 st_scanned += (unsigned long long)deg;
-            } else {
-                st_entries += 1;
             }
         }
         const int incl = warp_incl_scan(deg);
@@ -272,16 +348,18 @@ struct BatchKernel {
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[k] = 0;
         int cur_e = -1;  // lane index of the entry whose sums are in acc
+        auto flush_current = [&]() {
+            if (cur_e >= 0) {
+                uint32_t Fc[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) Fc[k] = __shfl_sync(kFull, F[k], cur_e);
+                sigma_flush(__shfl_sync(kFull, v, cur_e), Fc, acc);
+            }
+        };
         for (int cb = 0; cb < total; cb += kWarp) {
             const int ai = cb + lane;
             const bool has = ai < total;
-            // owner lane: the largest j with excl_j <= ai
-            int j = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                int ex = __shfl_sync(kFull, excl, j + step < 32 ? j + step : 31);
-                if (j + step < 32 && ex <= ai) j += step;
-            }
+            const int j = owner_of(excl, ai);
             const int bj = __shfl_sync(kFull, beg, j);
             const int exj = __shfl_sync(kFull, excl, j);
             uint32_t Fj[W], m[W];
@@ -302,56 +380,31 @@ struct BatchKernel {
                 uint32_t anym = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) anym |= m[k];
-                unsigned pend = __ballot_sync(kFull, anym != 0u);
-                while (pend) {
-                    const int jj = __ffs(pend) - 1;
-                    pend &= pend - 1;
-                    const int uj = __shfl_sync(kFull, u, jj);
-                    const int ej = __shfl_sync(kFull, j, jj);
+                const unsigned pend = __ballot_sync(kFull, anym != 0u);
+                pull_window<!kFloatSig>(sig(), u, j, m, pend, acc, [&](int ej) {
                     if (ej != cur_e) {
-                        if (cur_e >= 0) {
-                            uint32_t Fc[W];
-#pragma unroll
-                            for (int k = 0; k < W; ++k) Fc[k] = __shfl_sync(kFull, F[k], cur_e);
-                            sigma_flush(__shfl_sync(kFull, v, cur_e), Fc, acc);
-                        }
+                        flush_current();
                         cur_e = ej;
 #pragma unroll
                         for (int k = 0; k < W; ++k) acc[k] = 0;
                     }
-                    const SigT* row = sig() + (size_t)uj * B + lane;
-#pragma unroll
-                    for (int k = 0; k < W; ++k) {
-                        uint32_t mk = __shfl_sync(kFull, m[k], jj);
-                        if ((mk >> lane) & 1u) {
-                            SigT x = __ldcg(row + k * 32);
-                            if constexpr (kFloatSig) {
-                                acc[k] += x;
-                            } else {
-                                SigT s2 = acc[k] + x;
-                                ovf |= s2 < x;
-                                acc[k] = s2;
-                            }
-                        }
-                    }
-                }
+                });
             }
         }
-        if (cur_e >= 0) {
-            uint32_t Fc[W];
-#pragma unroll
-            for (int k = 0; k < W; ++k) Fc[k] = __shfl_sync(kFull, F[k], cur_e);
-            sigma_flush(__shfl_sync(kFull, v, cur_e), Fc, acc);
-        }
+        flush_current();
     }
 
-    // Segment g of this level's hubs (forward).
+    // One segment of a long row (forward).  g: segment index within level d.
     __device__ void fwd_hub_segment(int g) {
-        const int r = find_hub(a.hubs, hoff_d, hoff_d + nrec_d, g);
+        const int r = __ldcg(&a.segrec[soff_d + g]);
+        if (r < hoff_d || r >= hoff_d + nrec_d) {
+            if (lane == 0) set_error(ctl, kErrCorrupt);
+            return;
+        }
         const int hv = __ldcg(&a.hubs[r].v);
         const int nseg = __ldcg(&a.hubs[r].nseg);
         const int sb = __ldcg(&a.hubs[r].seg_base);
-        if (hv < 0 || hv >= a.n || nseg < 1 || sb < 0 || sb + nseg > a.segcap) {
+        if (hv < 0 || hv >= a.n || nseg < 1 || sb < 0 || sb + nseg > a.segcap || g < sb || g >= sb + nseg) {
             if (lane == 0) set_error(ctl, kErrCorrupt);
             return;
         }
@@ -385,30 +438,25 @@ struct BatchKernel {
                 uint32_t anym = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) anym |= m[k];
-                unsigned pend = __ballot_sync(kFull, anym != 0u);
-                while (pend) {
-                    const int jj = __ffs(pend) - 1;
-                    pend &= pend - 1;
-                    const int uj = __shfl_sync(kFull, u, jj);
-                    const SigT* row = sig() + (size_t)uj * B + lane;
-#pragma unroll
-                    for (int k = 0; k < W; ++k) {
-                        uint32_t mk = __shfl_sync(kFull, m[k], jj);
-                        if ((mk >> lane) & 1u) {
-                            SigT x = __ldcg(row + k * 32);
-                            if constexpr (kFloatSig) {
-                                acc[k] += x;
-                            } else {
-                                SigT s2 = acc[k] + x;
-                                ovf |= s2 < x;
-                                acc[k] = s2;
-                            }
-                        }
-                    }
-                }
+                const unsigned pend = __ballot_sync(kFull, anym != 0u);
+                pull_window<!kFloatSig>(sig(), u, 0, m, pend, acc, [](int) {});
             }
         }
         if (lane == 0) st_scanned += (unsigned long long)(end - beg);
+        auto count_entry = [&]() {
+            if (lane == 0) {
+                int pc = 0;
+#pragma unroll
+                for (int k = 0; k < W; ++k) pc += __popc(F[k]);
+                st_arcs += (unsigned long long)(re - rb) * (unsigned long long)pc;
+                st_reached += (unsigned long long)pc;
+            }
+        };
+        if (nseg == 1) {  // the whole row in one segment: no partial sums
+            count_entry();
+            if (d > 0) sigma_flush(hv, F, acc);
+            return;
+        }
         SigT* prow = reinterpret_cast<SigT*>(a.part) + (size_t)g * B + lane;
 #pragma unroll
         for (int k = 0; k < W; ++k) prow[k * 32] = acc[k];
@@ -439,24 +487,16 @@ struct BatchKernel {
                 }
             }
         }
-        if (lane == 0) {
-            int pc = 0;
-#pragma unroll
-            for (int k = 0; k < W; ++k) pc += __popc(F[k]);
-            st_arcs += (unsigned long long)(re - rb) * (unsigned long long)pc;
-            st_reached += (unsigned long long)pc;
-        }
+        count_entry();
         if (d > 0) sigma_flush(hv, F, tot);
     }
 
     // ---------------- backward ----------------
     __device__ void bwd_chunk(int e0, int qe, bool skip_arcs) {
         const int e = e0 + lane;
-        bool valid = e < qe;
-        unsigned qv = valid ? (unsigned)__ldcg(&a.ent[e]) : kHubFlag;
-        bool hubent = (qv & kHubFlag) != 0;
-        int v = (int)(qv & kVertexMask);
-        if (valid && v >= a.n) { set_error(ctl, kErrCorrupt); valid = false; hubent = true; v = 0; }
+        bool valid, hubent;
+        int v;
+        load_entry(e, qe, valid, hubent, v);
         uint32_t F[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) F[k] = 0u;
@@ -491,12 +531,7 @@ struct BatchKernel {
         for (int cb = 0; cb < total; cb += kWarp) {
             const int ai = cb + lane;
             const bool has = ai < total;
-            int j = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                int ex = __shfl_sync(kFull, excl, j + step < 32 ? j + step : 31);
-                if (j + step < 32 && ex <= ai) j += step;
-            }
+            const int j = owner_of(excl, ai);
             const int bj = __shfl_sync(kFull, beg, j);
             const int exj = __shfl_sync(kFull, excl, j);
             uint32_t m[W];
@@ -505,44 +540,34 @@ struct BatchKernel {
             int w = 0;
             if (has) {
                 w = __ldg(&a.ci[bj + (ai - exj)]);
-                uint32_t c[W];
-                load_mask<W>(next + (size_t)w * W, c);
-#pragma unroll
-                for (int k = 0; k < W; ++k) m[k] = c[k];
+                load_mask<W>(next + (size_t)w * W, m);
             }
-            // masks of the owners are needed lane-wise: AND after the shuffle below
             uint32_t anym = 0;
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                uint32_t Fj = __shfl_sync(kFull, F[k], j);
-                m[k] &= Fj;
+                m[k] &= __shfl_sync(kFull, F[k], j);
                 anym |= m[k];
             }
-            unsigned pend = __ballot_sync(kFull, has && anym != 0u);
-            while (pend) {
-                const int jj = __ffs(pend) - 1;
-                pend &= pend - 1;
-                const int wj = __shfl_sync(kFull, w, jj);
-                const int ej = __shfl_sync(kFull, j, jj);
+            const unsigned pend = __ballot_sync(kFull, has && anym != 0u);
+            pull_window<false>(th(), w, j, m, pend, acc, [&](int ej) {
                 if (ej > next_flush) flush_upto(ej);
-                const ThT* row = th() + (size_t)wj * B + lane;
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    uint32_t mk = __shfl_sync(kFull, m[k], jj);
-                    if ((mk >> lane) & 1u) acc[k] += (AccT)__ldcg(row + k * 32);
-                }
-            }
+            });
         }
         flush_upto(32);
     }
 
     __device__ void bwd_hub_segment(int g, bool skip_arcs) {
-        const int r = find_hub(a.hubs, hoff_d, hoff_d + nrec_d, g);
+        const int r = __ldcg(&a.segrec[soff_d + g]);
+        if (r < hoff_d || r >= hoff_d + nrec_d) {
+            if (lane == 0) set_error(ctl, kErrCorrupt);
+            return;
+        }
         const int hv = __ldcg(&a.hubs[r].v);
         const int qpos = __ldcg(&a.hubs[r].qpos);
         const int nseg = __ldcg(&a.hubs[r].nseg);
         const int sb = __ldcg(&a.hubs[r].seg_base);
-        if (hv < 0 || hv >= a.n || nseg < 1 || sb < 0 || sb + nseg > a.segcap || qpos < 0 || qpos >= a.ecap) {
+        if (hv < 0 || hv >= a.n || nseg < 1 || sb < 0 || sb + nseg > a.segcap || qpos < 0 || qpos >= a.ecap ||
+            g < sb || g >= sb + nseg) {
             if (lane == 0) set_error(ctl, kErrCorrupt);
             return;
         }
@@ -570,20 +595,14 @@ struct BatchKernel {
 #pragma unroll
                 for (int k = 0; k < W; ++k) { m[k] = c[k] & F[k]; anym |= m[k]; }
             }
-            unsigned pend = __ballot_sync(kFull, anym != 0u);
-            while (pend) {
-                const int jj = __ffs(pend) - 1;
-                pend &= pend - 1;
-                const int wj = __shfl_sync(kFull, w, jj);
-                const ThT* row = th() + (size_t)wj * B + lane;
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    uint32_t mk = __shfl_sync(kFull, m[k], jj);
-                    if ((mk >> lane) & 1u) acc[k] += (AccT)__ldcg(row + k * 32);
-                }
-            }
+            const unsigned pend = __ballot_sync(kFull, anym != 0u);
+            pull_window<false>(th(), w, 0, m, pend, acc, [](int) {});
         }
         if (lane == 0) st_scanned += (unsigned long long)(end - beg);
+        if (nseg == 1) {
+            delta_flush(hv, F, acc);
+            return;
+        }
         AccT* prow = reinterpret_cast<AccT*>(a.part) + (size_t)g * B + lane;
 #pragma unroll
         for (int k = 0; k < W; ++k) prow[k * 32] = acc[k];
@@ -635,7 +654,7 @@ struct BatchKernel {
 };
 
 template <int W, typename SigT, typename ThT>
-__global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(BatchArgs a) {
     using K_t = BatchKernel<W, SigT, ThT>;
     constexpr int B = K_t::B;
     constexpr bool kFloatSig = K_t::kFloatSig;
@@ -676,12 +695,14 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs a) {
         const int nb = min(B, a.nsrc - b0);
         // ---- init: sources of this batch at level 0 ----
         K.hoff_next = 0;
+        K.soff_next = 0;
         K.stamp_next = stamp_base;
         K.d = -1;
         if (tid == 0) {
             a.hcnt[1] = 0ull;
             a.eoff[0] = 0;
             a.hoff[0] = 0;
+            a.soff[0] = 0;
         }
         if constexpr (kFloatSig) {
             for (int i = tid; i < B; i += nthr) {
@@ -704,7 +725,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs a) {
 
         // ---- forward ----
         int qb = 0, qe = qsnap;
-        int hoff_d = 0;
+        int hoff_d = 0, soff_d = 0;
         int d = 0;
         while (true) {
             K.d = d;
@@ -714,9 +735,11 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs a) {
             K.stamp_next = stamp_base + d + 1;
             unsigned long long hc = ld_volatile(&a.hcnt[d]);
             K.hoff_d = hoff_d;
+            K.soff_d = soff_d;
             K.nrec_d = (int)(hc >> 32);
             K.nseg_d = (int)(hc & 0xFFFFFFFFull);
             K.hoff_next = hoff_d + K.nrec_d;
+            K.soff_next = soff_d + K.nseg_d;
             if (d + 2 >= a.lcap) { set_error(ctl, kErrCapLevels); }
             if constexpr (kFloatSig) {
 #pragma unroll
@@ -733,6 +756,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs a) {
             if (tid == 0) {
                 a.eoff[d + 1] = qe;
                 a.hoff[d] = hoff_d;
+                a.soff[d] = soff_d;
                 if (d + 2 < a.lcap + 2) a.hcnt[d + 2] = 0ull;
             }
             // clear dense F_{d-2}
@@ -750,6 +774,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs a) {
             if (!sync()) goto out;
             const int nq = qsnap;
             hoff_d = K.hoff_next;
+            soff_d = K.soff_next;
             if (nq == qe) break;
             qb = qe;
             qe = nq;
@@ -765,6 +790,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(BatchArgs a) {
             const int qbd = ld_volatile(&a.eoff[dd]), qed = ld_volatile(&a.eoff[dd + 1]);
             unsigned long long hc = ld_volatile(&a.hcnt[dd]);
             K.hoff_d = ld_volatile(&a.hoff[dd]);
+            K.soff_d = ld_volatile(&a.soff[dd]);
             K.nrec_d = (int)(hc >> 32);
             K.nseg_d = (int)(hc & 0xFFFFFFFFull);
             if constexpr (kFloatSig) {

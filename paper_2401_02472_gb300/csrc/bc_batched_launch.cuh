@@ -14,7 +14,7 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     const Graph* g = L.g;
     const int64_t n = g->n;
     cudaStream_t st = L.stream;
-    const int t_hub = 512, seg = 1024;
+    const int t_hub = 64, seg = 256;
 
     const void* fn;
     if (L.sigma_float)
@@ -32,9 +32,11 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     int64_t ecap_max = n * std::min<int64_t>(B, lcap);
     int64_t ecap = L.entry_cap > 0 ? L.entry_cap : std::max<int64_t>(8 * n, 1 << 16);
     ecap = std::max<int64_t>(1, std::min(ecap, ecap_max));
-    int64_t hcap = L.hub_cap > 0 ? L.hub_cap : (g->nnz / t_hub) * 8 + 1024;
-    int64_t segcap = g->nnz / seg + g->nnz / t_hub + 2;
-    if (hcap > INT32_MAX || segcap > INT32_MAX || ecap > INT32_MAX) return fail(SP_ERR_TOO_LARGE, "batched workspace");
+    int64_t hcap = L.hub_cap > 0 ? L.hub_cap : (g->nnz / t_hub) * 4 + 1024;
+    int64_t segcap = g->nnz / seg + g->nnz / t_hub + 2;              // segments of one level
+    int64_t scap = L.hub_cap > 0 ? 2 * L.hub_cap + 4 * (g->nnz / seg) : 4 * (g->nnz / seg) + hcap;  // all levels
+    if (hcap > INT32_MAX || segcap > INT32_MAX || ecap > INT32_MAX || scap > INT32_MAX)
+        return fail(SP_ERR_TOO_LARGE, "batched workspace");
     const size_t th_size = L.theta_f32 ? 4 : 8;
 
     size_t bytes = 0;
@@ -50,6 +52,8 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     size_t o_emask = take(sizeof(uint32_t) * (size_t)ecap * W);
     size_t o_eoff = take(sizeof(int32_t) * (size_t)(lcap + 2));
     size_t o_hoff = take(sizeof(int32_t) * (size_t)(lcap + 2));
+    size_t o_soff = take(sizeof(int32_t) * (size_t)(lcap + 2));
+    size_t o_segrec = take(sizeof(int32_t) * (size_t)scap);
     size_t o_hcnt = take(sizeof(unsigned long long) * (size_t)(lcap + 2));
     size_t o_hubs = take(sizeof(HubRec) * (size_t)hcap);
     size_t o_hdone = take(sizeof(int32_t) * 2 * (size_t)hcap);
@@ -85,6 +89,9 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.hubs = reinterpret_cast<HubRec*>(ws + o_hubs);
     a.hcap = (int32_t)hcap;
     a.hoff = reinterpret_cast<int32_t*>(ws + o_hoff);
+    a.soff = reinterpret_cast<int32_t*>(ws + o_soff);
+    a.segrec = reinterpret_cast<int32_t*>(ws + o_segrec);
+    a.scap = (int32_t)scap;
     a.hcnt = reinterpret_cast<unsigned long long*>(ws + o_hcnt);
     a.hdone = reinterpret_cast<int32_t*>(ws + o_hdone);
     a.part = ws + o_part;

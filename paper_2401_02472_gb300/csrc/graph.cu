@@ -20,24 +20,32 @@ struct ValidateOut {
     int duplicates;
     int asymmetric;        // 1 if some arc has no reverse (symmetric check only)
     unsigned long long isolated;
+    unsigned long long top;  // (max degree << 32) | ~vertex: the smallest-id vertex of maximum degree
 };
 
 __global__ void rowptr_kernel(const int32_t* __restrict__ rp, int32_t n, int64_t nnz, ValidateOut* out) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     int maxdeg = 0;
-    unsigned long long iso = 0;
+    unsigned long long iso = 0, top = 0;
     for (; v < n; v += gridDim.x * blockDim.x) {
         int a = rp[v], b = rp[v + 1];
         if (b < a || a < 0 || (int64_t)b > nnz) atomicMin(&out->bad_rowptr, v);
         int dg = b - a;
         maxdeg = max(maxdeg, dg);
         iso += dg == 0;
+        unsigned long long key = ((unsigned long long)(unsigned)max(dg, 0) << 32) | (unsigned)(~(unsigned)v);
+        top = key > top ? key : top;
     }
     maxdeg = warp_max_i32(maxdeg);
     iso = warp_sum_u64(iso);
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = shfl_u64(kFull, top, lane_id() ^ o);
+        top = y > top ? y : top;
+    }
     if ((threadIdx.x & 31) == 0) {
         atomicMax(&out->max_degree, maxdeg);
         atomicAdd(&out->isolated, iso);
+        atomicMax(&out->top, top);
     }
 }
 
@@ -140,6 +148,7 @@ sp_status validate_graph(Graph* g, uint32_t flags, cudaStream_t st, std::string*
     g->info.n = g->n;
     g->info.nnz = g->nnz;
     g->info.max_degree = h.max_degree;
+    g->top_vertex = g->n > 0 ? (int32_t)(~(unsigned)(h.top & 0xFFFFFFFFull)) : 0;
     g->info.isolated = (int64_t)h.isolated;
     g->info.sorted_rows = h.unsorted ? 0 : 1;
     g->info.has_self_loops = h.self_loops;

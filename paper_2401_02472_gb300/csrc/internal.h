@@ -27,6 +27,8 @@ struct Graph {
     int* err_latch_dev = nullptr;
     std::mutex mu;
     bool sigma_float = false;  // path counts of this graph overflowed 64-bit integers before
+    int32_t top_vertex = 0;     // a vertex of maximum degree
+    int32_t* d_top_dist = nullptr;  // BFS distances from top_vertex (computed on first use)
 };
 
 // Thread-local error text.

@@ -226,6 +226,22 @@ def test_run_to_run_bit_identical(form, batch):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
+def test_source_order_only_changes_rounding(precision):
+    # The batched form regroups sources by distance from a maximum-degree
+    # vertex; with SP_BC_KEEP_ORDER it keeps the caller's order.  Both are BC
+    # over the same multiset, so they agree within the tolerance, and the
+    # regrouped run is the same for any permutation of the caller's list.
+    g, G = graph("rmat12")
+    srcs = gen.sources(g, 150, 21)
+    a, _ = gpu_bc(G, srcs, precision, sp.SP_FORM_BATCHED, 64)
+    b, _ = gpu_bc(G, srcs, precision, sp.SP_FORM_BATCHED, 64, flags=sp.SP_BC_KEEP_ORDER)
+    assert_bc_close(a, b, RTOL[precision])
+    c, _ = gpu_bc(G, srcs[::-1].copy(), precision, sp.SP_FORM_BATCHED, 64)
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(c, want, RTOL[precision])
+
+
 def test_linearity_over_calls():
     g, G = graph("knn5000")
     s1, s2 = gen.sources(g, 40, 1), gen.sources(g, 70, 2)
