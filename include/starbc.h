@@ -177,6 +177,26 @@ SP_API sp_status sp_bfs(sp_graph g, const int32_t* sources, int32_t nsrc, int32_
  */
 SP_API sp_status sp_sigma(sp_graph g, int32_t src, double* mant_out, int64_t* exp2_out, sp_stream stream);
 
+/*
+ * BC for callers that cannot allocate device memory (the paper has no
+ * counterpart: this entry point exists for callers such as threads of a
+ * framework that owns all device memory, real-time or serving loops that
+ * must not call an allocator mid-run, and runtimes with a fixed memory plan).
+ * It runs the plain form with all of its scratch in one static device array
+ * of about 16 MB, reserved on every GPU that loads the library until the
+ * process exits, and calls no allocator.
+ *   row_ptr[n+1], col_idx[nnz], sources[nsrc], bc_out[n]: device memory of
+ *   the current device; the same CSR rules as sp_graph_create, checked on
+ *   the GPU.  n <= 262144 and nnz <= 16777216, else SP_ERR_TOO_LARGE.
+ *   bc_out is overwritten.  The call returns when the result is complete.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call uses
+ * the same array, so calls that overlap on the GPU (other streams or host
+ * threads) race and must be serialised by the caller.
+ */
+SP_API sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
+                               const int32_t* sources, int32_t nsrc, double* bc_out, sp_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of BC requests over resident graphs          */
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "sp_bc_ex": ([_P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "sp_bfs": ([_P, _P, _I32, _P, _P], ctypes.c_int),
     "sp_sigma": ([_P, _I32, _P, _P, _P], ctypes.c_int),
+    "sp_bc_noalloc": ([_P, _P, _I32, _I64, _P, _I32, _P, _P], ctypes.c_int),
     "sp_server_create": ([_SZ, _I32, _P], ctypes.c_int),
     "sp_server_add_graph": ([_P, _P, _P], ctypes.c_int),
     "sp_bc_submit": ([_P, _I32, _P, _I32, _P, _P, _P], ctypes.c_int),
@@ -213,6 +214,18 @@ def sp_sigma(g: int, src: int, mant_out, exp2_out, stream=None):
     _check_dtype(mant_out, "float64", "mant_out")
     _check_dtype(exp2_out, "int64", "exp2_out")
     _check(lib.sp_sigma(g, int(src), _ptr(mant_out), _ptr(exp2_out), _stream(stream)), "sp_sigma")
+
+
+def sp_bc_noalloc(row_ptr, col_idx, sources, bc_out, n: int | None = None, nnz: int | None = None, stream=None):
+    """BC with no device allocation; every array must be device memory (see include/starbc.h)."""
+    _check_dtype(row_ptr, "int32", "row_ptr")
+    _check_dtype(col_idx, "int32", "col_idx")
+    _check_dtype(sources, "int32", "sources")
+    _check_dtype(bc_out, "float64", "bc_out")
+    n = _count(row_ptr) - 1 if n is None else n
+    nnz = _count(col_idx) if nnz is None else nnz
+    _check(lib.sp_bc_noalloc(_ptr(row_ptr), _ptr(col_idx), n, nnz, _ptr(sources), _count(sources), _ptr(bc_out),
+                             _stream(stream)), "sp_bc_noalloc")
 
 
 def sp_server_create(hbm_budget_bytes: int, max_slots: int) -> int:

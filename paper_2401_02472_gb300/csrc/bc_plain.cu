@@ -1,31 +1,4 @@
-// Plain form: one source at a time, all of the GPU on it.
-//
-// Per source (paper Section 2, Fig. 1, ComputeBC; the level-synchronous BFS of
-// Section 3.3) one persistent cooperative launch runs
-//   init      level[] = -1, level[src] = 0, sigma[src] = 1
-//   forward   for d = 0, 1, ...: every vertex v at level d pulls sigma from its
-//             neighbours at level d-1 (the iterateInBFS sum over BFS parents)
-//             and claims its unvisited neighbours for level d+1 in the same
-//             adjacency scan; the level stack Q holds the levels in order
-//   backward  for d = L-1 ... 1: v pulls theta(w) = (1 + delta(w)) / sigma(w)
-//             from its neighbours at level d+1, then delta(v) = sigma(v) * sum,
-//             BC(v) += delta(v) (the iterateInReverse sum over BFS children,
-//             written so that no floating-point atomics are needed)
-// with a timed grid barrier between levels instead of the paper's host loop
-// that copies a `finished` flag every level (Section 3.3; Section 4.1).
-//
-// Work distribution inside a level: entries of Q are taken 32 at a time by a
-// warp; rows of at most t_thread arcs are walked by one lane, longer rows by
-// the whole warp, and rows longer than t_hub (hubs) are split into segments of
-// `seg` arcs taken by different warps, whose partial sums the last segment to
-// finish adds in segment order.  Every per-vertex sum therefore has an order
-// fixed by the graph alone: results are bit-identical from run to run.
-//
-// Path counts: exact unsigned 64-bit integer sums (identical to FP64 sums while
-// counts stay below 2^53), or, when counts overflow 64 bits, FP64 values with a
-// power-of-two exponent per level (recentred when the level strays from 2^0).
-#include <cooperative_groups.h>
-
+// Host launcher of the plain form (kernel in bc_plain_kernel.cuh).
 #include <climits>
 #include <type_traits>
 
@@ -34,456 +7,9 @@
 #include <vector>
 #include <string>
 
-#include "common.cuh"
-#include "internal.h"
+#include "bc_plain_kernel.cuh"
 
 namespace sp {
-
-constexpr int kPlainThreads = 512;
-
-struct PlainArgs {
-    const int32_t* rp;
-    const int32_t* ci;
-    int32_t n;
-    const int32_t* sources;
-    int32_t nsrc;
-    double* bc;
-    int32_t* lvl;
-    void* sig;
-    void* th;
-    int32_t* q;             // level stack, n entries
-    int32_t* qoff;          // [n+2]
-    HubRec* hubs;
-    int32_t hcap;
-    int32_t* hoff;          // [n+2]
-    unsigned long long* hcnt;  // [n+2]: records << 32 | segments, per level
-    int32_t* hdone;         // [2*hcap]: forward / backward finish counters
-    double* part;           // [segcap] per-segment partial sums (8-byte slots)
-    int32_t segcap;
-    int32_t* emax;          // [n+2] per-level exponent range of scaled sigma
-    int32_t* emin;          // [n+2]
-    long long* fexp;        // [n+2] cumulative exponent per level (sigma output)
-    Ctl* ctl;
-    int* err_latch;
-    int32_t* dist_out;
-    double* mant_out;
-    long long* exp_out;
-    int mode;
-    int debug_flags;
-    unsigned long long timeout_ns;
-    int t_thread, t_hub, seg;
-    int* trace;  // SP_TRACE builds: 8 ints per warp
-};
-
-template <typename SigT>
-struct SigOps;
-template <>
-struct SigOps<unsigned long long> {
-    static __device__ __forceinline__ unsigned long long add(unsigned long long a, unsigned long long b, bool& ovf) {
-        unsigned long long s = a + b;
-        ovf |= s < a;
-        return s;
-    }
-    static __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v, bool& ovf) {
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long y = shfl_u64(kFull, v, lane_id() ^ o);
-            v = add(v, y, ovf);
-        }
-        return v;
-    }
-};
-template <>
-struct SigOps<double> {
-    static __device__ __forceinline__ double add(double a, double b, bool&) { return a + b; }
-    static __device__ __forceinline__ double warp_sum(double v, bool&) { return warp_sum_f64(v); }
-};
-
-template <typename SigT, typename ThT>
-struct PlainKernel {
-    const PlainArgs& a;
-    Ctl* ctl;
-    int lane;
-    // per-level state (identical in every thread)
-    int d = 0;
-    int hoff_d = 0, nrec_d = 0, nseg_d = 0;  // hub records of level d
-    int hoff_next = 0;                       // first hub record of level d+1
-    int cshift_prev = 0;                     // centring shift between level d-1 and d
-    int cshift_cur = 0;                      // centring shift between level d and d+1 (backward)
-    // per-thread accumulators
-    int my_emax = INT_MIN, my_emin = INT_MAX;
-    bool ovf = false;
-    unsigned long long st_arcs = 0, st_reached = 0, st_scanned = 0, st_dag = 0;
-
-    __device__ PlainKernel(const PlainArgs& args) : a(args), ctl(args.ctl), lane(lane_id()) {}
-
-    __device__ __forceinline__ SigT* sig() const { return reinterpret_cast<SigT*>(a.sig); }
-    __device__ __forceinline__ ThT* th() const { return reinterpret_cast<ThT*>(a.th); }
-
-    // A vertex claimed for level `nl`: append to the level stack (and the hub list).
-    __device__ void push(int u, int nl) {
-        int du = __ldg(&a.rp[u + 1]) - __ldg(&a.rp[u]);
-        bool hub = du > a.t_hub;
-        int pos = aggregated_slot(&ctl->qtail);
-        if (pos >= a.n) { set_error(ctl, kErrCapacity); return; }
-        a.q[pos] = hub ? (int)((unsigned)u | kHubFlag) : u;
-        if (hub) {
-            int nseg = (du + a.seg - 1) / a.seg;
-            unsigned long long old = atomicAdd(&a.hcnt[nl], (1ull << 32) | (unsigned long long)(unsigned)nseg);
-            int rec = hoff_next + (int)(old >> 32);
-            int sb = (int)(old & 0xFFFFFFFFull);
-            if (rec >= a.hcap || sb + nseg > a.segcap) { set_error(ctl, kErrCapacity); return; }
-            HubRec h;
-            h.v = u; h.qpos = pos; h.nseg = nseg; h.seg_base = sb;
-            a.hubs[rec] = h;
-            a.hdone[rec] = 0;
-            a.hdone[a.hcap + rec] = 0;
-        }
-    }
-
-    // Forward visit of arc (v, u) by a vertex v at level d.
-    __device__ __forceinline__ SigT fwd_arc(int u) {
-        int lu = __ldcg(&a.lvl[u]);
-        SigT c = 0;
-        if (lu < 0) {
-            if (atomicCAS(&a.lvl[u], -1, d + 1) == -1) push(u, d + 1);
-        } else if (lu == d - 1) {
-            c = __ldcg(&sig()[u]);
-            st_dag += 1;
-        }
-        return c;
-    }
-
-    __device__ void fwd_finalize(int v, SigT acc, int deg) {
-        st_arcs += (unsigned long long)deg;
-        st_reached += 1;
-        if (d == 0) return;  // sigma[src] = 1 was set by the init phase
-        if constexpr (std::is_integral<SigT>::value) {  // integer path counts
-            sig()[v] = acc;
-        } else {
-            double val = scale2((double)acc, -cshift_prev);
-            if (!normal_finite(val)) set_error(ctl, SP_ERR_RANGE);
-            sig()[v] = (SigT)val;
-            int e = exp_field(val) - 1023;
-            my_emax = max(my_emax, e);
-            my_emin = min(my_emin, e);
-        }
-    }
-
-    __device__ __forceinline__ double bwd_arc(int w) {
-        int lw = __ldcg(&a.lvl[w]);
-        return lw == d + 1 ? (double)__ldcg(&th()[w]) : 0.0;
-    }
-
-    __device__ void bwd_finalize(int v, double acc) {
-        double sv = (double)__ldcg(&sig()[v]);
-        double delta = sv * acc;
-        if constexpr (!std::is_integral<SigT>::value) delta = scale2(delta, -cshift_cur);
-        double t = (1.0 + delta) / sv;
-        if constexpr (sizeof(ThT) == 4) {
-            float tf = (float)t;
-            if (!normal_finite_f(tf)) set_error(ctl, kErrThetaRange32);
-            th()[v] = (ThT)tf;
-        } else {
-            if (!normal_finite(t)) set_error(ctl, SP_ERR_RANGE);
-            th()[v] = (ThT)t;
-        }
-        a.bc[v] = __ldcg(&a.bc[v]) + delta;
-    }
-
-    // One chunk of 32 level-stack entries starting at index e0 (< qe).
-    template <bool FWD>
-    __device__ void chunk(int e0, int qe, bool skip_arcs) {
-        int e = e0 + lane;
-        bool valid = e < qe;
-        unsigned qv = valid ? (unsigned)__ldcg(&a.q[e]) : kHubFlag;
-        bool hubent = (qv & kHubFlag) != 0;
-        int v = (int)(qv & kVertexMask);
-        if (valid && v >= a.n) { set_error(ctl, kErrCorrupt); valid = false; hubent = true; v = 0; }
-        int beg = 0, deg = 0;
-        if (!hubent) {
-            beg = __ldg(&a.rp[v]);
-            deg = __ldg(&a.rp[v + 1]) - beg;
-        }
-        int walk = skip_arcs ? 0 : deg;
-        SigT sacc = 0;
-        double tacc = 0.0;
-        if (walk <= a.t_thread) {
-            for (int k = 0; k < walk; ++k) {
-                int u = __ldg(&a.ci[beg + k]);
-                if constexpr (FWD) sacc = SigOps<SigT>::add(sacc, fwd_arc(u), ovf);
-                else tacc += bwd_arc(u);
-            }
-        }
-        unsigned big = __ballot_sync(kFull, walk > a.t_thread);
-        while (big) {
-            int j = __ffs(big) - 1;
-            big &= big - 1;
-            int bj = __shfl_sync(kFull, beg, j), dj = __shfl_sync(kFull, deg, j);
-            SigT sp_ = 0;
-            double tp = 0.0;
-            for (int k = lane; k < dj; k += kWarp) {
-                int u = __ldg(&a.ci[bj + k]);
-                if constexpr (FWD) sp_ = SigOps<SigT>::add(sp_, fwd_arc(u), ovf);
-                else tp += bwd_arc(u);
-            }
-            if constexpr (FWD) {
-                sp_ = SigOps<SigT>::warp_sum(sp_, ovf);
-                if (lane == j) sacc = sp_;
-            } else {
-                tp = warp_sum_f64(tp);
-                if (lane == j) tacc = tp;
-            }
-        }
-        if (valid && !hubent) {
-            st_scanned += (unsigned long long)walk;
-            if constexpr (FWD) fwd_finalize(v, sacc, deg);
-            else bwd_finalize(v, tacc);
-        }
-    }
-
-    // Segment g of the hubs of level d.
-    template <bool FWD>
-    __device__ void hub_segment(int g, bool skip_arcs) {
-        int r = find_hub(a.hubs, hoff_d, hoff_d + nrec_d, g);
-        HubRec h;
-        h.v = __ldcg(&a.hubs[r].v);
-        h.nseg = __ldcg(&a.hubs[r].nseg);
-        h.seg_base = __ldcg(&a.hubs[r].seg_base);
-        if (h.v < 0 || h.v >= a.n || h.nseg < 1 || h.seg_base < 0 || h.seg_base + h.nseg > a.segcap) {
-            if (lane == 0) set_error(ctl, kErrCorrupt);
-            return;
-        }
-        int s = g - h.seg_base;
-        int rb = __ldg(&a.rp[h.v]), re = __ldg(&a.rp[h.v + 1]);
-        int beg = rb + s * a.seg;
-        int end = min(re, beg + a.seg);
-        if (skip_arcs) end = beg;
-        SigT sp_ = 0;
-        double tp = 0.0;
-        for (int k = beg + lane; k < end; k += kWarp) {
-            int u = __ldg(&a.ci[k]);
-            if constexpr (FWD) sp_ = SigOps<SigT>::add(sp_, fwd_arc(u), ovf);
-            else tp += bwd_arc(u);
-        }
-        if (lane == 0) st_scanned += (unsigned long long)(end - beg);
-        int* done = FWD ? &a.hdone[r] : &a.hdone[a.hcap + r];
-        int old = 0;
-        if constexpr (FWD) {
-            sp_ = SigOps<SigT>::warp_sum(sp_, ovf);
-            if (lane == 0) reinterpret_cast<SigT*>(a.part)[g] = sp_;
-        } else {
-            tp = warp_sum_f64(tp);
-            if (lane == 0) a.part[g] = tp;
-        }
-        if (lane == 0) {
-            __threadfence();
-            old = atomicAdd(done, 1);
-        }
-        old = __shfl_sync(kFull, old, 0);
-        if (old != h.nseg - 1) return;
-        __threadfence();
-        // Last segment: add the partial sums in segment order.
-        SigT st = 0;
-        double tt = 0.0;
-        for (int k = lane; k < h.nseg; k += kWarp) {
-            if constexpr (FWD) st = SigOps<SigT>::add(st, __ldcg(&reinterpret_cast<SigT*>(a.part)[h.seg_base + k]), ovf);
-            else tt += __ldcg(&a.part[h.seg_base + k]);
-        }
-        if constexpr (FWD) {
-            st = SigOps<SigT>::warp_sum(st, ovf);
-            if (lane == 0) fwd_finalize(h.v, st, re - rb);
-        } else {
-            tt = warp_sum_f64(tt);
-            if (lane == 0) bwd_finalize(h.v, tt);
-        }
-    }
-
-    template <bool FWD>
-    __device__ void level_work(int phase, int qb, int qe, bool skip_arcs) {
-        int nchunks = (qe - qb + kWarp - 1) / kWarp;
-        int total = nseg_d + nchunks;
-        while (true) {
-            int item = 0;
-            if (lane == 0) item = (int)atomicAdd(&ctl->work[phase & 3], 1u);
-            item = __shfl_sync(kFull, item, 0);
-#ifdef SP_TRACE
-            if (lane == 0 && a.trace) {
-                int* t = a.trace + 8 * ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-                t[0] = phase; t[1] = item; t[2] = total; t[3] = nseg_d; t[4] = qb; t[5] = qe; t[6] = d; t[7] += 1;
-            }
-#endif
-            if (item >= total) break;
-            if (item < nseg_d) hub_segment<FWD>(item, skip_arcs);
-            else chunk<FWD>(qb + (item - nseg_d) * kWarp, qe, skip_arcs);
-        }
-    }
-};
-
-template <typename SigT, typename ThT>
-__global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
-    constexpr bool kFloatSig = !std::is_integral<SigT>::value;
-    PlainKernel<SigT, ThT> K(a);
-    Ctl* ctl = a.ctl;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthr = gridDim.x * blockDim.x;
-    const int n = a.n;
-    int phase = 0;
-    int qsnap = 0;  // level-stack fill at the last barrier
-    int levels_max = 0;
-    // Barrier between phases; the work counter of phase p+2 is cleared in phase p.
-    auto sync = [&]() -> bool {
-        bool skip = (a.debug_flags & SP_DEBUG_SKIP_BARRIER) && blockIdx.x == 0 && phase == 1;
-        bool ok = grid_sync(ctl, gridDim.x, a.timeout_ns, phase++, skip, &qsnap);
-        if (tid == 0) ctl->work[(phase + 2) & 3] = 0u;
-        return ok;
-    };
-
-    if (a.mode == (int)PlainMode::BC)
-        for (int i = tid; i < n; i += nthr) a.bc[i] = 0.0;
-    if (!sync()) goto out;
-
-    for (int si = 0; si < a.nsrc; ++si) {
-        const int src = __ldg(&a.sources[si]);
-        // ---- init ----
-        for (int i = tid; i < n; i += nthr) a.lvl[i] = (i == src) ? 0 : -1;
-        if (tid == 0) {
-            int du = a.rp[src + 1] - a.rp[src];
-            a.q[0] = src;
-            ctl->qtail = 1;
-            a.qoff[0] = 0;
-            a.hoff[0] = 0;
-            a.hcnt[0] = 0ull;
-            a.hcnt[1] = 0ull;
-            a.emax[0] = 0;
-            a.emin[0] = 0;
-            reinterpret_cast<SigT*>(a.sig)[src] = (SigT)1;
-            if (du > a.t_hub) {
-                int nseg = (du + a.seg - 1) / a.seg;
-                if (a.hcap < 1 || nseg > a.segcap) set_error(ctl, kErrCapacity);
-                else {
-                    a.q[0] = (int)((unsigned)src | kHubFlag);
-                    HubRec h;
-                    h.v = src; h.qpos = 0; h.nseg = nseg; h.seg_base = 0;
-                    a.hubs[0] = h;
-                    a.hdone[0] = 0;
-                    a.hdone[a.hcap] = 0;
-                    a.hcnt[0] = (1ull << 32) | (unsigned long long)nseg;
-                }
-            }
-        }
-        if (!sync()) goto out;
-
-        // ---- forward ----
-        int qb = 0, qe = 1;
-        K.d = 0;
-        K.hoff_d = 0;
-        while (true) {
-                const int d = K.d;
-            unsigned long long hc = ld_volatile(&a.hcnt[d]);
-            K.nrec_d = (int)(hc >> 32);
-            K.nseg_d = (int)(hc & 0xFFFFFFFFull);
-            K.hoff_next = K.hoff_d + K.nrec_d;
-            if constexpr (kFloatSig) {
-                K.cshift_prev = d > 0 ? centre_shift(ld_volatile(&a.emax[d - 1]), ld_volatile(&a.emin[d - 1])) : 0;
-            }
-            if (tid == 0) {
-                a.qoff[d + 1] = qe;
-                a.hoff[d] = K.hoff_d;
-                a.hcnt[d + 2] = 0ull;
-                a.emax[d + 1] = INT_MIN;
-                a.emin[d + 1] = INT_MAX;
-            }
-            K.my_emax = INT_MIN;
-            K.my_emin = INT_MAX;
-            K.template level_work<true>(phase, qb, qe, false);
-            if constexpr (kFloatSig) {
-                int mx = warp_max_i32(K.my_emax), mn = warp_min_i32(K.my_emin);
-                if (K.lane == 0 && mx >= mn) {
-                    atomicMax(&a.emax[d], mx);
-                    atomicMin(&a.emin[d], mn);
-                }
-            }
-            if (K.ovf && a.mode != (int)PlainMode::BFS) set_error(ctl, kErrSigmaOverflow);
-            if (!sync()) goto out;
-            int nq = qsnap;
-            K.hoff_d = K.hoff_next;
-            if (nq == qe) break;
-            qb = qe;
-            qe = nq;
-            K.d = d + 1;
-        }
-        const int L = K.d + 1;
-        levels_max = max(levels_max, L);
-
-        if (a.mode == (int)PlainMode::BFS) {
-            int* row = a.dist_out + (size_t)si * (size_t)n;
-            for (int i = tid; i < n; i += nthr) row[i] = __ldcg(&a.lvl[i]);
-            if (!sync()) goto out;
-            continue;
-        }
-        if (a.mode == (int)PlainMode::SIGMA) {
-            if (tid == 0) {
-                long long f = 0;
-                for (int l = 0; l < L; ++l) {
-                    a.fexp[l] = f;
-                    if constexpr (kFloatSig) f += centre_shift(a.emax[l], a.emin[l]);
-                }
-            }
-            if (!sync()) goto out;
-            for (int i = tid; i < n; i += nthr) {
-                int l = __ldcg(&a.lvl[i]);
-                double m = 0.0;
-                long long e2 = 0;
-                if (l >= 0) {
-                    double s = (double)__ldcg(&reinterpret_cast<SigT*>(a.sig)[i]);
-                    int e = exp_field(s) - 1023;
-                    m = scale2(s, -e);
-                    e2 = (long long)e + __ldcg(&a.fexp[l]);
-                }
-                a.mant_out[i] = m;
-                a.exp_out[i] = e2;
-            }
-            if (!sync()) goto out;
-            continue;
-        }
-
-        // ---- backward ----
-        for (int d = L - 1; d >= 1; --d) {
-                K.d = d;
-            int qbd = ld_volatile(&a.qoff[d]);
-            int qed = ld_volatile(&a.qoff[d + 1]);
-            unsigned long long hc = ld_volatile(&a.hcnt[d]);
-            K.hoff_d = ld_volatile(&a.hoff[d]);
-            K.nrec_d = (int)(hc >> 32);
-            K.nseg_d = (int)(hc & 0xFFFFFFFFull);
-            if constexpr (kFloatSig) K.cshift_cur = centre_shift(ld_volatile(&a.emax[d]), ld_volatile(&a.emin[d]));
-            K.template level_work<false>(phase, qbd, qed, d == L - 1);
-            if (!sync()) goto out;
-        }
-    }
-
-out:
-    {
-        // statistics: block-level then one atomic per block
-        __shared__ unsigned long long s_st[4];
-        if (threadIdx.x == 0) { s_st[0] = 0; s_st[1] = 0; s_st[2] = 0; s_st[3] = 0; }
-        __syncthreads();
-        atomicAdd(&s_st[0], K.st_arcs);
-        atomicAdd(&s_st[1], K.st_reached);
-        atomicAdd(&s_st[2], K.st_scanned);
-        atomicAdd(&s_st[3], K.st_dag);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            atomicAdd(&ctl->traversed_arcs, s_st[0]);
-            atomicAdd(&ctl->reached, s_st[1]);
-            atomicAdd(&ctl->scanned_arcs, s_st[2]);
-            atomicAdd(&ctl->dag_arcs, s_st[3]);
-            atomicMax(&ctl->max_levels, levels_max);
-            int e = ld_volatile(&ctl->err);
-            if (e != 0 && a.err_latch) *(volatile int*)a.err_latch = e;
-        }
-    }
-}
 
 template <typename SigT, typename ThT>
 static const void* plain_fn() {
