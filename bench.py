@@ -208,6 +208,11 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     w, g, srcs = workload_inputs(args.workload, rank)
+    w = dict(w)
+    if args.form:
+        w["form"] = args.form
+    if args.nsrc:
+        srcs = srcs[:args.nsrc]
     prec = sp.SP_FP32_DELTA if w["precision"] == "fp32_delta" else sp.SP_FP64
     form = sp.SP_FORM_BATCHED if w["form"] == "batched" else sp.SP_FORM_PLAIN
     opts = sp.make_opts(precision=prec, form=form, batch=args.batch)
@@ -337,6 +342,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=0, help="fixed batch width (0 = autotuned)")
+    ap.add_argument("--form", default=None, choices=["plain", "batched"], help="override the workload's form")
+    ap.add_argument("--nsrc", type=int, default=0, help="override the workload's source count")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

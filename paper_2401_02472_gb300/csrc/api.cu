@@ -232,35 +232,52 @@ __global__ void source_keys_kernel(const int32_t* __restrict__ src, int32_t nsrc
 
 // A copy of the call's sources in key order (stable), or nullptr to keep the
 // caller's order (a single source, or the plain form).
+// Hop distances from a maximum-degree vertex (one plain-form BFS per graph,
+// kept with the graph): they key the source regrouping, and their largest
+// value estimates the diameter, which sizes the plain form's block groups.
+static sp_status ensure_top_bfs(Graph* g, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->d_top_dist || g->n == 0) return SP_OK;
+    int32_t* d_dist = nullptr;
+    int32_t* d_one = nullptr;
+    SP_CUDA(cudaMalloc((void**)&d_dist, sizeof(int32_t) * (size_t)g->n));
+    SP_CUDA(cudaMallocAsync((void**)&d_one, sizeof(int32_t), st));
+    SP_CUDA(cudaMemcpyAsync(d_one, &g->top_vertex, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    PlainLaunch L{};
+    L.g = g;
+    L.d_sources = d_one;
+    L.nsrc = 1;
+    L.d_dist = d_dist;
+    L.mode = PlainMode::BFS;
+    L.timeout_ns = bfs_timeout_ns();
+    L.stream = st;
+    LaunchResult r;
+    sp_status rc = run_plain(L, &r);
+    cudaFreeAsync(d_one, st);
+    if (rc == SP_OK) rc = map_device_error(r.err, "eccentricity BFS", r.diag);
+    if (rc != SP_OK) {
+        cudaFree(d_dist);
+        return rc;
+    }
+    g->d_top_dist = d_dist;
+    g->top_levels = r.levels;
+    return SP_OK;
+}
+
+// Blocks per group of the plain form: about 8,192 arcs of an average level
+// per block, from the estimated number of levels.
+static int plain_group_blocks(const Graph* g) {
+    const int64_t levels = std::max<int64_t>(1, g->top_levels);
+    const int64_t per_level = std::max<int64_t>(1, g->nnz / levels);
+    return (int)std::min<int64_t>((per_level + 8191) / 8192, 1 << 20);
+}
+
 static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cudaStream_t st, int32_t** out) {
     *out = nullptr;
     if (nsrc < 2 || g->n == 0) return SP_OK;
     {
-        std::lock_guard<std::mutex> lk(g->mu);
-        if (!g->d_top_dist) {
-            int32_t* d_dist = nullptr;
-            int32_t* d_one = nullptr;
-            SP_CUDA(cudaMalloc((void**)&d_dist, sizeof(int32_t) * (size_t)g->n));
-            SP_CUDA(cudaMallocAsync((void**)&d_one, sizeof(int32_t), st));
-            SP_CUDA(cudaMemcpyAsync(d_one, &g->top_vertex, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-            PlainLaunch L{};
-            L.g = g;
-            L.d_sources = d_one;
-            L.nsrc = 1;
-            L.d_dist = d_dist;
-            L.mode = PlainMode::BFS;
-            L.timeout_ns = bfs_timeout_ns();
-            L.stream = st;
-            LaunchResult r;
-            sp_status rc = run_plain(L, &r);
-            cudaFreeAsync(d_one, st);
-            if (rc == SP_OK) rc = map_device_error(r.err, "source ordering", r.diag);
-            if (rc != SP_OK) {
-                cudaFree(d_dist);
-                return rc;
-            }
-            g->d_top_dist = d_dist;
-        }
+        sp_status rc = ensure_top_bfs(g, st);
+        if (rc != SP_OK) return rc;
     }
     unsigned long long* d_keys = nullptr;
     SP_CUDA(cudaMallocAsync((void**)&d_keys, sizeof(unsigned long long) * (size_t)nsrc, st));
@@ -301,8 +318,18 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         sigma_float = g->sigma_float;
     }
     bool theta_f32 = o.precision == SP_FP32_DELTA;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (g->theta_f64) theta_f32 = false;
+    }
+    {
+        sp_status rc = ensure_top_bfs(g, st);
+        if (rc != SP_OK) return rc;
+    }
     int form = o.form;
-    if (form == SP_FORM_AUTO) form = nsrc >= 16 ? SP_FORM_BATCHED : SP_FORM_PLAIN;
+    // Automatic form: many narrow levels (high diameter) favour small block
+    // groups, one source each; wide levels and many sources favour batches.
+    if (form == SP_FORM_AUTO) form = (nsrc >= 16 && g->top_levels <= 64) ? SP_FORM_BATCHED : SP_FORM_PLAIN;
     int width = 1, launches = 0, tuned = 0;
     if (form == SP_FORM_BATCHED) {
         if (o.batch > 0) {
@@ -339,7 +366,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         ~FreeSorted() { if (p) cudaFreeAsync(p, s); }
     } free_sorted{d_sorted, st};
     int promoted = 0, sigma_batches = 0;
-    int64_t ecap = 0, hcap = 0, lcap = 0;
+    int64_t ecap = 0, hcap = 0, lcap = 0, plain_lcap = 0;
     double kernel_ms = 0.0;
     LaunchResult r;
     for (int attempt = 0; attempt < 16; ++attempt) {
@@ -358,6 +385,8 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             L.timeout_ns = timeout_of(o);
             L.debug_flags = o.debug_flags;
             L.stream = st;
+            L.group_blocks = plain_group_blocks(g);
+            L.level_cap = plain_lcap;
             rc = run_plain(L, &r);
         } else {
             BatchedLaunch L{};
@@ -390,6 +419,12 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         if (r.err == kErrThetaRange32 && theta_f32) {
             theta_f32 = false;
             promoted = 1;
+            std::lock_guard<std::mutex> lk(g->mu);
+            g->theta_f64 = true;
+            continue;
+        }
+        if (form == SP_FORM_PLAIN && r.err == kErrCapLevels && r.lcap < (int64_t)g->n + 2) {
+            plain_lcap = (int64_t)g->n + 2;
             continue;
         }
         if (form == SP_FORM_BATCHED) {
@@ -411,7 +446,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         stats->batch = width;
         stats->batches = form == SP_FORM_PLAIN ? nsrc : (nsrc + width - 1) / width;
         stats->form = form;
-        stats->promoted = promoted;
+        stats->promoted = promoted || (o.precision == SP_FP32_DELTA && !theta_f32);
         stats->sigma_float = sigma_float ? 1 : sigma_batches;
         stats->dag_arcs = (int64_t)r.dag_arcs;
         stats->kernel_ms = kernel_ms;
@@ -597,8 +632,17 @@ sp_status sp_bfs(sp_graph gh, const int32_t* sources, int32_t nsrc, int32_t* dis
         L.theta_f32 = false;
         L.timeout_ns = bfs_timeout_ns();
         L.stream = st;
+        rc = ensure_top_bfs(g, st);
+        L.group_blocks = plain_group_blocks(g);
         LaunchResult r;
-        rc = run_plain(L, &r);
+        for (int attempt = 0; rc == SP_OK && attempt < 2; ++attempt) {
+            rc = run_plain(L, &r);
+            if (rc == SP_OK && r.err == kErrCapLevels && L.level_cap < (int64_t)g->n + 2) {
+                L.level_cap = (int64_t)g->n + 2;
+                continue;
+            }
+            break;
+        }
         if (rc == SP_OK) rc = map_device_error(r.err, "bfs", r.diag);
     }
     if (rc == SP_OK && host_out) {

@@ -46,7 +46,8 @@ constexpr int kNone = 0x7F7F7F7F;
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t kOffCtl = 0;
-constexpr size_t kOffCheck = kOffCtl + align256(sizeof(Ctl));
+constexpr size_t kOffGctl = kOffCtl + align256(sizeof(Ctl));
+constexpr size_t kOffCheck = kOffGctl + align256(sizeof(GroupCtl));
 constexpr size_t kOffLvl = kOffCheck + align256(sizeof(NoallocCheck));
 constexpr size_t kOffSig = kOffLvl + align256(4 * kNoallocMaxN);
 constexpr size_t kOffTh = kOffSig + align256(8 * kNoallocMaxN);
@@ -61,6 +62,8 @@ constexpr size_t kOffEmax = kOffPart + align256(8 * kSegcap);
 constexpr size_t kOffEmin = kOffEmax + align256(4 * kLevels);
 constexpr size_t kOffFexp = kOffEmin + align256(4 * kLevels);
 constexpr size_t kScratchBytes = kOffFexp + align256(8 * kLevels);  // about 16 MB
+
+static_assert(kLevels < INT32_MAX, "level capacity");
 
 // The scratch.  Host code must not take this name as a device address (in
 // host code it names a host-side shadow); it uses the address returned by
@@ -175,6 +178,10 @@ extern "C" sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_id
     a.sources = sources;
     a.nsrc = nsrc;
     a.bc = bc_out;
+    a.bcpart = nullptr;
+    a.ngroups = 1;
+    a.lcap = (int32_t)kLevels;
+    a.gctl = reinterpret_cast<GroupCtl*>(ws + kOffGctl);
     a.lvl = reinterpret_cast<int32_t*>(ws + kOffLvl);
     a.sig = ws + kOffSig;
     a.th = ws + kOffTh;
@@ -208,6 +215,8 @@ extern "C" sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_id
         SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPlainThreads, 0));
         if (per_sm < 1) return fail(SP_ERR_CUDA, "sp_bc_noalloc: kernel cannot be resident");
         SP_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(Ctl), st));
+        SP_CUDA(cudaMemsetAsync(a.gctl, 0, sizeof(GroupCtl), st));
+        a.gblocks = per_sm * sms;
         void* args[] = {&a};
         SP_CUDA(cudaLaunchCooperativeKernel(fn, dim3(per_sm * sms), dim3(kPlainThreads), args, 0, st));
         int err = 0;

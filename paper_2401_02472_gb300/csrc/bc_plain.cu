@@ -1,7 +1,6 @@
 // Host launcher of the plain form (kernel in bc_plain_kernel.cuh).
+#include <algorithm>
 #include <climits>
-#include <type_traits>
-
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -18,7 +17,7 @@ static const void* plain_fn() {
 
 sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     const Graph* g = L.g;
-    const int n = g->n;
+    const int64_t n = g->n;
     cudaStream_t st = L.stream;
     Tiers tiers{16, 4096, 4096};
     const void* fn;
@@ -31,57 +30,78 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     if (per_sm < 1) return fail(SP_ERR_CUDA, "plain kernel cannot be resident");
     int grid = per_sm * device_sm_count(dev);
     if (L.max_ctas > 0 && L.max_ctas < grid) grid = L.max_ctas;
+    // Groups: `group_blocks` blocks each (0 = one group of every block), no
+    // more groups than sources; a fault-injection run keeps one group so that
+    // the skipped barrier is a real multi-block wait.
+    int gblocks = L.group_blocks > 0 ? std::min(L.group_blocks, grid) : grid;
+    if (L.debug_flags & SP_DEBUG_SKIP_BARRIER) gblocks = grid;
+    int ngroups = std::max(1, std::min(grid / gblocks, std::max(1, L.nsrc)));
+    if (ngroups > 1 && grid / ngroups > gblocks) gblocks = grid / ngroups;  // spread spare blocks
+    grid = ngroups * gblocks;
 
-    // Workspace
-    int64_t hcap = g->nnz / tiers.t_hub + 2;
-    int64_t segcap = g->nnz / tiers.seg + hcap + 2;
-    size_t nl = (size_t)n + 2;
+    // Workspace: one copy of the per-source arrays per group.
+    const int64_t lcap = L.level_cap > 0 ? std::min<int64_t>(L.level_cap, n + 2)
+                                         : (ngroups == 1 ? n + 2 : std::min<int64_t>(n + 2, 65536));
+    const int64_t hcap = g->nnz / tiers.t_hub + 2;
+    const int64_t segcap = g->nnz / tiers.seg + hcap + 2;
+    const size_t G = (size_t)ngroups;
     size_t bytes = 0;
     auto take = [&](size_t b) { size_t o = bytes; bytes += (b + 255) & ~(size_t)255; return o; };
     size_t o_ctl = take(sizeof(Ctl));
-    size_t o_lvl = take(sizeof(int32_t) * (size_t)n);
-    size_t o_sig = take(8 * (size_t)n);
-    size_t o_th = take(8 * (size_t)n);
-    size_t o_q = take(sizeof(int32_t) * (size_t)n);
-    size_t o_qoff = take(sizeof(int32_t) * nl);
-    size_t o_hubs = take(sizeof(HubRec) * (size_t)hcap);
-    size_t o_hoff = take(sizeof(int32_t) * nl);
-    size_t o_hcnt = take(sizeof(unsigned long long) * nl);
-    size_t o_hdone = take(sizeof(int32_t) * 2 * (size_t)hcap);
-    size_t o_part = take(sizeof(double) * (size_t)segcap);
-    size_t o_emax = take(sizeof(int32_t) * nl);
-    size_t o_emin = take(sizeof(int32_t) * nl);
-    size_t o_fexp = take(sizeof(long long) * nl);
+    size_t o_gctl = take(sizeof(GroupCtl) * G);
+    size_t zero_end = bytes;
+    size_t o_lvl = take(sizeof(int32_t) * (size_t)n * G);
+    size_t o_sig = take(8 * (size_t)n * G);
+    size_t o_th = take(8 * (size_t)n * G);
+    size_t o_q = take(sizeof(int32_t) * (size_t)n * G);
+    size_t o_qoff = take(sizeof(int32_t) * (size_t)lcap * G);
+    size_t o_hoff = take(sizeof(int32_t) * (size_t)lcap * G);
+    size_t o_hcnt = take(sizeof(unsigned long long) * (size_t)lcap * G);
+    size_t o_emax = take(sizeof(int32_t) * (size_t)lcap * G);
+    size_t o_emin = take(sizeof(int32_t) * (size_t)lcap * G);
+    size_t o_fexp = take(sizeof(long long) * (size_t)lcap * G);
+    size_t o_hubs = take(sizeof(HubRec) * (size_t)hcap * G);
+    size_t o_hdone = take(sizeof(int32_t) * 2 * (size_t)hcap * G);
+    size_t o_part = take(sizeof(double) * (size_t)segcap * G);
+    size_t o_bcpart = take(ngroups > 1 && L.mode == PlainMode::BC ? sizeof(double) * (size_t)n * G : 0);
     size_t o_trace = take(sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32));
     char* ws = nullptr;
     cudaError_t ce = cudaMallocAsync((void**)&ws, bytes, st);
-    if (ce != cudaSuccess) return fail(SP_ERR_OOM, "workspace allocation (plain form)");
-    ce = cudaMemsetAsync(ws + o_ctl, 0, sizeof(Ctl), st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SP_ERR_OOM, "workspace allocation (plain form, " + std::to_string(bytes >> 20) + " MiB)");
+    }
+    ce = cudaMemsetAsync(ws, 0, zero_end, st);
     if (ce != cudaSuccess) { cudaFreeAsync(ws, st); return cuda_fail(ce, "cudaMemsetAsync"); }
 
     PlainArgs a{};
     a.rp = g->d_rp;
     a.ci = g->d_ci;
-    a.n = n;
+    a.n = (int32_t)n;
     a.sources = L.d_sources;
     a.nsrc = L.nsrc;
     a.bc = L.d_bc;
+    a.bcpart = reinterpret_cast<double*>(ws + o_bcpart);
+    a.gblocks = gblocks;
+    a.ngroups = ngroups;
     a.lvl = reinterpret_cast<int32_t*>(ws + o_lvl);
     a.sig = ws + o_sig;
     a.th = ws + o_th;
     a.q = reinterpret_cast<int32_t*>(ws + o_q);
     a.qoff = reinterpret_cast<int32_t*>(ws + o_qoff);
-    a.hubs = reinterpret_cast<HubRec*>(ws + o_hubs);
-    a.hcap = (int32_t)hcap;
     a.hoff = reinterpret_cast<int32_t*>(ws + o_hoff);
     a.hcnt = reinterpret_cast<unsigned long long*>(ws + o_hcnt);
-    a.hdone = reinterpret_cast<int32_t*>(ws + o_hdone);
-    a.part = reinterpret_cast<double*>(ws + o_part);
-    a.segcap = (int32_t)segcap;
     a.emax = reinterpret_cast<int32_t*>(ws + o_emax);
     a.emin = reinterpret_cast<int32_t*>(ws + o_emin);
     a.fexp = reinterpret_cast<long long*>(ws + o_fexp);
+    a.hubs = reinterpret_cast<HubRec*>(ws + o_hubs);
+    a.hdone = reinterpret_cast<int32_t*>(ws + o_hdone);
+    a.part = reinterpret_cast<double*>(ws + o_part);
+    a.hcap = (int32_t)hcap;
+    a.segcap = (int32_t)segcap;
+    a.lcap = (int32_t)lcap;
     a.ctl = reinterpret_cast<Ctl*>(ws + o_ctl);
+    a.gctl = reinterpret_cast<GroupCtl*>(ws + o_gctl);
     a.err_latch = nullptr;
     a.dist_out = L.d_dist;
     a.mant_out = L.d_mant;
@@ -101,16 +121,26 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     cudaEventCreate(&ev1);
     cudaEventRecord(ev0, st);
     ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPlainThreads), args, 0, st);
+    if (ce == cudaSuccess && ngroups > 1 && L.mode == PlainMode::BC) {
+        int rgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count(dev) * 8);
+        sum_group_partials_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(a.bcpart, ngroups, n, L.d_bc);
+        ce = cudaGetLastError();
+    }
     cudaEventRecord(ev1, st);
     if (ce != cudaSuccess) {
         cudaFreeAsync(ws, st);
-        return cuda_fail(ce, "cudaLaunchCooperativeKernel (plain form)");
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        return cuda_fail(ce, "plain-form launch");
     }
     static thread_local Ctl h;
     std::memset(&h, 0, sizeof(h));
     ce = cudaMemcpyAsync(&h, ws + o_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) { cudaFreeAsync(ws, st); return cuda_fail(ce, "reading the plain-form result"); }
+    if (ce != cudaSuccess) {
+        cudaFreeAsync(ws, st);
+        return cuda_fail(ce, "reading the plain-form result");
+    }
     result->err = h.err;
     result->levels = h.max_levels;
     result->traversed_arcs = h.traversed_arcs;
@@ -118,11 +148,14 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     result->entries = h.reached;
     result->scanned_arcs = h.scanned_arcs;
     result->dag_arcs = h.dag_arcs;
+    result->lcap = lcap;
+    result->grid = grid;
+    result->groups = ngroups;
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) result->kernel_ms = ms;
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    result->launches = 1;
+    result->launches = ngroups > 1 && L.mode == PlainMode::BC ? 2 : 1;
     if (h.err == SP_ERR_TIMEOUT) result->diag = barrier_diagnostic(h, grid);
 #ifdef SP_TRACE
     if (h.err == SP_ERR_TIMEOUT) {

@@ -1,7 +1,7 @@
-// Plain form: one source at a time, all of the GPU on it.
+// Plain form: one source at a time per group of blocks.
 //
 // Per source (paper Section 2, Fig. 1, ComputeBC; the level-synchronous BFS of
-// Section 3.3) one persistent cooperative launch runs
+// Section 3.3) a group of blocks runs
 //   init      level[] = -1, level[src] = 0, sigma[src] = 1
 //   forward   for d = 0, 1, ...: every vertex v at level d pulls sigma from its
 //             neighbours at level d-1 (the iterateInBFS sum over BFS parents)
@@ -11,8 +11,17 @@
 //             from its neighbours at level d+1, then delta(v) = sigma(v) * sum,
 //             BC(v) += delta(v) (the iterateInReverse sum over BFS children,
 //             written so that no floating-point atomics are needed)
-// with a timed grid barrier between levels instead of the paper's host loop
-// that copies a `finished` flag every level (Section 3.3; Section 4.1).
+// with a timed barrier over the group's blocks between levels instead of the
+// paper's host loop that copies a `finished` flag every level (Section 3.3;
+// Section 4.1).
+//
+// Groups: the persistent launch is cut into `ngroups` groups of `gblocks`
+// blocks.  Group g takes sources g, g + ngroups, ... in order, with its own
+// level arrays, level stack, barrier and partial BC vector; the partial
+// vectors are added in group order by a second kernel.  One group of every
+// block suits graphs whose levels are wide (millions of arcs); many small
+// groups suit high-diameter graphs, whose thousands of narrow levels would
+// otherwise leave most of the GPU waiting at barriers.
 //
 // Work distribution inside a level: entries of Q are taken 32 at a time by a
 // warp; rows of at most t_thread arcs are walked by one lane, longer rows by
@@ -36,29 +45,45 @@ namespace sp {
 
 constexpr int kPlainThreads = 512;
 
+// Barrier and work counters of one block group (zeroed by the host).
+struct GroupCtl {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    unsigned int work[4];
+    int qtail;
+    int snap[2];
+    int pad[7];
+};
+
 struct PlainArgs {
     const int32_t* rp;
     const int32_t* ci;
     int32_t n;
     const int32_t* sources;
     int32_t nsrc;
-    double* bc;
-    int32_t* lvl;
-    void* sig;
-    void* th;
-    int32_t* q;             // level stack, n entries
-    int32_t* qoff;          // [n+2]
-    HubRec* hubs;
-    int32_t hcap;
-    int32_t* hoff;          // [n+2]
-    unsigned long long* hcnt;  // [n+2]: records << 32 | segments, per level
+    double* bc;             // output; written directly when ngroups == 1
+    double* bcpart;         // [ngroups][n] partial BC per group (ngroups > 1)
+    int32_t gblocks;        // blocks per group
+    int32_t ngroups;
+    // Per-group arrays: group g's copy starts at base + g * stride.
+    int32_t* lvl;           // [n]
+    void* sig;              // [n] 8-byte elements
+    void* th;               // [n] 8-byte slots
+    int32_t* q;             // [n] level stack
+    int32_t* qoff;          // [lcap]
+    int32_t* hoff;          // [lcap]
+    unsigned long long* hcnt;  // [lcap]: records << 32 | segments, per level
+    int32_t* emax;          // [lcap] per-level exponent range of scaled sigma
+    int32_t* emin;          // [lcap]
+    long long* fexp;        // [lcap] cumulative exponent per level (sigma output)
+    HubRec* hubs;           // [hcap]
     int32_t* hdone;         // [2*hcap]: forward / backward finish counters
     double* part;           // [segcap] per-segment partial sums (8-byte slots)
+    int32_t hcap;
     int32_t segcap;
-    int32_t* emax;          // [n+2] per-level exponent range of scaled sigma
-    int32_t* emin;          // [n+2]
-    long long* fexp;        // [n+2] cumulative exponent per level (sigma output)
-    Ctl* ctl;
+    int32_t lcap;
+    Ctl* ctl;               // launch-wide: error, statistics
+    GroupCtl* gctl;         // [ngroups]
     int* err_latch;
     int32_t* dist_out;
     double* mant_out;
@@ -69,6 +94,68 @@ struct PlainArgs {
     int t_thread, t_hub, seg;
     int* trace;  // SP_TRACE builds: 8 ints per warp
 };
+
+// Barrier over the `nblocks` blocks of one group: as grid_sync (common.cuh),
+// with the group's own counters; the last block to arrive snapshots the
+// group's level-stack fill.  A group of one block needs only __syncthreads.
+static __device__ __noinline__ bool group_sync(Ctl* ctl, GroupCtl* gc, unsigned nblocks, uint64_t timeout_ns,
+                                               int phase, bool skip, int* qtail_snap) {
+    __shared__ int s_ok, s_snap;
+    __syncthreads();
+    if (nblocks == 1) {
+        if (threadIdx.x == 0) {
+            if (blockIdx.x < 1024) ctl->block_phase[blockIdx.x] = phase;
+            s_snap = ld_volatile(&gc->qtail);
+            s_ok = (ld_volatile(&ctl->err) == 0 && !skip) ? 1 : 0;
+        }
+        __syncthreads();
+        *qtail_snap = s_snap;
+        return s_ok != 0;
+    }
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) {
+            int ok = skip ? 0 : 1;
+            int snapv = 0;
+            if (!skip) {
+                unsigned gen = ld_acquire_u32(&gc->bar_gen);
+                if (blockIdx.x < 1024) ctl->block_phase[blockIdx.x] = phase;
+                __threadfence();
+                unsigned arrived = atomicAdd(&gc->bar_count, 1u);
+                if (arrived == nblocks - 1) {
+                    gc->snap[gen & 1u] = ld_volatile(&gc->qtail);
+                    gc->bar_count = 0;
+                    st_release_u32(&gc->bar_gen, gen + 1);
+                } else {
+                    uint64_t t0 = globaltimer();
+                    unsigned ns = 32;
+                    while (ld_acquire_u32(&gc->bar_gen) == gen) {
+                        if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
+                        if (globaltimer() - t0 > timeout_ns) {
+                            if (atomicCAS(&ctl->err, 0, (int)SP_ERR_TIMEOUT) == 0) {
+                                ctl->err_where = phase;
+                                ctl->timeout_count = ld_volatile(&gc->bar_count);
+                            }
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(ns);
+                        if (ns < 512) ns <<= 1;
+                    }
+                }
+                __threadfence();
+                snapv = ld_volatile(&gc->snap[gen & 1u]);
+            }
+            __threadfence();
+            if (ld_volatile(&ctl->err) != 0) ok = 0;
+            s_ok = ok;
+            s_snap = snapv;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    *qtail_snap = s_snap;
+    return s_ok != 0;
+}
 
 template <typename SigT>
 struct SigOps;
@@ -97,8 +184,13 @@ template <typename SigT, typename ThT>
 struct PlainKernel {
     const PlainArgs& a;
     Ctl* ctl;
+    GroupCtl* gc;
     int lane;
-    // per-level state (identical in every thread)
+    int grp;     // group index
+    size_t gn;   // group offset into [n] arrays
+    size_t gl;   // group offset into [lcap] arrays
+    size_t gh;   // group offset into [hcap] arrays
+    // per-level state (identical in every thread of the group)
     int d = 0;
     int hoff_d = 0, nrec_d = 0, nseg_d = 0;  // hub records of level d
     int hoff_next = 0;                       // first hub record of level d+1
@@ -109,38 +201,52 @@ struct PlainKernel {
     bool ovf = false;
     unsigned long long st_arcs = 0, st_reached = 0, st_scanned = 0, st_dag = 0;
 
-    __device__ PlainKernel(const PlainArgs& args) : a(args), ctl(args.ctl), lane(lane_id()) {}
+    __device__ PlainKernel(const PlainArgs& args, int g)
+        : a(args), ctl(args.ctl), gc(args.gctl + g), lane(lane_id()), grp(g), gn((size_t)g * (size_t)args.n),
+          gl((size_t)g * (size_t)args.lcap), gh((size_t)g * (size_t)args.hcap) {}
 
-    __device__ __forceinline__ SigT* sig() const { return reinterpret_cast<SigT*>(a.sig); }
-    __device__ __forceinline__ ThT* th() const { return reinterpret_cast<ThT*>(a.th); }
+    __device__ __forceinline__ int32_t* lvl() const { return a.lvl + gn; }
+    __device__ __forceinline__ SigT* sig() const { return reinterpret_cast<SigT*>(a.sig) + gn; }
+    __device__ __forceinline__ ThT* th() const { return reinterpret_cast<ThT*>(reinterpret_cast<double*>(a.th) + gn); }
+    __device__ __forceinline__ int32_t* q() const { return a.q + gn; }
+    __device__ __forceinline__ int32_t* qoff() const { return a.qoff + gl; }
+    __device__ __forceinline__ int32_t* hoff() const { return a.hoff + gl; }
+    __device__ __forceinline__ unsigned long long* hcnt() const { return a.hcnt + gl; }
+    __device__ __forceinline__ int32_t* emax() const { return a.emax + gl; }
+    __device__ __forceinline__ int32_t* emin() const { return a.emin + gl; }
+    __device__ __forceinline__ long long* fexp() const { return a.fexp + gl; }
+    __device__ __forceinline__ HubRec* hubs() const { return a.hubs + gh; }
+    __device__ __forceinline__ int32_t* hdone() const { return a.hdone + 2 * gh; }
+    __device__ __forceinline__ double* part() const { return a.part + (size_t)grp * (size_t)a.segcap; }
+    __device__ __forceinline__ double* bcv() const { return a.ngroups == 1 ? a.bc : a.bcpart + gn; }
 
     // A vertex claimed for level `nl`: append to the level stack (and the hub list).
     __device__ void push(int u, int nl) {
         int du = __ldg(&a.rp[u + 1]) - __ldg(&a.rp[u]);
         bool hub = du > a.t_hub;
-        int pos = aggregated_slot(&ctl->qtail);
+        int pos = aggregated_slot(&gc->qtail);
         if (pos >= a.n) { set_error(ctl, kErrCapacity); return; }
-        a.q[pos] = hub ? (int)((unsigned)u | kHubFlag) : u;
+        q()[pos] = hub ? (int)((unsigned)u | kHubFlag) : u;
         if (hub) {
             int nseg = (du + a.seg - 1) / a.seg;
-            unsigned long long old = atomicAdd(&a.hcnt[nl], (1ull << 32) | (unsigned long long)(unsigned)nseg);
+            unsigned long long old = atomicAdd(&hcnt()[nl], (1ull << 32) | (unsigned long long)(unsigned)nseg);
             int rec = hoff_next + (int)(old >> 32);
             int sb = (int)(old & 0xFFFFFFFFull);
             if (rec >= a.hcap || sb + nseg > a.segcap) { set_error(ctl, kErrCapacity); return; }
             HubRec h;
             h.v = u; h.qpos = pos; h.nseg = nseg; h.seg_base = sb;
-            a.hubs[rec] = h;
-            a.hdone[rec] = 0;
-            a.hdone[a.hcap + rec] = 0;
+            hubs()[rec] = h;
+            hdone()[rec] = 0;
+            hdone()[a.hcap + rec] = 0;
         }
     }
 
     // Forward visit of arc (v, u) by a vertex v at level d.
     __device__ __forceinline__ SigT fwd_arc(int u) {
-        int lu = __ldcg(&a.lvl[u]);
+        int lu = __ldcg(&lvl()[u]);
         SigT c = 0;
         if (lu < 0) {
-            if (atomicCAS(&a.lvl[u], -1, d + 1) == -1) push(u, d + 1);
+            if (atomicCAS(&lvl()[u], -1, d + 1) == -1) push(u, d + 1);
         } else if (lu == d - 1) {
             c = __ldcg(&sig()[u]);
             st_dag += 1;
@@ -165,7 +271,7 @@ struct PlainKernel {
     }
 
     __device__ __forceinline__ double bwd_arc(int w) {
-        int lw = __ldcg(&a.lvl[w]);
+        int lw = __ldcg(&lvl()[w]);
         return lw == d + 1 ? (double)__ldcg(&th()[w]) : 0.0;
     }
 
@@ -182,7 +288,8 @@ struct PlainKernel {
             if (!normal_finite(t)) set_error(ctl, SP_ERR_RANGE);
             th()[v] = (ThT)t;
         }
-        a.bc[v] = __ldcg(&a.bc[v]) + delta;
+        double* b = bcv();
+        b[v] = __ldcg(&b[v]) + delta;
     }
 
     // One chunk of 32 level-stack entries starting at index e0 (< qe).
@@ -190,7 +297,7 @@ struct PlainKernel {
     __device__ void chunk(int e0, int qe, bool skip_arcs) {
         int e = e0 + lane;
         bool valid = e < qe;
-        unsigned qv = valid ? (unsigned)__ldcg(&a.q[e]) : kHubFlag;
+        unsigned qv = valid ? (unsigned)__ldcg(&q()[e]) : kHubFlag;
         bool hubent = (qv & kHubFlag) != 0;
         int v = (int)(qv & kVertexMask);
         if (valid && v >= a.n) { set_error(ctl, kErrCorrupt); valid = false; hubent = true; v = 0; }
@@ -239,11 +346,11 @@ struct PlainKernel {
     // Segment g of the hubs of level d.
     template <bool FWD>
     __device__ void hub_segment(int g, bool skip_arcs) {
-        int r = find_hub(a.hubs, hoff_d, hoff_d + nrec_d, g);
+        int r = find_hub(hubs(), hoff_d, hoff_d + nrec_d, g);
         HubRec h;
-        h.v = __ldcg(&a.hubs[r].v);
-        h.nseg = __ldcg(&a.hubs[r].nseg);
-        h.seg_base = __ldcg(&a.hubs[r].seg_base);
+        h.v = __ldcg(&hubs()[r].v);
+        h.nseg = __ldcg(&hubs()[r].nseg);
+        h.seg_base = __ldcg(&hubs()[r].seg_base);
         if (h.v < 0 || h.v >= a.n || h.nseg < 1 || h.seg_base < 0 || h.seg_base + h.nseg > a.segcap) {
             if (lane == 0) set_error(ctl, kErrCorrupt);
             return;
@@ -261,14 +368,14 @@ struct PlainKernel {
             else tp += bwd_arc(u);
         }
         if (lane == 0) st_scanned += (unsigned long long)(end - beg);
-        int* done = FWD ? &a.hdone[r] : &a.hdone[a.hcap + r];
+        int* done = FWD ? &hdone()[r] : &hdone()[a.hcap + r];
         int old = 0;
         if constexpr (FWD) {
             sp_ = SigOps<SigT>::warp_sum(sp_, ovf);
-            if (lane == 0) reinterpret_cast<SigT*>(a.part)[g] = sp_;
+            if (lane == 0) reinterpret_cast<SigT*>(part())[g] = sp_;
         } else {
             tp = warp_sum_f64(tp);
-            if (lane == 0) a.part[g] = tp;
+            if (lane == 0) part()[g] = tp;
         }
         if (lane == 0) {
             __threadfence();
@@ -281,8 +388,8 @@ struct PlainKernel {
         SigT st = 0;
         double tt = 0.0;
         for (int k = lane; k < h.nseg; k += kWarp) {
-            if constexpr (FWD) st = SigOps<SigT>::add(st, __ldcg(&reinterpret_cast<SigT*>(a.part)[h.seg_base + k]), ovf);
-            else tt += __ldcg(&a.part[h.seg_base + k]);
+            if constexpr (FWD) st = SigOps<SigT>::add(st, __ldcg(&reinterpret_cast<SigT*>(part())[h.seg_base + k]), ovf);
+            else tt += __ldcg(&part()[h.seg_base + k]);
         }
         if constexpr (FWD) {
             st = SigOps<SigT>::warp_sum(st, ovf);
@@ -299,7 +406,7 @@ struct PlainKernel {
         int total = nseg_d + nchunks;
         while (true) {
             int item = 0;
-            if (lane == 0) item = (int)atomicAdd(&ctl->work[phase & 3], 1u);
+            if (lane == 0) item = (int)atomicAdd(&gc->work[phase & 3], 1u);
             item = __shfl_sync(kFull, item, 0);
 #ifdef SP_TRACE
             if (lane == 0 && a.trace) {
@@ -317,10 +424,13 @@ struct PlainKernel {
 template <typename SigT, typename ThT>
 __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
     constexpr bool kFloatSig = !std::is_integral<SigT>::value;
-    PlainKernel<SigT, ThT> K(a);
+    const int g = blockIdx.x / a.gblocks;
+    if (g >= a.ngroups) return;  // the host sizes the grid to ngroups * gblocks
+    PlainKernel<SigT, ThT> K(a, g);
     Ctl* ctl = a.ctl;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthr = gridDim.x * blockDim.x;
+    GroupCtl* gc = K.gc;
+    const int tid = (blockIdx.x % a.gblocks) * blockDim.x + threadIdx.x;  // rank in the group
+    const int nthr = a.gblocks * blockDim.x;
     const int n = a.n;
     int phase = 0;
     int qsnap = 0;  // level-stack fill at the last barrier
@@ -328,41 +438,43 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
     // Barrier between phases; the work counter of phase p+2 is cleared in phase p.
     auto sync = [&]() -> bool {
         bool skip = (a.debug_flags & SP_DEBUG_SKIP_BARRIER) && blockIdx.x == 0 && phase == 1;
-        bool ok = grid_sync(ctl, gridDim.x, a.timeout_ns, phase++, skip, &qsnap);
-        if (tid == 0) ctl->work[(phase + 2) & 3] = 0u;
+        bool ok = group_sync(ctl, gc, a.gblocks, a.timeout_ns, phase++, skip, &qsnap);
+        if (tid == 0) gc->work[(phase + 2) & 3] = 0u;
         return ok;
     };
 
-    if (a.mode == (int)PlainMode::BC)
-        for (int i = tid; i < n; i += nthr) a.bc[i] = 0.0;
+    if (a.mode == (int)PlainMode::BC) {
+        double* b = K.bcv();
+        for (int i = tid; i < n; i += nthr) b[i] = 0.0;
+    }
     if (!sync()) goto out;
 
-    for (int si = 0; si < a.nsrc; ++si) {
+    for (int si = g; si < a.nsrc; si += a.ngroups) {
         const int src = __ldg(&a.sources[si]);
         // ---- init ----
-        for (int i = tid; i < n; i += nthr) a.lvl[i] = (i == src) ? 0 : -1;
+        for (int i = tid; i < n; i += nthr) K.lvl()[i] = (i == src) ? 0 : -1;
         if (tid == 0) {
             int du = a.rp[src + 1] - a.rp[src];
-            a.q[0] = src;
-            ctl->qtail = 1;
-            a.qoff[0] = 0;
-            a.hoff[0] = 0;
-            a.hcnt[0] = 0ull;
-            a.hcnt[1] = 0ull;
-            a.emax[0] = 0;
-            a.emin[0] = 0;
-            reinterpret_cast<SigT*>(a.sig)[src] = (SigT)1;
+            K.q()[0] = src;
+            gc->qtail = 1;
+            K.qoff()[0] = 0;
+            K.hoff()[0] = 0;
+            K.hcnt()[0] = 0ull;
+            K.hcnt()[1] = 0ull;
+            K.emax()[0] = 0;
+            K.emin()[0] = 0;
+            K.sig()[src] = (SigT)1;
             if (du > a.t_hub) {
                 int nseg = (du + a.seg - 1) / a.seg;
                 if (a.hcap < 1 || nseg > a.segcap) set_error(ctl, kErrCapacity);
                 else {
-                    a.q[0] = (int)((unsigned)src | kHubFlag);
+                    K.q()[0] = (int)((unsigned)src | kHubFlag);
                     HubRec h;
                     h.v = src; h.qpos = 0; h.nseg = nseg; h.seg_base = 0;
-                    a.hubs[0] = h;
-                    a.hdone[0] = 0;
-                    a.hdone[a.hcap] = 0;
-                    a.hcnt[0] = (1ull << 32) | (unsigned long long)nseg;
+                    K.hubs()[0] = h;
+                    K.hdone()[0] = 0;
+                    K.hdone()[a.hcap] = 0;
+                    K.hcnt()[0] = (1ull << 32) | (unsigned long long)nseg;
                 }
             }
         }
@@ -373,20 +485,25 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
         K.d = 0;
         K.hoff_d = 0;
         while (true) {
-                const int d = K.d;
-            unsigned long long hc = ld_volatile(&a.hcnt[d]);
+            const int d = K.d;
+            if (d + 2 >= a.lcap) {
+                if (tid == 0) set_error(ctl, kErrCapLevels);
+                sync();
+                goto out;
+            }
+            unsigned long long hc = ld_volatile(&K.hcnt()[d]);
             K.nrec_d = (int)(hc >> 32);
             K.nseg_d = (int)(hc & 0xFFFFFFFFull);
             K.hoff_next = K.hoff_d + K.nrec_d;
             if constexpr (kFloatSig) {
-                K.cshift_prev = d > 0 ? centre_shift(ld_volatile(&a.emax[d - 1]), ld_volatile(&a.emin[d - 1])) : 0;
+                K.cshift_prev = d > 0 ? centre_shift(ld_volatile(&K.emax()[d - 1]), ld_volatile(&K.emin()[d - 1])) : 0;
             }
             if (tid == 0) {
-                a.qoff[d + 1] = qe;
-                a.hoff[d] = K.hoff_d;
-                a.hcnt[d + 2] = 0ull;
-                a.emax[d + 1] = INT_MIN;
-                a.emin[d + 1] = INT_MAX;
+                K.qoff()[d + 1] = qe;
+                K.hoff()[d] = K.hoff_d;
+                K.hcnt()[d + 2] = 0ull;
+                K.emax()[d + 1] = INT_MIN;
+                K.emin()[d + 1] = INT_MAX;
             }
             K.my_emax = INT_MIN;
             K.my_emin = INT_MAX;
@@ -394,8 +511,8 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
             if constexpr (kFloatSig) {
                 int mx = warp_max_i32(K.my_emax), mn = warp_min_i32(K.my_emin);
                 if (K.lane == 0 && mx >= mn) {
-                    atomicMax(&a.emax[d], mx);
-                    atomicMin(&a.emin[d], mn);
+                    atomicMax(&K.emax()[d], mx);
+                    atomicMin(&K.emin()[d], mn);
                 }
             }
             if (K.ovf && a.mode != (int)PlainMode::BFS) set_error(ctl, kErrSigmaOverflow);
@@ -412,7 +529,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
 
         if (a.mode == (int)PlainMode::BFS) {
             int* row = a.dist_out + (size_t)si * (size_t)n;
-            for (int i = tid; i < n; i += nthr) row[i] = __ldcg(&a.lvl[i]);
+            for (int i = tid; i < n; i += nthr) row[i] = __ldcg(&K.lvl()[i]);
             if (!sync()) goto out;
             continue;
         }
@@ -420,20 +537,20 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
             if (tid == 0) {
                 long long f = 0;
                 for (int l = 0; l < L; ++l) {
-                    a.fexp[l] = f;
-                    if constexpr (kFloatSig) f += centre_shift(a.emax[l], a.emin[l]);
+                    K.fexp()[l] = f;
+                    if constexpr (kFloatSig) f += centre_shift(K.emax()[l], K.emin()[l]);
                 }
             }
             if (!sync()) goto out;
             for (int i = tid; i < n; i += nthr) {
-                int l = __ldcg(&a.lvl[i]);
+                int l = __ldcg(&K.lvl()[i]);
                 double m = 0.0;
                 long long e2 = 0;
                 if (l >= 0) {
-                    double s = (double)__ldcg(&reinterpret_cast<SigT*>(a.sig)[i]);
+                    double s = (double)__ldcg(&K.sig()[i]);
                     int e = exp_field(s) - 1023;
                     m = scale2(s, -e);
-                    e2 = (long long)e + __ldcg(&a.fexp[l]);
+                    e2 = (long long)e + __ldcg(&K.fexp()[l]);
                 }
                 a.mant_out[i] = m;
                 a.exp_out[i] = e2;
@@ -444,14 +561,14 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
 
         // ---- backward ----
         for (int d = L - 1; d >= 1; --d) {
-                K.d = d;
-            int qbd = ld_volatile(&a.qoff[d]);
-            int qed = ld_volatile(&a.qoff[d + 1]);
-            unsigned long long hc = ld_volatile(&a.hcnt[d]);
-            K.hoff_d = ld_volatile(&a.hoff[d]);
+            K.d = d;
+            int qbd = ld_volatile(&K.qoff()[d]);
+            int qed = ld_volatile(&K.qoff()[d + 1]);
+            unsigned long long hc = ld_volatile(&K.hcnt()[d]);
+            K.hoff_d = ld_volatile(&K.hoff()[d]);
             K.nrec_d = (int)(hc >> 32);
             K.nseg_d = (int)(hc & 0xFFFFFFFFull);
-            if constexpr (kFloatSig) K.cshift_cur = centre_shift(ld_volatile(&a.emax[d]), ld_volatile(&a.emin[d]));
+            if constexpr (kFloatSig) K.cshift_cur = centre_shift(ld_volatile(&K.emax()[d]), ld_volatile(&K.emin()[d]));
             K.template level_work<false>(phase, qbd, qed, d == L - 1);
             if (!sync()) goto out;
         }
@@ -477,6 +594,16 @@ out:
             int e = ld_volatile(&ctl->err);
             if (e != 0 && a.err_latch) *(volatile int*)a.err_latch = e;
         }
+    }
+}
+
+// Sum of the groups' partial BC vectors, in group order.
+static __global__ void sum_group_partials_kernel(const double* __restrict__ part, int ngroups, int64_t n,
+                                                 double* __restrict__ out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int gi = 0; gi < ngroups; ++gi) s += part[(int64_t)gi * n + v];
+        out[v] = s;
     }
 }
 

@@ -29,6 +29,8 @@ struct Graph {
     bool sigma_float = false;  // path counts of this graph overflowed 64-bit integers before
     int32_t top_vertex = 0;     // a vertex of maximum degree
     int32_t* d_top_dist = nullptr;  // BFS distances from top_vertex (computed on first use)
+    int32_t top_levels = 0;     // 1 + eccentricity of top_vertex (0 until computed)
+    bool theta_f64 = false;     // FP32 dependencies of this graph left the FP32 range before
 };
 
 // Thread-local error text.
@@ -66,6 +68,8 @@ struct PlainLaunch {
     uint64_t timeout_ns;
     int debug_flags;
     cudaStream_t stream;
+    int group_blocks;       // blocks per group (0 = one group of every block)
+    int64_t level_cap;      // BFS levels per group; 0 = default
 };
 
 struct LaunchResult {
@@ -77,6 +81,7 @@ struct LaunchResult {
     double kernel_ms = 0.0;                // CUDA-event time of the launch
     int launches = 0;
     int grid = 0;
+    int groups = 1;
     std::string diag;                      // barrier state when a wait timed out
 };
 
