@@ -43,6 +43,8 @@ WORKLOADS = {
                                    desc="RMAT scale 22, edge factor 16, 1,024 sources, autotuned batches"),
     "rmat22_128src_batched": dict(graph="rmat22", nsrc=128, seed=14, precision="fp32_delta", form="batched",
                                   desc="RMAT scale 22, edge factor 16, 128 sources (one batch; profiling case)"),
+    "rmat21_128src_batched": dict(graph="rmat21", nsrc=128, seed=14, precision="fp32_delta", form="batched",
+                                  desc="RMAT scale 21, edge factor 16, 128 sources (profiling case)"),
     "rmat20_64src_batched": dict(graph="rmat20", nsrc=64, seed=12, precision="fp32_delta", form="batched",
                                  desc="RMAT scale 20, edge factor 16, 64 sources"),
     "knn4_1m_256src_batched": dict(graph="knn4_1m", nsrc=256, seed=13, precision="fp32_delta", form="batched",
@@ -50,7 +52,142 @@ WORKLOADS = {
     "er2000_all_plain": dict(graph="er2000", nsrc=2000, seed=None, precision="fp64", form="plain",
                              desc="Erdos-Renyi n=2,000 m=10,000, all 2,000 sources"),
 }
+WORKLOADS["serving_8graphs"] = dict(graph=None, nsrc=0, seed=31, precision="fp32_delta", form="auto",
+                                    desc="Poisson stream (200 req/s) of BC requests over 8 resident ER/RMAT graphs, "
+                                         "1-256 sources each, continuous batching vs one request at a time")
 DEFAULT_WORKLOAD = "rmat22_1024src_batched"
+
+# The eight resident graphs of the serving workload (seeds 21-28).
+SERVING_GRAPHS = [
+    ("er", 10_000, 8, 21), ("rmat", 14, 8, 22), ("er", 100_000, 16, 23), ("rmat", 17, 16, 24),
+    ("er", 500_000, 32, 25), ("rmat", 19, 8, 26), ("er", 1_000_000, 16, 27), ("er", 2_000_000, 8, 28),
+]
+
+
+def serving_graphs():
+    out = []
+    for kind, size, deg, seed in SERVING_GRAPHS:
+        if kind == "er":
+            out.append(gen.er(size, size * deg // 2, seed))
+        else:
+            out.append(gen.rmat(size, deg, seed))
+    return out
+
+
+def serving_stream(gs, duration_s, rate, seed):
+    """(arrival s, graph index, sources) per request: Poisson arrivals, graph uniform, nsrc log-uniform 1-256."""
+    t = gen.poisson_arrivals(rate, duration_s, seed)
+    k = len(t)
+    which = gen.draws(gen.substream(seed, 21), 0, k) % np.uint64(len(gs))
+    sizes = gen.log_uniform_int(1, 256, seed, k)
+    reqs = []
+    for i in range(k):
+        gi = int(which[i])
+        reqs.append((float(t[i]), gi, gen.sources(gs[gi], int(sizes[i]), 100_000 + i)))
+    return reqs
+
+
+def run_serving(args, world):
+    import torch
+
+    import paper_2401_02472_gb300 as sp
+
+    torch.cuda.set_device(0)
+    dev = "cuda:0"
+    gs = serving_graphs()
+    Gs = [sp.Graph(g.row_ptr, g.col_idx) for g in gs]
+    reqs = serving_stream(gs, args.duration + args.serve_warmup, args.rate, 31)
+    opts = sp.make_opts(precision=sp.SP_FP32_DELTA)
+    dump = [torch.empty(g.n, dtype=torch.float64, device=dev) for g in gs]
+    sample_every = 20  # 5 % of the requests keep their own output for the alone-vs-mix check
+
+    def one_stream(server):
+        ids = [sp.sp_server_add_graph(server, G.handle) for G in Gs]
+        handles, kept = [], {}
+        t0 = time.perf_counter()
+        for i, (ta, gi, srcs) in enumerate(reqs):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            out = dump[gi]
+            if i % sample_every == 0:
+                out = torch.empty(gs[gi].n, dtype=torch.float64, device=dev)
+                kept[i] = out
+            handles.append(sp.sp_bc_submit(server, ids[gi], srcs, out, opts))
+        for h in handles:
+            sp.sp_bc_wait(server, h)
+        times = [sp.sp_request_times(server, h) for h in handles]
+        stats = [sp.sp_request_stats(server, h) for h in handles]
+        return times, stats, kept
+
+    server = sp.sp_server_create(args.serve_budget << 30, args.slots)
+    clocks = ClockSampler(0)
+    clocks.start()
+    times, stats, kept = one_stream(server)
+    clk = clocks.stop()
+    sp.sp_server_destroy(server)
+
+    warm = args.serve_warmup
+    sub0 = times[0][0]
+    lat, arcs = [], 0
+    first_sub, last_done = None, 0
+    for (ta, gi, srcs), (ts, tb, td), st in zip(reqs, times, stats):
+        if ta < warm:
+            continue
+        lat.append((td - ts) / 1e6)
+        arcs += st["traversed_arcs"]
+        first_sub = ts if first_sub is None else min(first_sub, ts)
+        last_done = max(last_done, td)
+    window_s = (last_done - first_sub) / 1e9
+    gteps = arcs / window_s / 1e9
+
+    # the same requests one at a time, plain form, in arrival order (open loop)
+    popts = sp.make_opts(precision=sp.SP_FP32_DELTA, form=sp.SP_FORM_PLAIN)
+    base_lat, base_arcs = [], 0
+    t0 = time.perf_counter()
+    for ta, gi, srcs in reqs:
+        delay = t0 + ta - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        st = sp.sp_bc_ex(Gs[gi].handle, torch.as_tensor(srcs, device=dev), dump[gi], popts)
+        done = time.perf_counter()
+        if ta >= warm:
+            base_lat.append((done - (t0 + ta)) * 1e3)
+            base_arcs += st["traversed_arcs"]
+        if done - t0 > 3 * (args.duration + warm):
+            break
+    base_window = time.perf_counter() - t0 - warm
+
+    # alone vs mixed, on the kept 5 %
+    same = 0
+    for i, out in kept.items():
+        _, gi, srcs = reqs[i]
+        s1 = sp.sp_server_create(args.serve_budget << 30, args.slots)
+        gid = [sp.sp_server_add_graph(s1, G.handle) for G in Gs][gi]
+        alone = torch.empty(gs[gi].n, dtype=torch.float64, device=dev)
+        sp.sp_bc_wait(s1, sp.sp_bc_submit(s1, gid, srcs, alone, opts))
+        sp.sp_server_destroy(s1)
+        same += int(torch.equal(alone, out))
+
+    pct = lambda xs, q: float(np.percentile(np.asarray(xs), q)) if xs else None
+    line = {
+        "metric": "BC GTEPS (serving)", "value": gteps, "unit": "GTEPS", "n_gpus": world, "steps": 1,
+        "warmup": 0, "ms_per_step": window_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64-sigma/f32-delta/f64-bc", "data": "synthetic",
+        "config": {"workload": "serving_8graphs", "desc": WORKLOADS["serving_8graphs"]["desc"],
+                   "rate_per_s": args.rate, "duration_s": args.duration, "warmup_s": warm, "slots": args.slots,
+                   "budget_gib": args.serve_budget, "requests": len(reqs)},
+        "serving": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "requests_measured": len(lat),
+                    "one_at_a_time_plain": {"p50_ms": pct(base_lat, 50), "p99_ms": pct(base_lat, 99),
+                                            "gteps": base_arcs / max(base_window, 1e-9) / 1e9,
+                                            "requests_measured": len(base_lat)},
+                    "alone_vs_mix_identical": f"{same} of {len(kept)}"},
+        "e2e": {"value": gteps, "unit": "GTEPS",
+                "h2d_bytes_per_step": int(sum(r[2].nbytes for r in reqs)), "d2h_bytes_per_step": 0},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
 
 
 def log(*a):
@@ -170,10 +307,32 @@ def cpu_baseline(g, srcs, budget_s=15.0):
 # ---------------------------------------------------------------------------
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle, on a bounded sample of the workload per step."""
-    w, g, srcs = workload_inputs(args.workload, rank)
     if rank != 0:
         return
     import oracle
+
+    if args.workload == "serving_8graphs":
+        gs = serving_graphs()
+        reqs = serving_stream(gs, args.duration + args.serve_warmup, args.rate, 31)
+        times, arcs = [], 0
+        for i in range(args.steps):
+            _, gi, srcs = reqs[(args.warmup + i) % len(reqs)]
+            t0 = time.perf_counter()
+            _, st = oracle.bc(gs[gi], srcs)
+            times.append(time.perf_counter() - t0)
+            arcs += int(st["arcs"].sum())
+        tot = sum(times)
+        value = arcs / tot / 1e9
+        print(json.dumps({
+            "impl": "reference", "metric": "BC GTEPS (serving)", "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "requests_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": "one request of the stream per step"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    w, g, srcs = workload_inputs(args.workload, rank)
 
     per_step = max(1, args.ref_sources)
     for i in range(args.warmup):
@@ -348,6 +507,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sources", type=int, default=1, help="reference arm: oracle sources per step")
+    ap.add_argument("--duration", type=float, default=30.0, help="serving: measured stream length (s)")
+    ap.add_argument("--serve-warmup", type=float, default=5.0, help="serving: warm-up part of the stream (s)")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
+    ap.add_argument("--serve-budget", type=int, default=64, help="serving: device memory budget (GiB)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("note: fewer than 3 warm-up steps")
@@ -367,6 +531,9 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.workload == "serving_8graphs":
+            if rank == 0:
+                run_serving(args, world)
         else:
             run_ours(args, rank, world, dist)
     finally:

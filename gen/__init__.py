@@ -232,6 +232,8 @@ def workload_graph(name: str) -> Graph:
         return knn2d(1_000_000, 4, 3)
     if name == "rmat22":
         return rmat(22, 16, 4)
+    if name == "rmat21":
+        return rmat(21, 16, 4)
     raise KeyError(name)
 
 

@@ -219,6 +219,8 @@ SP_API sp_status sp_bc_wait(sp_server s, sp_request req, int64_t timeout_ns); /*
 SP_API sp_status sp_bc_cancel(sp_server s, sp_request req);
 /* Host steady-clock times in ns: submission, first batch start, completion (0 if not yet). */
 SP_API sp_status sp_request_times(sp_server s, sp_request req, int64_t* submit_ns, int64_t* start_ns, int64_t* done_ns);
+/* Statistics of a request, summed over its batches (valid once it is done). */
+SP_API sp_status sp_request_stats(sp_server s, sp_request req, sp_bc_stats* out);
 SP_API sp_status sp_server_destroy(sp_server s); /* waits for running requests */
 
 /* ------------------------------------------------------------------------ */

@@ -81,6 +81,7 @@ SIGNATURES = {
     "sp_bc_wait": ([_P, _I64, _I64], ctypes.c_int),
     "sp_bc_cancel": ([_P, _I64], ctypes.c_int),
     "sp_request_times": ([_P, _I64, _P, _P, _P], ctypes.c_int),
+    "sp_request_stats": ([_P, _I64, _P], ctypes.c_int),
     "sp_server_destroy": ([_P], ctypes.c_int),
     "sp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "sp_last_error": ([], ctypes.c_char_p),
@@ -272,6 +273,12 @@ def sp_request_times(s: int, req: int):
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(lib.sp_request_times(s, req, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "sp_request_times")
     return a.value, b.value, c.value
+
+
+def sp_request_stats(s: int, req: int) -> dict:
+    st = sp_bc_stats()
+    _check(lib.sp_request_stats(s, req, ctypes.byref(st)), "sp_request_stats")
+    return st.as_dict()
 
 
 def sp_server_destroy(s: int):

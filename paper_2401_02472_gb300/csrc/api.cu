@@ -167,6 +167,22 @@ static std::tuple<int32_t, int64_t, int32_t, int32_t> tune_key(const Graph* g, i
     return std::make_tuple(g->n, g->nnz, g->info.max_degree, (int32_t)precision);
 }
 
+// Representation hints learnt by earlier calls on a graph with the same
+// signature: path counts past 64 bits (bit 0), FP32 dependencies out of range
+// (bit 1).  They only skip attempts that would fail and be rerun.
+static std::map<std::tuple<int32_t, int64_t, int32_t>, int> g_hints;
+
+static int range_hints(const Graph* g) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_hints.find(std::make_tuple(g->n, g->nnz, g->info.max_degree));
+    return it == g_hints.end() ? 0 : it->second;
+}
+
+static void add_range_hint(const Graph* g, int bit) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_hints[std::make_tuple(g->n, g->nnz, g->info.max_degree)] |= bit;
+}
+
 static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
                            sp_bc_stats* stats, cudaStream_t st);
 
@@ -319,8 +335,12 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
     }
     bool theta_f32 = o.precision == SP_FP32_DELTA;
     {
+        const int hints = range_hints(g);
         std::lock_guard<std::mutex> lk(g->mu);
+        if (hints & 1) g->sigma_float = true;
+        if (hints & 2) g->theta_f64 = true;
         if (g->theta_f64) theta_f32 = false;
+        sigma_float = g->sigma_float;
     }
     {
         sp_status rc = ensure_top_bfs(g, st);
@@ -329,7 +349,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
     int form = o.form;
     // Automatic form: many narrow levels (high diameter) favour small block
     // groups, one source each; wide levels and many sources favour batches.
-    if (form == SP_FORM_AUTO) form = (nsrc >= 16 && g->top_levels <= 64) ? SP_FORM_BATCHED : SP_FORM_PLAIN;
+    if (form == SP_FORM_AUTO) form = (nsrc >= 2 && g->top_levels <= 64) ? SP_FORM_BATCHED : SP_FORM_PLAIN;
     int width = 1, launches = 0, tuned = 0;
     if (form == SP_FORM_BATCHED) {
         if (o.batch > 0) {
@@ -412,6 +432,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         if (r.err == kErrSigmaOverflow && !sigma_float) {
             sigma_float = true;
             sigma_batches = 1;
+            add_range_hint(g, 1);
             std::lock_guard<std::mutex> lk(g->mu);
             g->sigma_float = true;
             continue;
@@ -419,6 +440,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         if (r.err == kErrThetaRange32 && theta_f32) {
             theta_f32 = false;
             promoted = 1;
+            add_range_hint(g, 2);
             std::lock_guard<std::mutex> lk(g->mu);
             g->theta_f64 = true;
             continue;

@@ -31,12 +31,13 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     int grid = per_sm * device_sm_count(dev);
     if (L.max_ctas > 0 && L.max_ctas < grid) grid = L.max_ctas;
     // Groups: `group_blocks` blocks each (0 = one group of every block), no
-    // more groups than sources; a fault-injection run keeps one group so that
-    // the skipped barrier is a real multi-block wait.
+    // more groups than sources (blocks beyond them are not launched: narrow
+    // levels gain nothing from more blocks but barrier cost); a
+    // fault-injection run keeps one group so that the skipped barrier is a
+    // real multi-block wait.
     int gblocks = L.group_blocks > 0 ? std::min(L.group_blocks, grid) : grid;
     if (L.debug_flags & SP_DEBUG_SKIP_BARRIER) gblocks = grid;
     int ngroups = std::max(1, std::min(grid / gblocks, std::max(1, L.nsrc)));
-    if (ngroups > 1 && grid / ngroups > gblocks) gblocks = grid / ngroups;  // spread spare blocks
     grid = ngroups * gblocks;
 
     // Workspace: one copy of the per-source arrays per group.

@@ -69,6 +69,7 @@ struct Request {
     sp_status status = SP_NOT_READY;
     bool admitted = false, cancelled = false, finished = false;
     int64_t t_submit = 0, t_start = 0, t_done = 0;
+    sp_bc_stats stats{};  // summed over the request's batches
 };
 
 struct Server {
@@ -143,6 +144,7 @@ struct Server {
             lk.unlock();
 
             sp_status rc = SP_OK;
+            sp_bc_stats bst{};
             if (!skip) {
                 if (r->partials == nullptr && r->nbatches > 1) rc = SP_ERR_OOM;
                 const int lo = b * r->width;
@@ -160,7 +162,7 @@ struct Server {
                     o.max_ctas = std::max(1, (sms * 4) / slots);
                     if (o.batch == 0 && o.form != SP_FORM_PLAIN) o.batch = r->width;
                     double* out = r->nbatches > 1 ? r->partials + (size_t)b * r->g->n : r->bc_out;
-                    rc = bc_device_entry(r->g, d_src, cnt, o, out, nullptr, st);
+                    rc = bc_device_entry(r->g, d_src, cnt, o, out, &bst, st);
                 }
                 if (d_src) cudaFreeAsync(d_src, st);
                 cudaStreamSynchronize(st);
@@ -168,6 +170,21 @@ struct Server {
 
             lk.lock();
             if (rc != SP_OK && r->status == SP_NOT_READY) r->status = rc;
+            if (rc == SP_OK && !skip) {
+                r->stats.traversed_arcs += bst.traversed_arcs;
+                r->stats.reached += bst.reached;
+                r->stats.entries += bst.entries;
+                r->stats.scanned_arcs += bst.scanned_arcs;
+                r->stats.dag_arcs += bst.dag_arcs;
+                r->stats.kernel_ms += bst.kernel_ms;
+                r->stats.max_levels = std::max(r->stats.max_levels, bst.max_levels);
+                r->stats.batches += 1;
+                r->stats.batch = r->width;
+                r->stats.form = bst.form;
+                r->stats.promoted |= bst.promoted;
+                r->stats.sigma_float |= bst.sigma_float;
+                r->stats.launches += bst.launches;
+            }
             r->done_batches++;
             if (r->done_batches == r->nbatches) {
                 sp_status fin = r->cancelled ? SP_ERR_CANCELLED : r->status;
@@ -266,7 +283,7 @@ sp_status sp_bc_submit(sp_server sh, int32_t graph_id, const int32_t* sources, i
             if (r->sources[i] < 0 || r->sources[i] >= g->n)
                 return fail(SP_ERR_INVALID_ARG, "source " + std::to_string(i) + " out of range");
     }
-    const bool plain = r->opts.form == SP_FORM_PLAIN || (r->opts.form == SP_FORM_AUTO && nsrc < 16);
+    const bool plain = r->opts.form == SP_FORM_PLAIN || (r->opts.form == SP_FORM_AUTO && nsrc < 2);
     r->width = plain ? std::max(1, nsrc) : (r->opts.batch > 0 ? r->opts.batch : default_batch_width(nsrc));
     r->nbatches = nsrc == 0 ? 1 : (nsrc + r->width - 1) / r->width;
     const bool theta32 = r->opts.precision == SP_FP32_DELTA;
@@ -348,6 +365,16 @@ sp_status sp_request_times(sp_server sh, sp_request req, int64_t* submit_ns, int
     if (submit_ns) *submit_ns = it->second->t_submit;
     if (start_ns) *start_ns = it->second->t_start;
     if (done_ns) *done_ns = it->second->t_done;
+    return SP_OK;
+}
+
+sp_status sp_request_stats(sp_server sh, sp_request req, sp_bc_stats* out) {
+    if (!sh || !out) return fail(SP_ERR_INVALID_ARG, "NULL argument");
+    Server* s = reinterpret_cast<Server*>(sh);
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(req);
+    if (it == s->reqs.end()) return fail(SP_ERR_INVALID_ARG, "unknown request");
+    *out = it->second->stats;
     return SP_OK;
 }
 

@@ -1,0 +1,109 @@
+"""Serving: continuous batching of BC requests over resident graphs.
+
+Each request's result must equal the oracle within the tolerance and be
+bit-identical whether it ran alone or mixed with other requests.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2401_02472_gb300 as sp
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+RTOL = {sp.SP_FP64: 1e-9, sp.SP_FP32_DELTA: 1e-4}
+
+
+def close(got, want, rtol):
+    return bool(np.all(np.abs(got - want) <= rtol * np.maximum(np.abs(want), 1.0)) and
+                np.all(got[want == 0.0] == 0.0))
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    gs = [gen.rmat(12, 16, 2), gen.knn2d(4000, 4, 3), gen.er(3000, 24000, 5)]
+    return gs, [sp.Graph(g.row_ptr, g.col_idx) for g in gs]
+
+
+def requests(gs, count, seed):
+    """(graph index, sources, precision) per request; nsrc log-uniform in [1, 300]."""
+    sizes = gen.log_uniform_int(1, 300, seed, count)
+    which = gen.draws(gen.substream(seed, 3), 0, count) % np.uint64(len(gs))
+    out = []
+    for i in range(count):
+        gi = int(which[i])
+        k = int(min(sizes[i], (gs[gi].degrees() > 0).sum()))
+        srcs = gen.sources(gs[gi], k, 1000 + seed * 100 + i)
+        out.append((gi, srcs, sp.SP_FP32_DELTA if i % 2 else sp.SP_FP64))
+    return out
+
+
+def serve(Gs, reqs, slots=4, budget=8 << 30):
+    s = sp.sp_server_create(budget, slots)
+    ids = [sp.sp_server_add_graph(s, G.handle) for G in Gs]
+    outs, handles = [], []
+    for gi, srcs, prec in reqs:
+        out = torch.full((Gs[gi].n,), -1.0, dtype=torch.float64, device=DEV)
+        h = sp.sp_bc_submit(s, ids[gi], srcs, out, sp.make_opts(precision=prec))
+        outs.append(out)
+        handles.append(h)
+    for h in handles:
+        assert sp.sp_bc_wait(s, h) == sp.SP_OK
+    times = [sp.sp_request_times(s, h) for h in handles]
+    stats = [sp.sp_request_stats(s, h) for h in handles]
+    sp.sp_server_destroy(s)
+    torch.cuda.synchronize()
+    return [o.cpu().numpy() for o in outs], times, stats
+
+
+def test_mixed_requests_match_oracle_and_run_alone(graphs):
+    gs, Gs = graphs
+    reqs = requests(gs, 14, 7)
+    mixed, times, stats = serve(Gs, reqs)
+    for (gi, srcs, prec), got, (t0, t1, t2), st in zip(reqs, mixed, times, stats):
+        want, ost = oracle.bc(gs[gi], srcs)
+        assert close(got, want, RTOL[prec]), (gi, len(srcs), prec)
+        assert 0 < t0 <= t1 <= t2
+        assert st["traversed_arcs"] == int(ost["arcs"].sum())
+    # every third request again, alone on a fresh server: bit-identical
+    for i in range(0, len(reqs), 3):
+        alone, _, _ = serve(Gs, [reqs[i]])
+        assert np.array_equal(alone[0], mixed[i]), i
+
+
+def test_budget_smaller_than_a_request_still_runs(graphs):
+    gs, Gs = graphs
+    reqs = requests(gs, 5, 11)
+    got, _, _ = serve(Gs, reqs, slots=2, budget=1)  # one request at a time
+    for (gi, srcs, prec), g in zip(reqs, got):
+        want, _ = oracle.bc(gs[gi], srcs)
+        assert close(g, want, RTOL[prec])
+
+
+def test_poll_cancel_and_empty_requests(graphs):
+    gs, Gs = graphs
+    s = sp.sp_server_create(8 << 30, 1)
+    gid = sp.sp_server_add_graph(s, Gs[0].handle)
+    big = [sp.sp_bc_submit(s, gid, gen.sources(gs[0], 300, 50 + i),
+                           torch.empty(gs[0].n, dtype=torch.float64, device=DEV)) for i in range(3)]
+    out = torch.empty(gs[0].n, dtype=torch.float64, device=DEV)
+    late = sp.sp_bc_submit(s, gid, gen.sources(gs[0], 200, 99), out)
+    rc = sp.sp_bc_cancel(s, late)
+    assert rc in (sp.SP_OK, sp.SP_ERR_CANCELLED)
+    final = sp.lib.sp_bc_wait(s, late, -1)
+    assert final in (sp.SP_ERR_CANCELLED, sp.SP_OK)
+    empty_out = torch.full((gs[0].n,), 7.0, dtype=torch.float64, device=DEV)
+    e = sp.sp_bc_submit(s, gid, np.zeros(0, np.int32), empty_out)
+    assert sp.sp_bc_poll(s, e) == sp.SP_OK
+    for h in big:
+        assert sp.sp_bc_wait(s, h) == sp.SP_OK
+    sp.sp_server_destroy(s)
+    assert torch.count_nonzero(empty_out).item() == 0
+    with pytest.raises(sp.StarbcError):
+        s2 = sp.sp_server_create(1 << 30, 2)
+        try:
+            sp.sp_bc_submit(s2, 5, np.array([0], np.int32), empty_out)
+        finally:
+            sp.sp_server_destroy(s2)
