@@ -277,6 +277,26 @@ def algorithmic_bytes(st: dict, n: int, form: str, theta_bytes: int, width: int)
     return int(b)
 
 
+def combine_ranks(dist, world, total_ms, steps, arcs, e2e_s, e2e_arcs, device="cpu"):
+    """Whole-job throughput: units of all ranks / the slowest rank's time.
+
+    Returns (GTEPS, end-to-end GTEPS, max over ranks of the timed region in ms).
+    """
+    import torch
+
+    t = torch.tensor([total_ms, float(arcs), e2e_s, float(e2e_arcs)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        parts = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(parts, t)
+        allt = torch.stack(parts).cpu().numpy()
+    else:
+        allt = t.cpu().numpy()[None, :]
+    total_ms_max = float(allt[:, 0].max())
+    value = float(allt[:, 1].sum()) / (total_ms_max / steps / 1e3) / 1e9
+    e2e_value = float(allt[:, 3].sum()) / float(allt[:, 2].max()) / 1e9
+    return value, e2e_value, total_ms_max
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -434,22 +454,8 @@ def run_ours(args, rank, world, dist):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
     arcs = stats[-1]["traversed_arcs"]
-    gteps_rank = arcs / (total_ms / args.steps / 1e3) / 1e9
-    e2e_rank = st_e["traversed_arcs"] / e2e_s / 1e9
-    # aggregate: units over all ranks / max time over ranks
-    if dist is not None:
-        t = torch.tensor([total_ms, float(arcs), e2e_s, float(st_e["traversed_arcs"])], dtype=torch.float64,
-                         device=dev)
-        allt = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(allt, t)
-        allt = torch.stack(allt).cpu().numpy()
-        total_ms_max = allt[:, 0].max()
-        value = allt[:, 1].sum() / (total_ms_max / args.steps / 1e3) / 1e9
-        e2e_value = allt[:, 3].sum() / allt[:, 2].max() / 1e9
-    else:
-        total_ms_max = total_ms
-        value = gteps_rank
-        e2e_value = e2e_rank
+    value, e2e_value, total_ms_max = combine_ranks(dist, world, total_ms, args.steps, arcs, e2e_s,
+                                                   st_e["traversed_arcs"], dev)
     if rank != 0:
         return
 
