@@ -35,6 +35,7 @@
 namespace sp {
 
 constexpr int kBatchThreads = 256;
+
 #ifndef SP_BATCH_MINB
 #define SP_BATCH_MINB 4  // resident blocks per SM the register budget is sized for
 #endif
@@ -65,6 +66,8 @@ struct BatchArgs {
     int32_t* hdone;           // [2*hcap]
     void* part;               // [segcap][B] 8-byte slots
     int32_t segcap;
+    unsigned long long* smax; // [lcap] largest integer path count of each level
+    unsigned long long sig_limit;  // counts above this could overflow 64 bits in a sum of max-degree terms
     int32_t* emax;            // [lcap][B]
     int32_t* emin;            // [lcap][B]
     int32_t lcap;
@@ -124,13 +127,22 @@ struct BatchKernel {
     int hoff_d = 0, nrec_d = 0, nseg_d = 0, hoff_next = 0;  // hub records of level d / d+1
     int soff_d = 0, soff_next = 0;                            // segments of level d / d+1
     int stamp_next = 0;
+    bool backward = false;
     uint32_t* prev = nullptr;  // dense F_{d-1}
     uint32_t* cur = nullptr;   // dense F_d
     uint32_t* next = nullptr;  // dense F_{d+1}
     int cshift[W];             // per-source shift between level d-1 and d (forward) / d and d+1 (backward)
     int my_emax[W], my_emin[W];
     bool ovf = false;
+    unsigned long long my_smax = 0;  // largest integer path count this thread stored at this level
     unsigned long long st_arcs = 0, st_reached = 0, st_entries = 0, st_scanned = 0, st_dag = 0;
+
+    // Arcs whose row loads a warp issues together: chunks, and segments of long rows.
+    static constexpr int kGChunk = W >= 8 ? 2 : 8 / W;
+#ifndef SP_GSEG
+#define SP_GSEG 16
+#endif
+    static constexpr int kGSeg = (SP_GSEG / W) > 0 ? SP_GSEG / W : 1;
 
     __device__ BatchKernel(const BatchArgs& args) : a(args), ctl(args.ctl), lane(lane_id()) {
 #pragma unroll
@@ -194,10 +206,14 @@ struct BatchKernel {
     // Loads of G arcs are issued before any of them is added, so that a warp
     // keeps G*W row loads in flight.  on_owner(o) runs before the arcs of
     // entry o are added.
-    template <bool CHECK_OVF, typename RowT, typename AccType, typename OnOwner>
+    template <int G, typename RowT, typename AccType, typename OnOwner>
     __device__ __forceinline__ void pull_window(const RowT* base, int u, int owner, const uint32_t (&m)[W],
                                                 unsigned pend, AccType (&acc)[W], OnOwner&& on_owner) {
-        constexpr int G = W >= 8 ? 1 : 8 / W;
+        // which of the lane's mask words are non-empty: words without bits
+        // are skipped by the whole warp (regrouped sources leave most empty)
+        uint32_t wm = 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k) wm |= (m[k] != 0u ? 1u : 0u) << k;
         while (pend) {
             int jj[G];
 #pragma unroll
@@ -207,16 +223,22 @@ struct BatchKernel {
             }
             AccType x[G][W];
             int oi[G];
+            uint32_t wi[G];
 #pragma unroll
             for (int i = 0; i < G; ++i) {
                 const int srcl = jj[i] >= 0 ? jj[i] : 0;
                 const int ui = __shfl_sync(kFull, u, srcl);
                 oi[i] = __shfl_sync(kFull, owner, srcl);
+                wi[i] = __shfl_sync(kFull, wm, srcl);
+                if (jj[i] < 0) wi[i] = 0u;
                 const RowT* row = base + (size_t)ui * B + lane;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
-                    const uint32_t mk = __shfl_sync(kFull, m[k], srcl);
-                    x[i][k] = (jj[i] >= 0 && ((mk >> lane) & 1u)) ? (AccType)__ldcg(row + k * 32) : (AccType)0;
+                    x[i][k] = (AccType)0;
+                    if ((wi[i] >> k) & 1u) {
+                        const uint32_t mk = __shfl_sync(kFull, m[k], srcl);
+                        if ((mk >> lane) & 1u) x[i][k] = (AccType)__ldcg(row + k * 32);
+                    }
                 }
             }
 #pragma unroll
@@ -224,15 +246,8 @@ struct BatchKernel {
                 if (jj[i] < 0) break;
                 on_owner(oi[i]);
 #pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    if constexpr (CHECK_OVF) {
-                        AccType s2 = acc[k] + x[i][k];
-                        ovf |= s2 < x[i][k];
-                        acc[k] = s2;
-                    } else {
-                        acc[k] += x[i][k];
-                    }
-                }
+                for (int k = 0; k < W; ++k)
+                    if ((wi[i] >> k) & 1u) acc[k] += x[i][k];
             }
         }
     }
@@ -252,6 +267,7 @@ struct BatchKernel {
                     my_emin[k] = min(my_emin[k], e);
                 } else {
                     sig()[idx] = acc[k];
+                    my_smax = acc[k] > my_smax ? acc[k] : my_smax;
                 }
             }
         }
@@ -381,7 +397,7 @@ struct BatchKernel {
 #pragma unroll
                 for (int k = 0; k < W; ++k) anym |= m[k];
                 const unsigned pend = __ballot_sync(kFull, anym != 0u);
-                pull_window<!kFloatSig>(sig(), u, j, m, pend, acc, [&](int ej) {
+                pull_window<kGChunk>(sig(), u, j, m, pend, acc, [&](int ej) {
                     if (ej != cur_e) {
                         flush_current();
                         cur_e = ej;
@@ -439,7 +455,7 @@ struct BatchKernel {
 #pragma unroll
                 for (int k = 0; k < W; ++k) anym |= m[k];
                 const unsigned pend = __ballot_sync(kFull, anym != 0u);
-                pull_window<!kFloatSig>(sig(), u, 0, m, pend, acc, [](int) {});
+                pull_window<kGSeg>(sig(), u, 0, m, pend, acc, [](int) {});
             }
         }
         if (lane == 0) st_scanned += (unsigned long long)(end - beg);
@@ -477,14 +493,7 @@ struct BatchKernel {
             const SigT* pr = reinterpret_cast<const SigT*>(a.part) + (size_t)(sb + q) * B + lane;
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                SigT x = __ldcg(pr + k * 32);
-                if constexpr (kFloatSig) {
-                    tot[k] += x;
-                } else {
-                    SigT s2 = tot[k] + x;
-                    ovf |= s2 < x;
-                    tot[k] = s2;
-                }
+                tot[k] += __ldcg(pr + k * 32);
             }
         }
         count_entry();
@@ -549,7 +558,7 @@ struct BatchKernel {
                 anym |= m[k];
             }
             const unsigned pend = __ballot_sync(kFull, has && anym != 0u);
-            pull_window<false>(th(), w, j, m, pend, acc, [&](int ej) {
+            pull_window<kGChunk>(th(), w, j, m, pend, acc, [&](int ej) {
                 if (ej > next_flush) flush_upto(ej);
             });
         }
@@ -596,7 +605,7 @@ struct BatchKernel {
                 for (int k = 0; k < W; ++k) { m[k] = c[k] & F[k]; anym |= m[k]; }
             }
             const unsigned pend = __ballot_sync(kFull, anym != 0u);
-            pull_window<false>(th(), w, 0, m, pend, acc, [](int) {});
+            pull_window<kGSeg>(th(), w, 0, m, pend, acc, [](int) {});
         }
         if (lane == 0) st_scanned += (unsigned long long)(end - beg);
         if (nseg == 1) {
@@ -668,9 +677,26 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
     int qsnap = 0;  // level-stack fill at the last barrier
     int levels_max = 0;
     int stamp_base = 1;
+#ifdef SP_PROFILE
+    unsigned long long prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long prof_t = clock64();
+#define SP_PROF_MARK(cat)                        \
+    do {                                         \
+        unsigned long long t_ = clock64();       \
+        prof[(cat)] += t_ - prof_t;              \
+        prof_t = t_;                             \
+    } while (0)
+#else
+#define SP_PROF_MARK(cat) do {} while (0)
+#endif
     auto sync = [&]() -> bool {
         bool skip = (a.debug_flags & SP_DEBUG_SKIP_BARRIER) && blockIdx.x == 0 && phase == 1;
+        SP_PROF_MARK(5);
         bool ok = grid_sync(ctl, gridDim.x, a.timeout_ns, phase++, skip, &qsnap);
+        SP_PROF_MARK(4);
+#ifdef SP_PROFILE
+        if (tid == 0 && phase < 256) ctl->phase_ns[phase] = globaltimer();
+#endif
         if (tid == 0) ctl->work[(phase + 2) & 3] = 0u;
         return ok;
     };
@@ -683,8 +709,14 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
             if (lane == 0) item = (int)atomicAdd(&ctl->work[phase & 3], 1u);
             item = __shfl_sync(kFull, item, 0);
             if (item >= total) break;
-            if (item < nitems_hub) on_hub(item);
-            else on_chunk(qb + (item - nitems_hub) * kWarp);
+            SP_PROF_MARK(5);
+            if (item < nitems_hub) {
+                on_hub(item);
+                SP_PROF_MARK(K.d >= 0 && !K.backward ? 1 : 3);
+            } else {
+                on_chunk(qb + (item - nitems_hub) * kWarp);
+                SP_PROF_MARK(K.d >= 0 && !K.backward ? 0 : 2);
+            }
         }
     };
 
@@ -703,6 +735,8 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
             a.eoff[0] = 0;
             a.hoff[0] = 0;
             a.soff[0] = 0;
+            a.smax[0] = 1ull;
+            a.smax[1] = 0ull;
         }
         if constexpr (kFloatSig) {
             for (int i = tid; i < B; i += nthr) {
@@ -758,6 +792,13 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
                 a.hoff[d] = hoff_d;
                 a.soff[d] = soff_d;
                 if (d + 2 < a.lcap + 2) a.hcnt[d + 2] = 0ull;
+                if (d + 1 < a.lcap) a.smax[d + 1] = 0ull;
+            }
+            // Integer path counts: level d sums at most max-degree counts of
+            // level d-1, so they cannot overflow while level d-1 stays below
+            // the limit; past it the call reruns with FP64 counts.
+            if constexpr (!kFloatSig) {
+                if (d > 0 && tid == 0 && ld_volatile(&a.smax[d - 1]) > a.sig_limit) set_error(ctl, kErrSigmaOverflow);
             }
             // clear dense F_{d-2}
             if (d >= 2) {
@@ -770,7 +811,15 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
             }
             work(K.nseg_d, qb, qe, [&](int g) { K.fwd_hub_segment(g); }, [&](int e0) { K.fwd_chunk(e0, qe); });
             K.flush_exponents(d);
-            if (K.ovf) set_error(ctl, kErrSigmaOverflow);
+            if constexpr (!kFloatSig) {
+                unsigned long long mx = K.my_smax;
+                for (int o = 16; o > 0; o >>= 1) {
+                    unsigned long long y = shfl_u64(kFull, mx, lane ^ o);
+                    mx = y > mx ? y : mx;
+                }
+                if (lane == 0 && mx > 0 && d < a.lcap) atomicMax(&a.smax[d], mx);
+                K.my_smax = 0;
+            }
             if (!sync()) goto out;
             const int nq = qsnap;
             hoff_d = K.hoff_next;
@@ -784,6 +833,7 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
         levels_max = max(levels_max, L);
 
         // ---- backward ----
+        K.backward = true;
         for (int dd = L - 1; dd >= 1; --dd) {
             K.d = dd;
             K.next = a.dense + (size_t)((dd + 1) & 3) * n * W;  // dense F_{dd+1}
@@ -825,6 +875,7 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
             if (!sync()) goto out;
         }
 
+        K.backward = false;
         // ---- cleanup: dense levels 0..2, seen of the sources; reset the stack ----
         for (int j = 0; j < 3 && j < L; ++j) {
             const int cb = ld_volatile(&a.eoff[j]), ce = ld_volatile(&a.eoff[j + 1]);
@@ -864,6 +915,10 @@ out:
             int e = ld_volatile(&ctl->err);
             if (e != 0 && a.err_latch) *(volatile int*)a.err_latch = e;
         }
+#ifdef SP_PROFILE
+        if ((threadIdx.x & 31) == 0)
+            for (int c = 0; c < 8; ++c) atomicAdd(&ctl->prof[c], prof[c]);
+#endif
     }
 }
 

@@ -1,6 +1,7 @@
 // Host side of the batched form for one width: workspace layout and launch.
 #pragma once
 
+#include <cstdio>
 #include <cstring>
 #include <string>
 
@@ -58,6 +59,7 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     size_t o_hubs = take(sizeof(HubRec) * (size_t)hcap);
     size_t o_hdone = take(sizeof(int32_t) * 2 * (size_t)hcap);
     size_t o_part = take(8 * (size_t)segcap * B);
+    size_t o_smax = take(sizeof(unsigned long long) * (size_t)lcap);
     size_t o_emax = take(sizeof(int32_t) * (size_t)lcap * B);
     size_t o_emin = take(sizeof(int32_t) * (size_t)lcap * B);
 
@@ -96,6 +98,8 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.hdone = reinterpret_cast<int32_t*>(ws + o_hdone);
     a.part = ws + o_part;
     a.segcap = (int32_t)segcap;
+    a.smax = reinterpret_cast<unsigned long long*>(ws + o_smax);
+    a.sig_limit = ~0ull / (unsigned long long)std::max(1, g->info.max_degree);
     a.emax = reinterpret_cast<int32_t*>(ws + o_emax);
     a.emin = reinterpret_cast<int32_t*>(ws + o_emin);
     a.lcap = (int32_t)lcap;
@@ -136,6 +140,21 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     cudaEventDestroy(ev1);
     result->launches = 1;
     result->grid = grid;
+#ifdef SP_PROFILE
+    {
+        const char* names[8] = {"fwd chunks", "fwd segments", "bwd chunks", "bwd segments", "barrier", "other",
+                                "-", "-"};
+        unsigned long long tot = 0;
+        for (int c = 0; c < 6; ++c) tot += h.prof[c];
+        fprintf(stderr, "profile W=%d grid=%d kernel %.3f ms, levels %d\n", W, grid, result->kernel_ms, h.max_levels);
+        for (int c = 0; c < 6; ++c)
+            fprintf(stderr, "  %-13s %6.2f%%\n", names[c], tot ? 100.0 * (double)h.prof[c] / (double)tot : 0.0);
+        fprintf(stderr, "  phase ms:");
+        for (int p = 2; p < 256 && h.phase_ns[p]; ++p)
+            fprintf(stderr, " %.3f", (double)(h.phase_ns[p] - h.phase_ns[p - 1]) * 1e-6);
+        fprintf(stderr, "\n");
+    }
+#endif
     if (h.err == SP_ERR_TIMEOUT) result->diag = barrier_diagnostic(h, grid);
     result->ecap = ecap;
     result->hcap = hcap;

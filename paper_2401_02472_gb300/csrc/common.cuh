@@ -45,6 +45,8 @@ struct Ctl {
     int max_levels;
     unsigned int timeout_count;      // arrivals seen by the first wait that timed out
     int snap[2];                     // qtail as the last block found it, per barrier parity
+    unsigned long long prof[8];      // SP_PROFILE builds: SM cycles by kind of work, summed over warps
+    unsigned long long phase_ns[256];  // SP_PROFILE builds: %globaltimer at each of the first barriers
     int block_phase[1024];           // last barrier each block arrived at (diagnostics)
 };
 
