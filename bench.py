@@ -394,7 +394,7 @@ def run_ours(args, rank, world, dist):
         srcs = srcs[:args.nsrc]
     prec = sp.SP_FP32_DELTA if w["precision"] == "fp32_delta" else sp.SP_FP64
     form = sp.SP_FORM_BATCHED if w["form"] == "batched" else sp.SP_FORM_PLAIN
-    opts = sp.make_opts(precision=prec, form=form, batch=args.batch)
+    opts = sp.make_opts(precision=prec, form=form, batch=args.batch, bottom_up=args.bottom_up)
     theta_bytes = 4 if prec == sp.SP_FP32_DELTA else 8
 
     d_rp = torch.as_tensor(g.row_ptr, device=dev)
@@ -509,6 +509,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="fixed batch width (0 = autotuned)")
     ap.add_argument("--form", default=None, choices=["plain", "batched"], help="override the workload's form")
     ap.add_argument("--nsrc", type=int, default=0, help="override the workload's source count")
+    ap.add_argument("--bottom-up", type=int, default=0, help="plain form: bottom-up on levels > n/this (-1 never)")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

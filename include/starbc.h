@@ -119,7 +119,10 @@ typedef struct {
     int64_t barrier_timeout_ns; /* per device-side wait; 0 = 20 s */
     int32_t debug_flags;        /* SP_DEBUG_* (tests only) */
     int32_t flags;              /* SP_BC_* */
-    int32_t reserved[2];
+    int32_t bottom_up;          /* plain form: discover bottom-up on levels holding more than n / bottom_up
+                                   vertices (direction-optimising BFS); 0 = default (100 on graphs of
+                                   2^20 or more vertices, else never), -1 = never */
+    int32_t reserved[1];
 } sp_bc_opts;
 
 /* flags: run the batched form's sources in the caller's order.  By default

@@ -32,7 +32,8 @@ SP_BC_KEEP_ORDER = 0x1
 class sp_bc_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("form", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("max_ctas", ctypes.c_int32), ("barrier_timeout_ns", ctypes.c_int64),
-                ("debug_flags", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("debug_flags", ctypes.c_int32), ("flags", ctypes.c_int32), ("bottom_up", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class sp_bc_stats(ctypes.Structure):
@@ -182,11 +183,11 @@ def sp_graph_check(g: int):
 
 
 def make_opts(precision=SP_FP64, form=SP_FORM_AUTO, batch=0, max_ctas=0, barrier_timeout_ns=0,
-              debug_flags=0, flags=0) -> sp_bc_opts:
+              debug_flags=0, flags=0, bottom_up=0) -> sp_bc_opts:
     o = sp_bc_opts()
     lib.sp_bc_opts_default(ctypes.byref(o))
     o.precision, o.form, o.batch, o.max_ctas = precision, form, batch, max_ctas
-    o.barrier_timeout_ns, o.debug_flags, o.flags = barrier_timeout_ns, debug_flags, flags
+    o.barrier_timeout_ns, o.debug_flags, o.flags, o.bottom_up = barrier_timeout_ns, debug_flags, flags, bottom_up
     return o
 
 

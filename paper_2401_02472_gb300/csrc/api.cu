@@ -288,6 +288,15 @@ static int plain_group_blocks(const Graph* g) {
     return (int)std::min<int64_t>((per_level + 8191) / 8192, 1 << 20);
 }
 
+// Bottom-up discovery threshold of the plain form: by default on levels
+// holding more than n/100 vertices of graphs with at least 2^20 vertices
+// (on small graphs the per-lane row scans cost more than the atomics they save).
+static int plain_bottom_up(const Graph* g, int32_t opt) {
+    if (opt < 0) return 0;
+    if (opt > 0) return opt;
+    return g->n >= (1 << 20) ? 100 : 0;
+}
+
 static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cudaStream_t st, int32_t** out) {
     *out = nullptr;
     if (nsrc < 2 || g->n == 0) return SP_OK;
@@ -407,6 +416,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             L.stream = st;
             L.group_blocks = plain_group_blocks(g);
             L.level_cap = plain_lcap;
+            L.bottom_up_den = plain_bottom_up(g, o.bottom_up);
             rc = run_plain(L, &r);
         } else {
             BatchedLaunch L{};
@@ -593,7 +603,7 @@ sp_status sp_bc_ex(sp_graph gh, const int32_t* sources, int32_t nsrc, const sp_b
     if (o.form < SP_FORM_AUTO || o.form > SP_FORM_BATCHED) return fail(SP_ERR_INVALID_ARG, "form");
     if (o.batch != 0 && o.batch != 32 && o.batch != 64 && o.batch != 128 && o.batch != 256)
         return fail(SP_ERR_INVALID_ARG, "batch must be 0, 32, 64, 128 or 256");
-    if (o.max_ctas < 0 || o.barrier_timeout_ns < 0) return fail(SP_ERR_INVALID_ARG, "negative option");
+    if (o.max_ctas < 0 || o.barrier_timeout_ns < 0 || o.bottom_up < -1) return fail(SP_ERR_INVALID_ARG, "negative option");
     if (o.flags & ~(int32_t)SP_BC_KEEP_ORDER) return fail(SP_ERR_INVALID_ARG, "unknown flag");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -656,6 +666,7 @@ sp_status sp_bfs(sp_graph gh, const int32_t* sources, int32_t nsrc, int32_t* dis
         L.stream = st;
         rc = ensure_top_bfs(g, st);
         L.group_blocks = plain_group_blocks(g);
+        L.bottom_up_den = plain_bottom_up(g, 0);
         LaunchResult r;
         for (int attempt = 0; rc == SP_OK && attempt < 2; ++attempt) {
             rc = run_plain(L, &r);

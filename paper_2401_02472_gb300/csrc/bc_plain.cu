@@ -113,6 +113,7 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     a.t_thread = tiers.t_thread;
     a.t_hub = tiers.t_hub;
     a.seg = tiers.seg;
+    a.bu_den = L.bottom_up_den;
     a.trace = reinterpret_cast<int*>(ws + o_trace);
     cudaMemsetAsync(a.trace, 0, sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32), st);
 

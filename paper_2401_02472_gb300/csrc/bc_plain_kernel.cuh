@@ -92,6 +92,7 @@ struct PlainArgs {
     int debug_flags;
     unsigned long long timeout_ns;
     int t_thread, t_hub, seg;
+    int bu_den;  // bottom-up discovery on levels with more than n / bu_den vertices (0 = never)
     int* trace;  // SP_TRACE builds: 8 ints per warp
 };
 
@@ -196,6 +197,7 @@ struct PlainKernel {
     int hoff_next = 0;                       // first hub record of level d+1
     int cshift_prev = 0;                     // centring shift between level d-1 and d
     int cshift_cur = 0;                      // centring shift between level d and d+1 (backward)
+    bool discover = true;                    // top-down discovery by the level's entries
     // per-thread accumulators
     int my_emax = INT_MIN, my_emin = INT_MAX;
     bool ovf = false;
@@ -246,7 +248,7 @@ struct PlainKernel {
         int lu = __ldcg(&lvl()[u]);
         SigT c = 0;
         if (lu < 0) {
-            if (atomicCAS(&lvl()[u], -1, d + 1) == -1) push(u, d + 1);
+            if (discover && atomicCAS(&lvl()[u], -1, d + 1) == -1) push(u, d + 1);
         } else if (lu == d - 1) {
             c = __ldcg(&sig()[u]);
             st_dag += 1;
@@ -400,10 +402,33 @@ struct PlainKernel {
         }
     }
 
+    // Bottom-up discovery of level d+1 (direction-optimising BFS, Beamer et
+    // al., SC 2012): each still-unvisited vertex of a range of 256 scans its
+    // row and stops at the first neighbour on level d.  Only the scanning
+    // thread writes the vertex's level, so no atomic is needed; path counts
+    // are pulled as usual when the vertex's level is processed.
+    __device__ void bottom_up_range(int base) {
+#pragma unroll 1
+        for (int i = 0; i < 8; ++i) {
+            const int u = base + i * kWarp + lane;
+            if (u < a.n && __ldcg(&lvl()[u]) < 0) {
+                const int b = __ldg(&a.rp[u]), e = __ldg(&a.rp[u + 1]);
+                for (int k = b; k < e; ++k) {
+                    st_scanned += 1;
+                    if (__ldcg(&lvl()[__ldg(&a.ci[k])]) == d) {
+                        lvl()[u] = d + 1;
+                        push(u, d + 1);
+                        break;
+                    }
+                }
+            }
+        }
+    }
+
     template <bool FWD>
-    __device__ void level_work(int phase, int qb, int qe, bool skip_arcs) {
+    __device__ void level_work(int phase, int qb, int qe, bool skip_arcs, int bu_items = 0) {
         int nchunks = (qe - qb + kWarp - 1) / kWarp;
-        int total = nseg_d + nchunks;
+        int total = nseg_d + nchunks + bu_items;
         while (true) {
             int item = 0;
             if (lane == 0) item = (int)atomicAdd(&gc->work[phase & 3], 1u);
@@ -416,7 +441,8 @@ struct PlainKernel {
 #endif
             if (item >= total) break;
             if (item < nseg_d) hub_segment<FWD>(item, skip_arcs);
-            else chunk<FWD>(qb + (item - nseg_d) * kWarp, qe, skip_arcs);
+            else if (item < nseg_d + nchunks) chunk<FWD>(qb + (item - nseg_d) * kWarp, qe, skip_arcs);
+            else bottom_up_range((item - nseg_d - nchunks) * (8 * kWarp));
         }
     }
 };
@@ -507,7 +533,11 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
             }
             K.my_emax = INT_MIN;
             K.my_emin = INT_MAX;
-            K.template level_work<true>(phase, qb, qe, false);
+            // Direction: fat levels discover bottom-up.
+            const bool bu = a.bu_den > 0 && d > 0 && (int64_t)(qe - qb) * a.bu_den > (int64_t)n;
+            K.discover = !bu;
+            K.template level_work<true>(phase, qb, qe, false, bu ? (n + 8 * kWarp - 1) / (8 * kWarp) : 0);
+            K.discover = true;
             if constexpr (kFloatSig) {
                 int mx = warp_max_i32(K.my_emax), mn = warp_min_i32(K.my_emin);
                 if (K.lane == 0 && mx >= mn) {

@@ -70,6 +70,7 @@ struct PlainLaunch {
     cudaStream_t stream;
     int group_blocks;       // blocks per group (0 = one group of every block)
     int64_t level_cap;      // BFS levels per group; 0 = default
+    int bottom_up_den;      // bottom-up discovery on levels wider than n / this (0 = top-down only)
 };
 
 struct LaunchResult {

@@ -226,6 +226,19 @@ def test_run_to_run_bit_identical(form, batch):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("name", ["rmat12", "er2000", "knn5000", "mixed"])
+def test_plain_direction_does_not_change_results(name):
+    # Bottom-up discovery on wide levels (any level above n/2, n/20, or never)
+    # finds the same levels, so the per-vertex sums and BC are bit-identical.
+    g, G = graph(name)
+    srcs = gen.sources(g, min(20, int((g.degrees() > 0).sum())), 31)
+    runs = [gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_PLAIN, bottom_up=bu)[0] for bu in (-1, 2, 20, 1000)]
+    for r in runs[1:]:
+        assert np.array_equal(r, runs[0])
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(runs[0], want, 1e-9)
+
+
 @pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
 def test_source_order_only_changes_rounding(precision):
     # The batched form regroups sources by distance from a maximum-degree
