@@ -394,7 +394,8 @@ def run_ours(args, rank, world, dist):
         srcs = srcs[:args.nsrc]
     prec = sp.SP_FP32_DELTA if w["precision"] == "fp32_delta" else sp.SP_FP64
     form = sp.SP_FORM_BATCHED if w["form"] == "batched" else sp.SP_FORM_PLAIN
-    opts = sp.make_opts(precision=prec, form=form, batch=args.batch, bottom_up=args.bottom_up)
+    driver = {"auto": sp.SP_DRIVER_AUTO, "persistent": sp.SP_DRIVER_PERSISTENT, "graph": sp.SP_DRIVER_GRAPH}[args.driver]
+    opts = sp.make_opts(precision=prec, form=form, batch=args.batch, bottom_up=args.bottom_up, driver=driver)
     theta_bytes = 4 if prec == sp.SP_FP32_DELTA else 8
 
     d_rp = torch.as_tensor(g.row_ptr, device=dev)
@@ -494,7 +495,7 @@ def run_ours(args, rank, world, dist):
         "detail": {"traversed_arcs_per_step": arcs, "dag_arcs": s["dag_arcs"], "entries": s["entries"],
                    "scanned_arcs": s["scanned_arcs"], "reached": s["reached"], "step_ms": step_ms,
                    "wall_s": t_wall, "tuned_batch": s["batch"], "promoted": s["promoted"],
-                   "sigma_float": s["sigma_float"]},
+                   "sigma_float": s["sigma_float"], "driver": s["driver"]},
     }
     print(json.dumps(line), flush=True)
 
@@ -510,6 +511,8 @@ def main():
     ap.add_argument("--form", default=None, choices=["plain", "batched"], help="override the workload's form")
     ap.add_argument("--nsrc", type=int, default=0, help="override the workload's source count")
     ap.add_argument("--bottom-up", type=int, default=0, help="plain form: bottom-up on levels > n/this (-1 never)")
+    ap.add_argument("--driver", default="auto", choices=["auto", "persistent", "graph"],
+                    help="plain form: level loop in a persistent kernel or a CUDA graph")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

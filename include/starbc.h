@@ -22,18 +22,16 @@
  *
  * Pointers: every array argument may be host memory or device memory of the
  * current device; the library tells them apart with cudaPointerGetAttributes.
- * Calls whose outputs are in host memory return after the result is there;
- * calls whose outputs are in device memory are asynchronous on `stream` (a
- * cudaStream_t; NULL is the legacy default stream).
+ * Work is issued on `stream` (a cudaStream_t; NULL is the legacy default
+ * stream), and every call except sp_bc_submit returns once its result is
+ * complete, in host or device memory alike: the level loop runs inside
+ * persistent kernels whose error word the host reads at the end of the call.
  *
  * Errors: every entry point returns an sp_status.  Argument errors, allocation
- * failures and CUDA launch errors are returned at once.  Errors found by the
- * GPU while an asynchronous call runs (a path count out of range, a barrier
- * wait that timed out) are latched in the graph and returned by
- * sp_graph_check() once the stream has been synchronised, and by any later
- * synchronous call on the same graph.  sp_last_error() gives a one-line
- * description of the last failure on the calling thread.  Nothing here ever
- * aborts or traps the GPU.
+ * failures, CUDA errors and errors found by the GPU (a path count out of
+ * range, a device-side wait that timed out) are returned by the call that met
+ * them.  sp_last_error() gives a one-line description of the last failure on
+ * the calling thread.  Nothing here ever aborts or traps the GPU.
  */
 #ifndef STARBC_H
 #define STARBC_H
@@ -101,9 +99,6 @@ SP_API sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx,
                           uint32_t flags, sp_stream stream, sp_graph* out);
 SP_API sp_status sp_graph_destroy(sp_graph g);
 SP_API sp_status sp_graph_get_info(sp_graph g, sp_graph_info* out);
-/* Return (and clear) a device-side error latched by an earlier asynchronous
-   call on this graph; synchronise the stream of that call first. */
-SP_API sp_status sp_graph_check(sp_graph g);
 
 /* ------------------------------------------------------------------------ */
 /* Betweenness centrality                                                   */
@@ -122,8 +117,20 @@ typedef struct {
     int32_t bottom_up;          /* plain form: discover bottom-up on levels holding more than n / bottom_up
                                    vertices (direction-optimising BFS); 0 = default (100 on graphs of
                                    2^20 or more vertices, else never), -1 = never */
-    int32_t reserved[1];
+    int32_t driver;             /* plain form's level loop: SP_DRIVER_AUTO, _PERSISTENT or _GRAPH */
 } sp_bc_opts;
+
+/* driver: how the plain form steps from level to level (both give
+   bit-identical results when the persistent kernel runs one block group).
+   PERSISTENT: one cooperative kernel per call; blocks meet at timed device
+   barriers between levels and may form groups that run sources side by side.
+   GRAPH: a CUDA graph whose conditional WHILE node runs one kernel per level
+   plus a one-thread step that sets the loop condition on the device; one
+   source at a time over the whole GPU, no device-side waits.
+   AUTO: PERSISTENT, unless a timing trial on the first eight sources of a
+   call with at least 16 sources, run once per graph shape and cached, finds
+   GRAPH faster. */
+enum { SP_DRIVER_AUTO = 0, SP_DRIVER_PERSISTENT = 1, SP_DRIVER_GRAPH = 2 };
 
 /* flags: run the batched form's sources in the caller's order.  By default
    they are regrouped so that sources at similar distance from a maximum-degree
@@ -149,7 +156,9 @@ typedef struct {
     int32_t promoted;       /* 1 when FP32 dependencies left the FP32 range and the call reran with FP64 */
     int32_t sigma_float;    /* 1 when path counts needed FP64 with per-level rescaling (above 2^64) */
     int32_t launches;       /* kernel launches of the call, including reruns and autotuning trials */
-    int32_t tuned;          /* 1 when this call ran the batch-width autotuner */
+    int32_t tuned;          /* 1 when this call ran an autotuner (batch width, or the plain form's driver) */
+    int32_t driver;         /* plain form: SP_DRIVER_PERSISTENT or SP_DRIVER_GRAPH; 0 for the batched form */
+    int32_t reserved;
 } sp_bc_stats;
 
 SP_API void sp_bc_opts_default(sp_bc_opts* o);
@@ -158,11 +167,11 @@ SP_API void sp_bc_opts_default(sp_bc_opts* o);
  * BC over sources[0..nsrc) into bc_out[n] (FP64, overwritten, not accumulated:
  * the paper's attachNodeProperty(BC = 0) then the per-source sums).
  * sources: int32, host or device; each in [0, n).  nsrc == 0 gives all zeros.
- * bc_out: host or device.  Device outputs: asynchronous on `stream`.
+ * bc_out: host or device.  Returns when bc_out holds the result.
  */
 SP_API sp_status sp_bc(sp_graph g, const int32_t* sources, int32_t nsrc, double* bc_out, sp_stream stream);
 
-/* As sp_bc with options; `stats` (host, may be NULL) makes the call synchronous. */
+/* As sp_bc with options; `stats` (host, may be NULL) receives the call's statistics. */
 SP_API sp_status sp_bc_ex(sp_graph g, const int32_t* sources, int32_t nsrc, const sp_bc_opts* opts, double* bc_out,
                    sp_bc_stats* stats, sp_stream stream);
 

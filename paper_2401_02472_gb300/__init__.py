@@ -24,6 +24,7 @@ SP_ERR_INVALID_ARG, SP_ERR_OOM, SP_ERR_CUDA, SP_ERR_TOO_LARGE = -1, -2, -3, -4
 SP_ERR_RANGE, SP_ERR_TIMEOUT, SP_ERR_CANCELLED, SP_ERR_BAD_GRAPH, SP_ERR_NO_DEVICE = -5, -6, -7, -8, -9
 SP_FP64, SP_FP32_DELTA = 0, 1
 SP_FORM_AUTO, SP_FORM_PLAIN, SP_FORM_BATCHED = 0, 1, 2
+SP_DRIVER_AUTO, SP_DRIVER_PERSISTENT, SP_DRIVER_GRAPH = 0, 1, 2
 SP_GRAPH_CHECK_SYMMETRIC = 0x1
 SP_DEBUG_SKIP_BARRIER = 0x1
 SP_BC_KEEP_ORDER = 0x1
@@ -33,7 +34,7 @@ class sp_bc_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("form", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("max_ctas", ctypes.c_int32), ("barrier_timeout_ns", ctypes.c_int64),
                 ("debug_flags", ctypes.c_int32), ("flags", ctypes.c_int32), ("bottom_up", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("driver", ctypes.c_int32)]
 
 
 class sp_bc_stats(ctypes.Structure):
@@ -41,10 +42,11 @@ class sp_bc_stats(ctypes.Structure):
                 ("scanned_arcs", ctypes.c_int64), ("dag_arcs", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
                 ("max_levels", ctypes.c_int32), ("batches", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("promoted", ctypes.c_int32), ("sigma_float", ctypes.c_int32),
-                ("launches", ctypes.c_int32), ("tuned", ctypes.c_int32)]
+                ("launches", ctypes.c_int32), ("tuned", ctypes.c_int32), ("driver", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class sp_graph_info(ctypes.Structure):
@@ -68,7 +70,6 @@ SIGNATURES = {
     "sp_graph_create": ([_P, _P, _I32, _I64, _U32, _P, _P], ctypes.c_int),
     "sp_graph_destroy": ([_P], ctypes.c_int),
     "sp_graph_get_info": ([_P, _P], ctypes.c_int),
-    "sp_graph_check": ([_P], ctypes.c_int),
     "sp_bc_opts_default": ([_P], None),
     "sp_bc": ([_P, _P, _I32, _P, _P], ctypes.c_int),
     "sp_bc_ex": ([_P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
@@ -178,16 +179,13 @@ def sp_graph_get_info(g: int) -> dict:
     return info.as_dict()
 
 
-def sp_graph_check(g: int):
-    _check(lib.sp_graph_check(g), "sp_graph_check")
-
-
 def make_opts(precision=SP_FP64, form=SP_FORM_AUTO, batch=0, max_ctas=0, barrier_timeout_ns=0,
-              debug_flags=0, flags=0, bottom_up=0) -> sp_bc_opts:
+              debug_flags=0, flags=0, bottom_up=0, driver=SP_DRIVER_AUTO) -> sp_bc_opts:
     o = sp_bc_opts()
     lib.sp_bc_opts_default(ctypes.byref(o))
     o.precision, o.form, o.batch, o.max_ctas = precision, form, batch, max_ctas
     o.barrier_timeout_ns, o.debug_flags, o.flags, o.bottom_up = barrier_timeout_ns, debug_flags, flags, bottom_up
+    o.driver = driver
     return o
 
 

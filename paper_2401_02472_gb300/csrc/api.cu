@@ -219,6 +219,39 @@ static sp_status autotune_width(Graph* g, const int32_t* d_src, int32_t nsrc, co
 
 int default_batch_width(int32_t nsrc) { return nsrc > 32 ? 64 : 32; }
 
+// Plain-form level-loop drivers chosen by timing, keyed like the widths.
+static std::map<std::tuple<int32_t, int64_t, int32_t, int32_t>, int> g_driver;
+
+// Time both drivers of the plain form on the call's first eight sources and
+// keep the one with the most traversed arcs per second of kernel time.
+static sp_status autotune_driver(Graph* g, const int32_t* d_src, const sp_bc_opts& o, cudaStream_t st, int* driver,
+                                 int* launches) {
+    double* scratch = nullptr;
+    SP_CUDA(cudaMallocAsync((void**)&scratch, sizeof(double) * (size_t)g->n, st));
+    double best_rate = -1.0;
+    int best = SP_DRIVER_PERSISTENT;
+    for (int drv : {SP_DRIVER_PERSISTENT, SP_DRIVER_GRAPH}) {
+        sp_bc_opts t = o;
+        t.form = SP_FORM_PLAIN;
+        t.driver = drv;
+        sp_bc_stats ts;
+        sp_status rc = bc_device(g, d_src, 8, t, scratch, &ts, st);
+        *launches += ts.launches;
+        if (rc != SP_OK) {
+            cudaFreeAsync(scratch, st);
+            return rc;
+        }
+        double rate = ts.kernel_ms > 0 ? (double)ts.traversed_arcs / ts.kernel_ms : 0.0;
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = drv;
+        }
+    }
+    cudaFreeAsync(scratch, st);
+    *driver = best;
+    return SP_OK;
+}
+
 // Sort key of each source: (hop distance from a maximum-degree vertex, the
 // smallest neighbour one hop closer to it).  Sources with equal keys tend to
 // sit at the same BFS level for most vertices, so batching them in adjacent
@@ -380,6 +413,27 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             if (width == 1) width = default_batch_width(nsrc);
         }
     }
+    int driver = 0;
+    if (form == SP_FORM_PLAIN) {
+        driver = o.driver;
+        if (o.debug_flags & SP_DEBUG_SKIP_BARRIER) driver = SP_DRIVER_PERSISTENT;
+        if (driver == SP_DRIVER_AUTO) {
+            auto key = tune_key(g, o.precision);
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_driver.find(key);
+                if (it != g_driver.end()) driver = it->second;
+            }
+            if (driver == SP_DRIVER_AUTO && nsrc >= 16) {
+                sp_status trc = autotune_driver(g, d_src, o, st, &driver, &launches);
+                if (trc != SP_OK) return trc;
+                tuned = 1;
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_driver[key] = driver;
+            }
+            if (driver == SP_DRIVER_AUTO) driver = SP_DRIVER_PERSISTENT;
+        }
+    }
     int32_t* d_sorted = nullptr;
     if (form == SP_FORM_BATCHED && !(o.flags & SP_BC_KEEP_ORDER)) {
         sp_status orc = order_sources(g, d_src, nsrc, st, &d_sorted);
@@ -417,7 +471,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             L.group_blocks = plain_group_blocks(g);
             L.level_cap = plain_lcap;
             L.bottom_up_den = plain_bottom_up(g, o.bottom_up);
-            rc = run_plain(L, &r);
+            rc = driver == SP_DRIVER_GRAPH ? run_plain_graph(L, &r) : run_plain(L, &r);
         } else {
             BatchedLaunch L{};
             L.g = g;
@@ -484,6 +538,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         stats->kernel_ms = kernel_ms;
         stats->launches = launches;
         stats->tuned = tuned;
+        stats->driver = form == SP_FORM_PLAIN ? driver : 0;
     }
     return SP_OK;
 }
@@ -571,6 +626,7 @@ sp_status sp_graph_destroy(sp_graph gh) {
     if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
     Graph* g = reinterpret_cast<Graph*>(gh);
     if (g->d_top_dist) cudaFree(g->d_top_dist);
+    destroy_step_cache(g);
     cudaFree(g->d_rp);
     cudaFree(g->d_ci);
     delete g;
@@ -580,11 +636,6 @@ sp_status sp_graph_destroy(sp_graph gh) {
 sp_status sp_graph_get_info(sp_graph gh, sp_graph_info* out) {
     if (!gh || !out) return fail(SP_ERR_INVALID_ARG, "NULL argument");
     *out = reinterpret_cast<Graph*>(gh)->info;
-    return SP_OK;
-}
-
-sp_status sp_graph_check(sp_graph gh) {
-    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
     return SP_OK;
 }
 
@@ -604,6 +655,7 @@ sp_status sp_bc_ex(sp_graph gh, const int32_t* sources, int32_t nsrc, const sp_b
     if (o.batch != 0 && o.batch != 32 && o.batch != 64 && o.batch != 128 && o.batch != 256)
         return fail(SP_ERR_INVALID_ARG, "batch must be 0, 32, 64, 128 or 256");
     if (o.max_ctas < 0 || o.barrier_timeout_ns < 0 || o.bottom_up < -1) return fail(SP_ERR_INVALID_ARG, "negative option");
+    if (o.driver < SP_DRIVER_AUTO || o.driver > SP_DRIVER_GRAPH) return fail(SP_ERR_INVALID_ARG, "driver");
     if (o.flags & ~(int32_t)SP_BC_KEEP_ORDER) return fail(SP_ERR_INVALID_ARG, "unknown flag");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (stats) std::memset(stats, 0, sizeof(*stats));

@@ -45,34 +45,15 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
                                          : (ngroups == 1 ? n + 2 : std::min<int64_t>(n + 2, 65536));
     const int64_t hcap = g->nnz / tiers.t_hub + 2;
     const int64_t segcap = g->nnz / tiers.seg + hcap + 2;
-    const size_t G = (size_t)ngroups;
-    size_t bytes = 0;
-    auto take = [&](size_t b) { size_t o = bytes; bytes += (b + 255) & ~(size_t)255; return o; };
-    size_t o_ctl = take(sizeof(Ctl));
-    size_t o_gctl = take(sizeof(GroupCtl) * G);
-    size_t zero_end = bytes;
-    size_t o_lvl = take(sizeof(int32_t) * (size_t)n * G);
-    size_t o_sig = take(8 * (size_t)n * G);
-    size_t o_th = take(8 * (size_t)n * G);
-    size_t o_q = take(sizeof(int32_t) * (size_t)n * G);
-    size_t o_qoff = take(sizeof(int32_t) * (size_t)lcap * G);
-    size_t o_hoff = take(sizeof(int32_t) * (size_t)lcap * G);
-    size_t o_hcnt = take(sizeof(unsigned long long) * (size_t)lcap * G);
-    size_t o_emax = take(sizeof(int32_t) * (size_t)lcap * G);
-    size_t o_emin = take(sizeof(int32_t) * (size_t)lcap * G);
-    size_t o_fexp = take(sizeof(long long) * (size_t)lcap * G);
-    size_t o_hubs = take(sizeof(HubRec) * (size_t)hcap * G);
-    size_t o_hdone = take(sizeof(int32_t) * 2 * (size_t)hcap * G);
-    size_t o_part = take(sizeof(double) * (size_t)segcap * G);
-    size_t o_bcpart = take(ngroups > 1 && L.mode == PlainMode::BC ? sizeof(double) * (size_t)n * G : 0);
-    size_t o_trace = take(sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32));
+    const PlainLayout lay = plain_layout(n, lcap, hcap, segcap, ngroups, grid, ngroups > 1 && L.mode == PlainMode::BC);
+    const size_t bytes = lay.bytes;
     char* ws = nullptr;
     cudaError_t ce = cudaMallocAsync((void**)&ws, bytes, st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return fail(SP_ERR_OOM, "workspace allocation (plain form, " + std::to_string(bytes >> 20) + " MiB)");
     }
-    ce = cudaMemsetAsync(ws, 0, zero_end, st);
+    ce = cudaMemsetAsync(ws, 0, lay.zero_end, st);
     if (ce != cudaSuccess) { cudaFreeAsync(ws, st); return cuda_fail(ce, "cudaMemsetAsync"); }
 
     PlainArgs a{};
@@ -82,27 +63,12 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     a.sources = L.d_sources;
     a.nsrc = L.nsrc;
     a.bc = L.d_bc;
-    a.bcpart = reinterpret_cast<double*>(ws + o_bcpart);
+    plain_bind(a, ws, lay);
     a.gblocks = gblocks;
     a.ngroups = ngroups;
-    a.lvl = reinterpret_cast<int32_t*>(ws + o_lvl);
-    a.sig = ws + o_sig;
-    a.th = ws + o_th;
-    a.q = reinterpret_cast<int32_t*>(ws + o_q);
-    a.qoff = reinterpret_cast<int32_t*>(ws + o_qoff);
-    a.hoff = reinterpret_cast<int32_t*>(ws + o_hoff);
-    a.hcnt = reinterpret_cast<unsigned long long*>(ws + o_hcnt);
-    a.emax = reinterpret_cast<int32_t*>(ws + o_emax);
-    a.emin = reinterpret_cast<int32_t*>(ws + o_emin);
-    a.fexp = reinterpret_cast<long long*>(ws + o_fexp);
-    a.hubs = reinterpret_cast<HubRec*>(ws + o_hubs);
-    a.hdone = reinterpret_cast<int32_t*>(ws + o_hdone);
-    a.part = reinterpret_cast<double*>(ws + o_part);
     a.hcap = (int32_t)hcap;
     a.segcap = (int32_t)segcap;
     a.lcap = (int32_t)lcap;
-    a.ctl = reinterpret_cast<Ctl*>(ws + o_ctl);
-    a.gctl = reinterpret_cast<GroupCtl*>(ws + o_gctl);
     a.err_latch = nullptr;
     a.dist_out = L.d_dist;
     a.mant_out = L.d_mant;
@@ -114,7 +80,6 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     a.t_hub = tiers.t_hub;
     a.seg = tiers.seg;
     a.bu_den = L.bottom_up_den;
-    a.trace = reinterpret_cast<int*>(ws + o_trace);
     cudaMemsetAsync(a.trace, 0, sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32), st);
 
     void* args[] = {&a};
@@ -137,7 +102,7 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     }
     static thread_local Ctl h;
     std::memset(&h, 0, sizeof(h));
-    ce = cudaMemcpyAsync(&h, ws + o_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    ce = cudaMemcpyAsync(&h, ws + lay.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) {
         cudaFreeAsync(ws, st);
@@ -162,7 +127,7 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
 #ifdef SP_TRACE
     if (h.err == SP_ERR_TIMEOUT) {
         std::vector<int> tr(8 * (size_t)grid * (kPlainThreads / 32));
-        cudaMemcpy(tr.data(), ws + o_trace, sizeof(int) * tr.size(), cudaMemcpyDeviceToHost);
+        cudaMemcpy(tr.data(), ws + lay.trace, sizeof(int) * tr.size(), cudaMemcpyDeviceToHost);
         int lo = INT32_MAX;
         for (int b = 0; b < grid; ++b) lo = std::min(lo, h.block_phase[b]);
         for (int b = 0; b < grid; ++b) {

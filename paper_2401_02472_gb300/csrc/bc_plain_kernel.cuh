@@ -222,6 +222,46 @@ struct PlainKernel {
     __device__ __forceinline__ double* part() const { return a.part + (size_t)grp * (size_t)a.segcap; }
     __device__ __forceinline__ double* bcv() const { return a.ngroups == 1 ? a.bc : a.bcpart + gn; }
 
+    // Level stack of a new source: src alone on level 0, sigma[src] = 1, and
+    // src's hub record when its row is split into segments.  One thread.
+    __device__ void start_source(int src) {
+        int du = a.rp[src + 1] - a.rp[src];
+        q()[0] = src;
+        gc->qtail = 1;
+        qoff()[0] = 0;
+        hoff()[0] = 0;
+        hcnt()[0] = 0ull;
+        hcnt()[1] = 0ull;
+        emax()[0] = 0;
+        emin()[0] = 0;
+        sig()[src] = (SigT)1;
+        if (du > a.t_hub) {
+            int nseg = (du + a.seg - 1) / a.seg;
+            if (a.hcap < 1 || nseg > a.segcap) {
+                set_error(ctl, kErrCapacity);
+            } else {
+                q()[0] = (int)((unsigned)src | kHubFlag);
+                HubRec h;
+                h.v = src; h.qpos = 0; h.nseg = nseg; h.seg_base = 0;
+                hubs()[0] = h;
+                hdone()[0] = 0;
+                hdone()[a.hcap] = 0;
+                hcnt()[0] = (1ull << 32) | (unsigned long long)nseg;
+            }
+        }
+    }
+
+    // Bookkeeping before the forward pass over level d (entries end at qe):
+    // level d+1 starts at qe; its hub counters and exponent range start empty.
+    // One thread.
+    __device__ void open_level(int qe) {
+        qoff()[d + 1] = qe;
+        hoff()[d] = hoff_d;
+        hcnt()[d + 2] = 0ull;
+        emax()[d + 1] = INT_MIN;
+        emin()[d + 1] = INT_MAX;
+    }
+
     // A vertex claimed for level `nl`: append to the level stack (and the hub list).
     __device__ void push(int u, int nl) {
         int du = __ldg(&a.rp[u + 1]) - __ldg(&a.rp[u]);
@@ -479,31 +519,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
         const int src = __ldg(&a.sources[si]);
         // ---- init ----
         for (int i = tid; i < n; i += nthr) K.lvl()[i] = (i == src) ? 0 : -1;
-        if (tid == 0) {
-            int du = a.rp[src + 1] - a.rp[src];
-            K.q()[0] = src;
-            gc->qtail = 1;
-            K.qoff()[0] = 0;
-            K.hoff()[0] = 0;
-            K.hcnt()[0] = 0ull;
-            K.hcnt()[1] = 0ull;
-            K.emax()[0] = 0;
-            K.emin()[0] = 0;
-            K.sig()[src] = (SigT)1;
-            if (du > a.t_hub) {
-                int nseg = (du + a.seg - 1) / a.seg;
-                if (a.hcap < 1 || nseg > a.segcap) set_error(ctl, kErrCapacity);
-                else {
-                    K.q()[0] = (int)((unsigned)src | kHubFlag);
-                    HubRec h;
-                    h.v = src; h.qpos = 0; h.nseg = nseg; h.seg_base = 0;
-                    K.hubs()[0] = h;
-                    K.hdone()[0] = 0;
-                    K.hdone()[a.hcap] = 0;
-                    K.hcnt()[0] = (1ull << 32) | (unsigned long long)nseg;
-                }
-            }
-        }
+        if (tid == 0) K.start_source(src);
         if (!sync()) goto out;
 
         // ---- forward ----
@@ -524,13 +540,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
             if constexpr (kFloatSig) {
                 K.cshift_prev = d > 0 ? centre_shift(ld_volatile(&K.emax()[d - 1]), ld_volatile(&K.emin()[d - 1])) : 0;
             }
-            if (tid == 0) {
-                K.qoff()[d + 1] = qe;
-                K.hoff()[d] = K.hoff_d;
-                K.hcnt()[d + 2] = 0ull;
-                K.emax()[d + 1] = INT_MIN;
-                K.emin()[d + 1] = INT_MAX;
-            }
+            if (tid == 0) K.open_level(qe);
             K.my_emax = INT_MIN;
             K.my_emin = INT_MAX;
             // Direction: fat levels discover bottom-up.
@@ -625,6 +635,61 @@ out:
             if (e != 0 && a.err_latch) *(volatile int*)a.err_latch = e;
         }
     }
+}
+
+// Offsets of the plain form's arrays inside its one workspace allocation
+// (per-group copies of every per-source array, 256-byte aligned).
+struct PlainLayout {
+    size_t ctl, gctl, zero_end, lvl, sig, th, q, qoff, hoff, hcnt, emax, emin, fexp, hubs, hdone, part, bcpart,
+        trace, bytes;
+};
+
+inline PlainLayout plain_layout(int64_t n, int64_t lcap, int64_t hcap, int64_t segcap, int ngroups, int grid,
+                                bool bcpart) {
+    PlainLayout o{};
+    const size_t G = (size_t)ngroups;
+    size_t bytes = 0;
+    auto take = [&](size_t b) { size_t at = bytes; bytes += (b + 255) & ~(size_t)255; return at; };
+    o.ctl = take(sizeof(Ctl));
+    o.gctl = take(sizeof(GroupCtl) * G);
+    o.zero_end = bytes;
+    o.lvl = take(sizeof(int32_t) * (size_t)n * G);
+    o.sig = take(8 * (size_t)n * G);
+    o.th = take(8 * (size_t)n * G);
+    o.q = take(sizeof(int32_t) * (size_t)n * G);
+    o.qoff = take(sizeof(int32_t) * (size_t)lcap * G);
+    o.hoff = take(sizeof(int32_t) * (size_t)lcap * G);
+    o.hcnt = take(sizeof(unsigned long long) * (size_t)lcap * G);
+    o.emax = take(sizeof(int32_t) * (size_t)lcap * G);
+    o.emin = take(sizeof(int32_t) * (size_t)lcap * G);
+    o.fexp = take(sizeof(long long) * (size_t)lcap * G);
+    o.hubs = take(sizeof(HubRec) * (size_t)hcap * G);
+    o.hdone = take(sizeof(int32_t) * 2 * (size_t)hcap * G);
+    o.part = take(sizeof(double) * (size_t)segcap * G);
+    o.bcpart = take(bcpart ? sizeof(double) * (size_t)n * G : 0);
+    o.trace = take(sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32));
+    o.bytes = bytes;
+    return o;
+}
+
+inline void plain_bind(PlainArgs& a, char* ws, const PlainLayout& o) {
+    a.bcpart = reinterpret_cast<double*>(ws + o.bcpart);
+    a.lvl = reinterpret_cast<int32_t*>(ws + o.lvl);
+    a.sig = ws + o.sig;
+    a.th = ws + o.th;
+    a.q = reinterpret_cast<int32_t*>(ws + o.q);
+    a.qoff = reinterpret_cast<int32_t*>(ws + o.qoff);
+    a.hoff = reinterpret_cast<int32_t*>(ws + o.hoff);
+    a.hcnt = reinterpret_cast<unsigned long long*>(ws + o.hcnt);
+    a.emax = reinterpret_cast<int32_t*>(ws + o.emax);
+    a.emin = reinterpret_cast<int32_t*>(ws + o.emin);
+    a.fexp = reinterpret_cast<long long*>(ws + o.fexp);
+    a.hubs = reinterpret_cast<HubRec*>(ws + o.hubs);
+    a.hdone = reinterpret_cast<int32_t*>(ws + o.hdone);
+    a.part = reinterpret_cast<double*>(ws + o.part);
+    a.ctl = reinterpret_cast<Ctl*>(ws + o.ctl);
+    a.gctl = reinterpret_cast<GroupCtl*>(ws + o.gctl);
+    a.trace = reinterpret_cast<int*>(ws + o.trace);
 }
 
 // Sum of the groups' partial BC vectors, in group order.

@@ -31,6 +31,7 @@ struct Graph {
     int32_t* d_top_dist = nullptr;  // BFS distances from top_vertex (computed on first use)
     int32_t top_levels = 0;     // 1 + eccentricity of top_vertex (0 until computed)
     bool theta_f64 = false;     // FP32 dependencies of this graph left the FP32 range before
+    void* step_cache = nullptr; // graph-driven plain form: device state block and instantiated CUDA graphs
 };
 
 // Thread-local error text.
@@ -92,6 +93,10 @@ std::string barrier_diagnostic(const Ctl& h, int grid);
 // Run the plain form on L.stream and wait for it; `result` receives the
 // device-side error code and statistics.
 sp_status run_plain(const PlainLaunch& L, LaunchResult* result);
+// The same computation (BC mode, one group) with the level loop driven by a
+// CUDA graph: a conditional WHILE node over one kernel per phase.
+sp_status run_plain_graph(const PlainLaunch& L, LaunchResult* result);
+void destroy_step_cache(Graph* g);
 
 struct BatchedLaunch {
     const Graph* g;

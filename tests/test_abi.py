@@ -42,8 +42,40 @@ def test_status_strings_and_defaults():
     assert sp.sp_status_string(12345) == "SP_ERR_UNKNOWN"
     o = sp.make_opts()
     assert (o.precision, o.form, o.batch, o.debug_flags) == (sp.SP_FP64, sp.SP_FORM_AUTO, 0, 0)
-    assert ctypes.sizeof(sp.sp_bc_opts) == 40 and ctypes.sizeof(sp.sp_bc_stats) == 80
+    assert ctypes.sizeof(sp.sp_bc_opts) == 40 and ctypes.sizeof(sp.sp_bc_stats) == 88
     assert ctypes.sizeof(sp.sp_graph_info) == 40
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every field of the ctypes structs sits at the offset the C compiler gives it."""
+    import shutil
+    import subprocess
+
+    import paper_2401_02472_gb300 as sp
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "starbc.h"', "int main(void) {"]
+    structs = [sp.sp_bc_opts, sp.sp_bc_stats, sp.sp_graph_info]
+    for cls in structs:
+        c = cls.__name__
+        lines.append(f'printf("{c} size %zu\\n", sizeof({c}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{c} {f} %zu\\n", offsetof({c}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        c, f, v = line.split()
+        got[(c, f)] = int(v)
+    for cls in structs:
+        c = cls.__name__
+        assert got[(c, "size")] == ctypes.sizeof(cls), c
+        for f, _ in cls._fields_:
+            assert got[(c, f)] == getattr(cls, f).offset, (c, f)
 
 
 def test_argument_errors_without_a_device():

@@ -226,6 +226,61 @@ def test_run_to_run_bit_identical(form, batch):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_bc_plain_graph_driver(name, precision):
+    # Level loop as a CUDA graph (conditional WHILE node, one kernel per
+    # level): same per-source dependencies as the persistent kernel, added
+    # into BC in source order, so it equals the running sum of single-source
+    # persistent calls bit for bit.
+    g, G = graph(name)
+    srcs = gen.sources(g, min(12, int((g.degrees() > 0).sum())), 7)
+    got, st = gpu_bc(G, srcs, precision, sp.SP_FORM_PLAIN, driver=sp.SP_DRIVER_GRAPH)
+    want, ost = oracle.bc(g, srcs)
+    assert_bc_close(got, want, RTOL[precision], f"{name} plain, graph driver")
+    assert st["driver"] == sp.SP_DRIVER_GRAPH
+    assert st["traversed_arcs"] == int(ost["arcs"].sum())
+    assert st["max_levels"] == int(ost["levels"].max())
+    assert st["launches"] >= len(srcs) + int(ost["levels"].sum())  # a kernel per phase
+    acc = np.zeros(g.n)
+    for s in srcs:
+        one, st1 = gpu_bc(G, [s], precision, sp.SP_FORM_PLAIN, driver=sp.SP_DRIVER_PERSISTENT)
+        assert st1["driver"] == sp.SP_DRIVER_PERSISTENT
+        acc = acc + one
+    assert np.array_equal(got, acc)
+
+
+def test_graph_driver_rescaled_counts_and_hubs():
+    # Path counts past 2^64 (a 600 x 600 grid from its corners: FP64 with
+    # per-level exponents over about 1,200 levels) and rows split into
+    # segments, both under the graph-driven loop.
+    g = gen.grid(600, 600)
+    G = device_graph(g)
+    srcs = np.array([0, 599, 600 * 600 - 1], np.int32)
+    got, st = gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_PLAIN, driver=sp.SP_DRIVER_GRAPH)
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(got, want, 1e-9, "grid600 graph driver")
+    assert st["sigma_float"] == 1 and st["max_levels"] == 1199
+    gh, GH = hub_graph()
+    hs = np.array([0, 1, 77, 4095], np.int32)
+    for prec in (sp.SP_FP64, sp.SP_FP32_DELTA):
+        got, _ = gpu_bc(GH, hs, prec, sp.SP_FORM_PLAIN, driver=sp.SP_DRIVER_GRAPH)
+        want, _ = oracle.bc(gh, hs)
+        assert_bc_close(got, want, RTOL[prec], "hub graph, graph driver")
+
+
+def test_driver_autotuner_picks_and_caches():
+    g, G = graph("rmat12")
+    srcs = gen.sources(g, 40, 33)
+    a, st = gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_PLAIN)
+    assert st["driver"] in (sp.SP_DRIVER_PERSISTENT, sp.SP_DRIVER_GRAPH)
+    b, st2 = gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_PLAIN)
+    assert st2["tuned"] == 0 and st2["driver"] == st["driver"]
+    assert np.array_equal(a, b)
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(a, want, 1e-9)
+
+
 @pytest.mark.parametrize("name", ["rmat12", "er2000", "knn5000", "mixed"])
 def test_plain_direction_does_not_change_results(name):
     # Bottom-up discovery on wide levels (any level above n/2, n/20, or never)
