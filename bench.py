@@ -49,8 +49,9 @@ WORKLOADS = {
                                  desc="RMAT scale 20, edge factor 16, 64 sources"),
     "knn4_1m_256src_batched": dict(graph="knn4_1m", nsrc=256, seed=13, precision="fp32_delta", form="batched",
                                    desc="2-D 4-NN graph of 10^6 uniform points, 256 sources"),
-    "er2000_all_plain": dict(graph="er2000", nsrc=2000, seed=None, precision="fp64", form="plain",
-                             desc="Erdos-Renyi n=2,000 m=10,000, all 2,000 sources"),
+    "er2000_all": dict(graph="er2000", nsrc=2000, seed=None, precision="fp64", form="auto",
+                       desc="Erdos-Renyi n=2,000 m=10,000, all 2,000 sources, exact FP64 "
+                            "(automatic form: one block per source, state in shared memory)"),
 }
 WORKLOADS["serving_8graphs"] = dict(graph=None, nsrc=0, seed=31, precision="fp32_delta", form="auto",
                                     desc="Poisson stream (200 req/s) of BC requests over 8 resident ER/RMAT graphs, "
@@ -277,6 +278,40 @@ def algorithmic_bytes(st: dict, n: int, form: str, theta_bytes: int, width: int)
     return int(b)
 
 
+def kernel_source_hash() -> str:
+    """Short hash of the library's kernel sources: a recorded DRAM traffic
+    figure is used only while the kernels it was measured on are unchanged."""
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_2401_02472_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, width: int):
+    """DRAM bytes per launch of the dominant kernel from an ncu capture summarised
+    in profiles/ (a `traffic-record:` line naming the workload, the batch width and
+    the kernel source hash), or None when no record matches the current kernels."""
+    want = {"workload": workload, "width": str(width), "sources": kernel_source_hash()}
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith(".md"):
+            continue
+        for line in open(os.path.join(pdir, name)):
+            if not line.startswith("traffic-record:"):
+                continue
+            kv = dict(x.split("=", 1) for x in line.split()[1:] if "=" in x)
+            if all(kv.get(k) == v for k, v in want.items()):
+                return float(kv["dram_bytes"])
+    return None
+
+
 def combine_ranks(dist, world, total_ms, steps, arcs, e2e_s, e2e_arcs, device="cpu"):
     """Whole-job throughput: units of all ranks / the slowest rank's time.
 
@@ -393,7 +428,8 @@ def run_ours(args, rank, world, dist):
     if args.nsrc:
         srcs = srcs[:args.nsrc]
     prec = sp.SP_FP32_DELTA if w["precision"] == "fp32_delta" else sp.SP_FP64
-    form = sp.SP_FORM_BATCHED if w["form"] == "batched" else sp.SP_FORM_PLAIN
+    form = {"auto": sp.SP_FORM_AUTO, "plain": sp.SP_FORM_PLAIN, "batched": sp.SP_FORM_BATCHED,
+            "small": sp.SP_FORM_SMALL}[w["form"]]
     driver = {"auto": sp.SP_DRIVER_AUTO, "persistent": sp.SP_DRIVER_PERSISTENT, "graph": sp.SP_DRIVER_GRAPH}[args.driver]
     opts = sp.make_opts(precision=prec, form=form, batch=args.batch, bottom_up=args.bottom_up, driver=driver)
     theta_bytes = 4 if prec == sp.SP_FP32_DELTA else 8
@@ -465,7 +501,7 @@ def run_ours(args, rank, world, dist):
     kernel_ms = s["kernel_ms"]
     alg = algorithmic_bytes(s, g.n, w["form"], theta_bytes, s["batch"] if s["form"] == sp.SP_FORM_BATCHED else 0)
     achieved = alg / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0
-    launches_per_step = s["launches"] + 2  # + graph validation (row_ptr, rows)
+    launches_per_step = s["launches"] + 3  # + graph validation (row_ptr, rows) + eccentricity BFS
     base = cpu_baseline(g, srcs, args.cpu_budget) if not args.no_cpu_baseline else None
     line = {
         "metric": "BC GTEPS (fwd+bwd)",
@@ -481,14 +517,17 @@ def run_ours(args, rank, world, dist):
         "dtype": "u64-sigma/f32-delta/f64-bc" if prec == sp.SP_FP32_DELTA else "u64-sigma/f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "n": g.n, "arcs": g.nnz,
-                   "sources": int(len(srcs)), "batch": s["batch"], "form": w["form"], "max_levels": s["max_levels"],
+                   "sources": int(len(srcs)), "batch": s["batch"],
+                   "form": {1: "plain", 2: "batched", 3: "small"}.get(s["form"], str(s["form"])),
+                   "max_levels": s["max_levels"],
                    "l2": "inputs larger than L2 (no flush)"},
         "e2e": {"value": e2e_value, "unit": "GTEPS",
                 "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col_idx.nbytes + srcs.nbytes),
                 "d2h_bytes_per_step": int(g.n * 8)},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None, "traffic": args.traffic,
+                     "frac": achieved / peak if peak else None,
+                     "traffic": args.traffic if args.traffic is not None else recorded_traffic(args.workload, s["batch"]),
                      "peak_kind": peak_kind, "kernel_ms": kernel_ms, "algorithmic_bytes": alg},
         "cpu_baseline": base,
         "clocks": clk,
@@ -508,7 +547,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=0, help="fixed batch width (0 = autotuned)")
-    ap.add_argument("--form", default=None, choices=["plain", "batched"], help="override the workload's form")
+    ap.add_argument("--form", default=None, choices=["auto", "plain", "batched", "small"],
+                    help="override the workload's form")
     ap.add_argument("--nsrc", type=int, default=0, help="override the workload's source count")
     ap.add_argument("--bottom-up", type=int, default=0, help="plain form: bottom-up on levels > n/this (-1 never)")
     ap.add_argument("--driver", default="auto", choices=["auto", "persistent", "graph"],

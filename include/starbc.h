@@ -104,11 +104,14 @@ SP_API sp_status sp_graph_get_info(sp_graph g, sp_graph_info* out);
 /* Betweenness centrality                                                   */
 
 enum { SP_FP64 = 0, SP_FP32_DELTA = 1 };
-enum { SP_FORM_AUTO = 0, SP_FORM_PLAIN = 1, SP_FORM_BATCHED = 2 };
+enum { SP_FORM_AUTO = 0, SP_FORM_PLAIN = 1, SP_FORM_BATCHED = 2, SP_FORM_SMALL = 3 };
 
 typedef struct {
     int32_t precision;          /* SP_FP64 (delta in FP64) or SP_FP32_DELTA (delta stored in FP32) */
-    int32_t form;               /* SP_FORM_AUTO, SP_FORM_PLAIN (one source at a time) or SP_FORM_BATCHED */
+    int32_t form;               /* SP_FORM_AUTO, SP_FORM_PLAIN (one source at a time per block group),
+                                   SP_FORM_BATCHED (bitmap batches of sources) or SP_FORM_SMALL (one
+                                   block per source, state in shared memory; graphs of up to about
+                                   14,500 vertices, else SP_ERR_TOO_LARGE) */
     int32_t batch;              /* batched form: sources per batch, 32, 64, 128 or 256; 0 = autotuned */
     int32_t max_ctas;           /* cap on the persistent grid (0 = every co-resident CTA) */
     int64_t barrier_timeout_ns; /* per device-side wait; 0 = 20 s */
@@ -152,7 +155,7 @@ typedef struct {
     int32_t max_levels;     /* max over sources of L = 1 + eccentricity of s */
     int32_t batches;        /* batches (plain form: one per source) */
     int32_t batch;          /* sources per batch used (1 for the plain form) */
-    int32_t form;           /* SP_FORM_PLAIN or SP_FORM_BATCHED */
+    int32_t form;           /* SP_FORM_PLAIN, SP_FORM_BATCHED or SP_FORM_SMALL */
     int32_t promoted;       /* 1 when FP32 dependencies left the FP32 range and the call reran with FP64 */
     int32_t sigma_float;    /* 1 when path counts needed FP64 with per-level rescaling (above 2^64) */
     int32_t launches;       /* kernel launches of the call, including reruns and autotuning trials */
@@ -213,13 +216,17 @@ SP_API sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_idx, i
 /* Serving: continuous batching of BC requests over resident graphs          */
 
 /*
- * A server owns a host scheduler thread and `max_slots` CUDA streams.  Graphs
- * added to it stay resident.  A request is admitted when its device footprint
- * fits in what is left of `hbm_budget_bytes`; admitted requests are split into
- * source batches that run concurrently on free slots, so requests that arrive
- * while others run start as soon as a slot and memory free up.  A request's
- * result does not depend on what else runs: its batches and their order are
- * fixed by the request alone.
+ * A server owns `max_slots` scheduler threads, each with its own CUDA stream.
+ * Graphs added to it stay resident (the paper keeps the graph on the device
+ * across kernels, Section 4.1).  A request is admitted, in arrival order, when
+ * its device footprint fits in what is left of `hbm_budget_bytes`; a free slot
+ * takes the oldest admitted request and runs it as one BC call (regrouped
+ * source batches of the width tuned for the graph, in one persistent launch).
+ * With several slots, each launch is capped to its share of the SMs, so a
+ * request that arrives while others run starts at once and overlaps with
+ * them on the device.  A request's result does not depend on what else runs:
+ * its batches and the order in which their BC is added are fixed by the
+ * request alone.
  */
 SP_API sp_status sp_server_create(size_t hbm_budget_bytes, int32_t max_slots, sp_server* out);
 SP_API sp_status sp_server_add_graph(sp_server s, sp_graph g, int32_t* graph_id);

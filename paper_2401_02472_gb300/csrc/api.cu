@@ -389,9 +389,17 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         if (rc != SP_OK) return rc;
     }
     int form = o.form;
-    // Automatic form: many narrow levels (high diameter) favour small block
-    // groups, one source each; wide levels and many sources favour batches.
-    if (form == SP_FORM_AUTO) form = (nsrc >= 2 && g->top_levels <= 64) ? SP_FORM_BATCHED : SP_FORM_PLAIN;
+    // Automatic form: graphs whose per-source state fits in shared memory run
+    // one block per source; otherwise many narrow levels (high diameter)
+    // favour small block groups, one source each, and wide levels with many
+    // sources favour batches.  Path counts past 64 bits need the plain or
+    // batched form's FP64 representation.
+    if (form == SP_FORM_AUTO) {
+        if (!sigma_float && (int64_t)g->n <= small_form_max_n(g->device)) form = SP_FORM_SMALL;
+        else form = (nsrc >= 2 && g->top_levels <= 64) ? SP_FORM_BATCHED : SP_FORM_PLAIN;
+    }
+    if (form == SP_FORM_SMALL && (int64_t)g->n > small_form_max_n(g->device))
+        return fail(SP_ERR_TOO_LARGE, "graph too large for the small form (" + std::to_string(g->n) + " vertices)");
     int width = 1, launches = 0, tuned = 0;
     if (form == SP_FORM_BATCHED) {
         if (o.batch > 0) {
@@ -407,8 +415,9 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
                 sp_status trc = autotune_width(g, d_src, nsrc, o, st, &width, &launches);
                 if (trc != SP_OK) return trc;
                 tuned = 1;
+                // first result wins, so that concurrent calls agree on one width
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tuned[key] = width;
+                width = g_tuned.emplace(key, width).first->second;
             }
             if (width == 1) width = default_batch_width(nsrc);
         }
@@ -429,7 +438,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
                 if (trc != SP_OK) return trc;
                 tuned = 1;
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_driver[key] = driver;
+                driver = g_driver.emplace(key, driver).first->second;
             }
             if (driver == SP_DRIVER_AUTO) driver = SP_DRIVER_PERSISTENT;
         }
@@ -455,7 +464,17 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
     for (int attempt = 0; attempt < 16; ++attempt) {
         r = LaunchResult{};
         sp_status rc;
-        if (form == SP_FORM_PLAIN) {
+        if (form == SP_FORM_SMALL) {
+            SmallLaunch L{};
+            L.g = g;
+            L.d_sources = d_src;
+            L.nsrc = nsrc;
+            L.d_bc = d_bc;
+            L.theta_f32 = theta_f32;
+            L.max_ctas = o.max_ctas;
+            L.stream = st;
+            rc = run_small(L, &r);
+        } else if (form == SP_FORM_PLAIN) {
             PlainLaunch L{};
             L.g = g;
             L.d_sources = d_src;
@@ -493,6 +512,17 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         if (rc != SP_OK) return rc;
         kernel_ms += r.kernel_ms;
         launches += r.launches;
+        if (r.err == kErrSigmaOverflow && form == SP_FORM_SMALL) {
+            // the small form holds exact counts only: rerun in the plain form
+            form = SP_FORM_PLAIN;
+            driver = SP_DRIVER_PERSISTENT;
+            sigma_float = true;
+            sigma_batches = 1;
+            add_range_hint(g, 1);
+            std::lock_guard<std::mutex> lk(g->mu);
+            g->sigma_float = true;
+            continue;
+        }
         if (r.err == kErrSigmaOverflow && !sigma_float) {
             sigma_float = true;
             sigma_batches = 1;
@@ -520,7 +550,8 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         }
         break;
     }
-    sp_status rc = map_device_error(r.err, form == SP_FORM_PLAIN ? "plain form" : "batched form", r.diag);
+    sp_status rc = map_device_error(
+        r.err, form == SP_FORM_PLAIN ? "plain form" : (form == SP_FORM_SMALL ? "small form" : "batched form"), r.diag);
     if (rc != SP_OK) return rc;
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
@@ -530,7 +561,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         stats->scanned_arcs = (int64_t)r.scanned_arcs;
         stats->max_levels = r.levels;
         stats->batch = width;
-        stats->batches = form == SP_FORM_PLAIN ? nsrc : (nsrc + width - 1) / width;
+        stats->batches = form == SP_FORM_BATCHED ? (nsrc + width - 1) / width : nsrc;
         stats->form = form;
         stats->promoted = promoted || (o.precision == SP_FP32_DELTA && !theta_f32);
         stats->sigma_float = sigma_float ? 1 : sigma_batches;
@@ -651,7 +682,7 @@ sp_status sp_bc_ex(sp_graph gh, const int32_t* sources, int32_t nsrc, const sp_b
     sp_bc_opts_default(&o);
     if (opts) o = *opts;
     if (o.precision != SP_FP64 && o.precision != SP_FP32_DELTA) return fail(SP_ERR_INVALID_ARG, "precision");
-    if (o.form < SP_FORM_AUTO || o.form > SP_FORM_BATCHED) return fail(SP_ERR_INVALID_ARG, "form");
+    if (o.form < SP_FORM_AUTO || o.form > SP_FORM_SMALL) return fail(SP_ERR_INVALID_ARG, "form");
     if (o.batch != 0 && o.batch != 32 && o.batch != 64 && o.batch != 128 && o.batch != 256)
         return fail(SP_ERR_INVALID_ARG, "batch must be 0, 32, 64, 128 or 256");
     if (o.max_ctas < 0 || o.barrier_timeout_ns < 0 || o.bottom_up < -1) return fail(SP_ERR_INVALID_ARG, "negative option");

@@ -332,7 +332,7 @@ struct BatchKernel {
     }
 
     // ---------------- forward ----------------
-    // Chunk of up to 32 level-stack entries [e0, min(e0+32, qe)).
+    // Chunk of level-stack entries [e0, qe), at most 32.
     __device__ void fwd_chunk(int e0, int qe) {
         const int e = e0 + lane;
         bool valid, hubent;
@@ -701,22 +701,28 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
         return ok;
     };
     // Work loop of one level: hub segments first, then chunks of 32 entries.
+    // Warp w takes item w first and further items from a shared counter, so a
+    // level with fewer items than warps costs no atomics.
+    const int nwarps = nthr / kWarp;
+    const int gwarp = tid / kWarp;
     auto work = [&](int nitems_hub, int qb, int qe, auto&& on_hub, auto&& on_chunk) {
-        const int nchunks = (qe - qb + kWarp - 1) / kWarp;
+        const int c = entries_per_item(qe - qb, nwarps);
+        const int nchunks = (qe - qb + c - 1) / c;
         const int total = nitems_hub + nchunks;
-        while (true) {
-            int item = 0;
-            if (lane == 0) item = (int)atomicAdd(&ctl->work[phase & 3], 1u);
-            item = __shfl_sync(kFull, item, 0);
-            if (item >= total) break;
+        for (int item = gwarp; item < total;) {
             SP_PROF_MARK(5);
             if (item < nitems_hub) {
                 on_hub(item);
                 SP_PROF_MARK(K.d >= 0 && !K.backward ? 1 : 3);
             } else {
-                on_chunk(qb + (item - nitems_hub) * kWarp);
+                const int e0 = qb + (item - nitems_hub) * c;
+                on_chunk(e0, min(e0 + c, qe));
                 SP_PROF_MARK(K.d >= 0 && !K.backward ? 0 : 2);
             }
+            if (nwarps >= total) break;
+            int next = 0;
+            if (lane == 0) next = nwarps + (int)atomicAdd(&ctl->work[phase & 3], 1u);
+            item = __shfl_sync(kFull, next, 0);
         }
     };
 
@@ -809,7 +815,7 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
                     zero_mask<W>(clr + (size_t)v * W);
                 }
             }
-            work(K.nseg_d, qb, qe, [&](int g) { K.fwd_hub_segment(g); }, [&](int e0) { K.fwd_chunk(e0, qe); });
+            work(K.nseg_d, qb, qe, [&](int g) { K.fwd_hub_segment(g); }, [&](int e0, int e1) { K.fwd_chunk(e0, e1); });
             K.flush_exponents(d);
             if constexpr (!kFloatSig) {
                 unsigned long long mx = K.my_smax;
@@ -871,7 +877,7 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
             }
             const bool skip = dd == L - 1;
             work(K.nseg_d, qbd, qed, [&](int g) { K.bwd_hub_segment(g, skip); },
-                 [&](int e0) { K.bwd_chunk(e0, qed, skip); });
+                 [&](int e0, int e1) { K.bwd_chunk(e0, e1, skip); });
             if (!sync()) goto out;
         }
 

@@ -188,7 +188,7 @@ static __device__ __forceinline__ void step_work(PlainKernel<SigT, ThT>& K, cons
 }
 
 template <typename SigT, typename ThT>
-__global__ void __launch_bounds__(kPlainThreads) plain_step_kernel(StepBlock* blk, cudaGraphConditionalHandle cond) {
+__global__ void __launch_bounds__(kPlainThreads, 2) plain_step_kernel(StepBlock* blk, cudaGraphConditionalHandle cond) {
     __shared__ PlainArgs sa;
     __shared__ StepState ss;
     if (threadIdx.x == 0) {

@@ -43,6 +43,8 @@
 
 namespace sp {
 
+// 512 threads, two blocks per SM: every variant fits in 64 registers, so the
+// persistent grid (and the number of block groups) is the same for all.
 constexpr int kPlainThreads = 512;
 
 // Barrier and work counters of one block group (zeroed by the host).
@@ -283,9 +285,9 @@ struct PlainKernel {
         }
     }
 
-    // Forward visit of arc (v, u) by a vertex v at level d.
-    __device__ __forceinline__ SigT fwd_arc(int u) {
-        int lu = __ldcg(&lvl()[u]);
+    // Forward visit of arc (v, u) by a vertex v at level d, u's level already
+    // loaded as lu: claim u for level d+1, or return sigma[u] if u is a parent.
+    __device__ __forceinline__ SigT fwd_visit(int u, int lu) {
         SigT c = 0;
         if (lu < 0) {
             if (discover && atomicCAS(&lvl()[u], -1, d + 1) == -1) push(u, d + 1);
@@ -295,6 +297,7 @@ struct PlainKernel {
         }
         return c;
     }
+    __device__ __forceinline__ SigT fwd_arc(int u) { return fwd_visit(u, __ldcg(&lvl()[u])); }
 
     __device__ void fwd_finalize(int v, SigT acc, int deg) {
         st_arcs += (unsigned long long)deg;
@@ -334,7 +337,7 @@ struct PlainKernel {
         b[v] = __ldcg(&b[v]) + delta;
     }
 
-    // One chunk of 32 level-stack entries starting at index e0 (< qe).
+    // One chunk of level-stack entries [e0, qe), at most 32.
     template <bool FWD>
     __device__ void chunk(int e0, int qe, bool skip_arcs) {
         int e = e0 + lane;
@@ -352,10 +355,29 @@ struct PlainKernel {
         SigT sacc = 0;
         double tacc = 0.0;
         if (walk <= a.t_thread) {
-            for (int k = 0; k < walk; ++k) {
-                int u = __ldg(&a.ci[beg + k]);
-                if constexpr (FWD) sacc = SigOps<SigT>::add(sacc, fwd_arc(u), ovf);
-                else tacc += bwd_arc(u);
+            // one lane walks the row, four arcs at a time: their column ids,
+            // then their levels, then their sigma / theta loads are issued
+            // together; the sums still run in CSR order
+            constexpr int G = 4;
+            for (int k0 = 0; k0 < walk; k0 += G) {
+                int u[G], lu[G];
+#pragma unroll
+                for (int i = 0; i < G; ++i) u[i] = k0 + i < walk ? __ldg(&a.ci[beg + k0 + i]) : -1;
+#pragma unroll
+                for (int i = 0; i < G; ++i) lu[i] = u[i] >= 0 ? __ldcg(&lvl()[u[i]]) : INT_MIN;
+                if constexpr (FWD) {
+                    SigT c[G];
+#pragma unroll
+                    for (int i = 0; i < G; ++i) c[i] = u[i] >= 0 ? fwd_visit(u[i], lu[i]) : (SigT)0;
+#pragma unroll
+                    for (int i = 0; i < G; ++i) sacc = SigOps<SigT>::add(sacc, c[i], ovf);
+                } else {
+                    double t[G];
+#pragma unroll
+                    for (int i = 0; i < G; ++i) t[i] = lu[i] == d + 1 ? (double)__ldcg(&th()[u[i]]) : 0.0;
+#pragma unroll
+                    for (int i = 0; i < G; ++i) tacc += t[i];
+                }
             }
         }
         unsigned big = __ballot_sync(kFull, walk > a.t_thread);
@@ -465,14 +487,18 @@ struct PlainKernel {
         }
     }
 
+    // Items of one level: hub segments, chunks of 32 entries, bottom-up
+    // ranges.  Warp w of the group takes item w first and further items from
+    // the group's counter, so a level with fewer items than warps costs no
+    // atomics.
     template <bool FWD>
     __device__ void level_work(int phase, int qb, int qe, bool skip_arcs, int bu_items = 0) {
-        int nchunks = (qe - qb + kWarp - 1) / kWarp;
+        const int nwarps = a.gblocks * (int)(blockDim.x / kWarp);
+        const int c = entries_per_item(qe - qb, nwarps);
+        int nchunks = (qe - qb + c - 1) / c;
         int total = nseg_d + nchunks + bu_items;
+        int item = (int)(((blockIdx.x % a.gblocks) * blockDim.x + threadIdx.x) / kWarp);
         while (true) {
-            int item = 0;
-            if (lane == 0) item = (int)atomicAdd(&gc->work[phase & 3], 1u);
-            item = __shfl_sync(kFull, item, 0);
 #ifdef SP_TRACE
             if (lane == 0 && a.trace) {
                 int* t = a.trace + 8 * ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -481,14 +507,21 @@ struct PlainKernel {
 #endif
             if (item >= total) break;
             if (item < nseg_d) hub_segment<FWD>(item, skip_arcs);
-            else if (item < nseg_d + nchunks) chunk<FWD>(qb + (item - nseg_d) * kWarp, qe, skip_arcs);
+            else if (item < nseg_d + nchunks) {
+                const int e0 = qb + (item - nseg_d) * c;
+                chunk<FWD>(e0, min(e0 + c, qe), skip_arcs);
+            }
             else bottom_up_range((item - nseg_d - nchunks) * (8 * kWarp));
+            if (nwarps >= total) break;
+            int next = 0;
+            if (lane == 0) next = nwarps + (int)atomicAdd(&gc->work[phase & 3], 1u);
+            item = __shfl_sync(kFull, next, 0);
         }
     }
 };
 
 template <typename SigT, typename ThT>
-__global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
+__global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
     constexpr bool kFloatSig = !std::is_integral<SigT>::value;
     const int g = blockIdx.x / a.gblocks;
     if (g >= a.ngroups) return;  // the host sizes the grid to ngroups * gblocks

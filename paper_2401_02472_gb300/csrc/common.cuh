@@ -214,6 +214,14 @@ __device__ __forceinline__ int warp_min_i32(int v) {
     for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
     return v;
 }
+// Level-stack entries per work item: 32 (one per lane), or fewer when the
+// level holds fewer than 32 entries per warp, so that a small level is spread
+// over more warps and its slowest item (the level's critical path) is short.
+__device__ __forceinline__ int entries_per_item(int entries, int nwarps) {
+    const int c = (entries + nwarps - 1) / max(nwarps, 1);
+    return c >= 32 ? 32 : (c < 1 ? 1 : c);
+}
+
 // Inclusive prefix sum over the warp.
 __device__ __forceinline__ int warp_incl_scan(int v) {
     int lane = lane_id();

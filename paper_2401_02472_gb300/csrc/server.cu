@@ -5,22 +5,19 @@
 // The server takes that to many queries: graphs stay resident, and BC
 // requests (a graph and a source multiset) arrive at any time.
 //
-//   admission  a request enters when its device footprint (its partial-BC
-//              buffers plus the workspace of the batches it can run at once)
-//              fits in what is left of the memory budget; otherwise it waits
-//              in arrival order.
-//   batching   an admitted request is cut into source batches fixed by the
-//              request alone (its sources in order, `width` at a time).
-//   slots      `max_slots` worker threads, each with its own CUDA stream and a
-//              persistent grid of 1/max_slots of the GPU, take the next batch
-//              of the oldest admitted request as soon as they are free, so a
-//              new request starts while older ones are still running and the
-//              batches of different requests overlap on the device.
-//   completion the last batch of a request adds the request's partial BC
-//              vectors in batch order into the caller's output and marks the
-//              request done.
-// A request's result therefore depends only on the request: alone or in a
-// mix of other requests it is bit-identical.
+//   admission  a request enters when its device footprint (the workspace of
+//              the batched launch it will run) fits in what is left of the
+//              memory budget; otherwise it waits in arrival order.
+//   slots      `max_slots` worker threads, each with its own CUDA stream, take
+//              the oldest admitted request as soon as they are free and run
+//              it as one call: its sources are regrouped and cut into batches
+//              of the width tuned for the graph, all batches in one persistent
+//              launch.  With several slots each launch is capped to its share
+//              of the SMs, so requests that arrive while others run start at
+//              once and their launches overlap on the device.
+// A request's batches, their order and the order in which their BC is added
+// depend only on the request (and the width tuned for the graph), so its
+// result is bit-identical alone or in any mix of other requests.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -46,30 +43,17 @@ static int64_t now_ns() {
         .count();
 }
 
-__global__ void sum_partials_kernel(const double* __restrict__ part, int nb, int64_t n, double* __restrict__ out) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += part[(int64_t)b * n + v];
-        out[v] = s;
-    }
-}
-
 struct Request {
     sp_request id = 0;
     Graph* g = nullptr;
     std::vector<int32_t> sources;
     sp_bc_opts opts{};
     double* bc_out = nullptr;
-    int width = 0;
-    int nbatches = 0;
-    int next_batch = 0;   // next batch to hand to a slot
-    int done_batches = 0;
     size_t footprint = 0;
-    double* partials = nullptr;  // [nbatches][n] when nbatches > 1
     sp_status status = SP_NOT_READY;
-    bool admitted = false, cancelled = false, finished = false;
+    bool admitted = false, taken = false, cancelled = false, finished = false;
     int64_t t_submit = 0, t_start = 0, t_done = 0;
-    sp_bc_stats stats{};  // summed over the request's batches
+    sp_bc_stats stats{};
 };
 
 struct Server {
@@ -81,11 +65,10 @@ struct Server {
     std::vector<Graph*> graphs;
     std::unordered_map<sp_request, std::shared_ptr<Request>> reqs;
     std::deque<std::shared_ptr<Request>> waiting;   // not yet admitted, arrival order
-    std::deque<std::shared_ptr<Request>> admitted;  // admitted with batches left, arrival order
+    std::deque<std::shared_ptr<Request>> admitted;  // admitted, not yet taken by a slot, arrival order
     std::vector<std::thread> workers;
     bool stopping = false;
     sp_request next_id = 1;
-    cudaStream_t aux = nullptr;
 
     void admit_locked() {
         while (!waiting.empty()) {
@@ -117,95 +100,43 @@ struct Server {
     }
 
     void worker(int slot) {
+        (void)slot;
         cudaSetDevice(device);
         cudaStream_t st;
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        int sms = device_sm_count(device);
+        const int sms = device_sm_count(device);
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
-            cv_work.wait(lk, [&] {
-                if (stopping) return true;
-                for (auto& r : admitted)
-                    if (r->next_batch < r->nbatches) return true;
-                return false;
-            });
+            cv_work.wait(lk, [&] { return stopping || !admitted.empty(); });
             if (stopping) break;
-            std::shared_ptr<Request> r;
-            for (auto& x : admitted)
-                if (x->next_batch < x->nbatches) { r = x; break; }
-            if (!r) continue;
-            const int b = r->next_batch++;
-            if (r->next_batch == r->nbatches) {
-                for (auto it = admitted.begin(); it != admitted.end(); ++it)
-                    if (it->get() == r.get()) { admitted.erase(it); break; }
-            }
-            if (r->t_start == 0) r->t_start = now_ns();
-            bool skip = r->cancelled || r->status != SP_NOT_READY;
+            std::shared_ptr<Request> r = admitted.front();
+            admitted.pop_front();
+            r->taken = true;
+            r->t_start = now_ns();
+            const bool skip = r->cancelled;
             lk.unlock();
 
             sp_status rc = SP_OK;
             sp_bc_stats bst{};
             if (!skip) {
-                if (r->partials == nullptr && r->nbatches > 1) rc = SP_ERR_OOM;
-                const int lo = b * r->width;
-                const int cnt = std::min<int>(r->width, (int)r->sources.size() - lo);
+                const int cnt = (int)r->sources.size();
                 int32_t* d_src = nullptr;
-                if (rc == SP_OK) {
-                    cudaError_t e = cudaMallocAsync((void**)&d_src, sizeof(int32_t) * cnt, st);
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(d_src, r->sources.data() + lo, sizeof(int32_t) * cnt,
-                                            cudaMemcpyHostToDevice, st);
-                    if (e != cudaSuccess) rc = cuda_fail(e, "server batch sources");
-                }
+                cudaError_t e = cudaMallocAsync((void**)&d_src, sizeof(int32_t) * cnt, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(d_src, r->sources.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) rc = cuda_fail(e, "server request sources");
                 if (rc == SP_OK) {
                     sp_bc_opts o = r->opts;
-                    o.max_ctas = std::max(1, (sms * 4) / slots);
-                    if (o.batch == 0 && o.form != SP_FORM_PLAIN) o.batch = r->width;
-                    double* out = r->nbatches > 1 ? r->partials + (size_t)b * r->g->n : r->bc_out;
-                    rc = bc_device_entry(r->g, d_src, cnt, o, out, &bst, st);
+                    if (slots > 1 && o.max_ctas == 0) o.max_ctas = std::max(1, (sms * 4) / slots);
+                    rc = bc_device_entry(r->g, d_src, cnt, o, r->bc_out, &bst, st);
                 }
                 if (d_src) cudaFreeAsync(d_src, st);
                 cudaStreamSynchronize(st);
             }
 
             lk.lock();
-            if (rc != SP_OK && r->status == SP_NOT_READY) r->status = rc;
-            if (rc == SP_OK && !skip) {
-                r->stats.traversed_arcs += bst.traversed_arcs;
-                r->stats.reached += bst.reached;
-                r->stats.entries += bst.entries;
-                r->stats.scanned_arcs += bst.scanned_arcs;
-                r->stats.dag_arcs += bst.dag_arcs;
-                r->stats.kernel_ms += bst.kernel_ms;
-                r->stats.max_levels = std::max(r->stats.max_levels, bst.max_levels);
-                r->stats.batches += 1;
-                r->stats.batch = r->width;
-                r->stats.form = bst.form;
-                r->stats.promoted |= bst.promoted;
-                r->stats.sigma_float |= bst.sigma_float;
-                r->stats.launches += bst.launches;
-            }
-            r->done_batches++;
-            if (r->done_batches == r->nbatches) {
-                sp_status fin = r->cancelled ? SP_ERR_CANCELLED : r->status;
-                if (fin == SP_NOT_READY) fin = SP_OK;
-                if (fin == SP_OK && r->nbatches > 1) {
-                    lk.unlock();
-                    int64_t n = r->g->n;
-                    int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-                    if (grid < 1) grid = 1;
-                    sum_partials_kernel<<<grid, 256, 0, st>>>(r->partials, r->nbatches, n, r->bc_out);
-                    cudaError_t e = cudaGetLastError();
-                    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-                    if (e != cudaSuccess) fin = cuda_fail(e, "server reduction");
-                    lk.lock();
-                }
-                if (r->partials) {
-                    cudaFreeAsync(r->partials, st);
-                    r->partials = nullptr;
-                }
-                finish_locked(r, fin);
-            }
+            if (rc == SP_OK && !skip) r->stats = bst;
+            finish_locked(r, skip ? SP_ERR_CANCELLED : rc);
         }
         lk.unlock();
         cudaStreamSynchronize(st);
@@ -284,20 +215,10 @@ sp_status sp_bc_submit(sp_server sh, int32_t graph_id, const int32_t* sources, i
                 return fail(SP_ERR_INVALID_ARG, "source " + std::to_string(i) + " out of range");
     }
     const bool plain = r->opts.form == SP_FORM_PLAIN || (r->opts.form == SP_FORM_AUTO && nsrc < 2);
-    r->width = plain ? std::max(1, nsrc) : (r->opts.batch > 0 ? r->opts.batch : default_batch_width(nsrc));
-    r->nbatches = nsrc == 0 ? 1 : (nsrc + r->width - 1) / r->width;
+    const int width = r->opts.batch > 0 ? r->opts.batch : (nsrc >= 128 ? 256 : default_batch_width(nsrc));
     const bool theta32 = r->opts.precision == SP_FP32_DELTA;
-    size_t ws = plain ? (size_t)g->n * 40 + (size_t)g->nnz : batched_workspace_bytes(g, r->width, theta32);
-    r->footprint = (r->nbatches > 1 ? (size_t)r->nbatches * (size_t)g->n * sizeof(double) : 0) +
-                   (size_t)std::min(r->nbatches, s->slots) * ws;
+    r->footprint = plain ? (size_t)g->n * 40 + (size_t)g->nnz : batched_workspace_bytes(g, width, theta32);
     r->t_submit = now_ns();
-    if (r->nbatches > 1) {
-        cudaError_t e = cudaMalloc((void**)&r->partials, (size_t)r->nbatches * (size_t)g->n * sizeof(double));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(SP_ERR_OOM, "partial BC buffers");
-        }
-    }
     if (nsrc == 0) {
         if (g->n > 0 && cudaMemset(bc_out, 0, sizeof(double) * (size_t)g->n) != cudaSuccess)
             return cuda_fail(cudaGetLastError(), "zeroing bc_out");
@@ -393,8 +314,6 @@ sp_status sp_server_destroy(sp_server sh) {
         s->cv_work.notify_all();
     }
     for (auto& t : s->workers) t.join();
-    for (auto& kv : s->reqs)
-        if (kv.second->partials) cudaFree(kv.second->partials);
     delete s;
     return SP_OK;
 }

@@ -54,3 +54,20 @@ def test_ranks_draw_their_own_sources():
 def test_single_rank_has_no_collective():
     v, e2e, tmax = bench.combine_ranks(None, 1, 800.0, 4, 4e9, 2.0, 4e9)
     assert tmax == 800.0 and abs(v - 4e9 / 0.2 / 1e9) < 1e-9 and abs(e2e - 2.0) < 1e-9
+
+
+def test_recorded_traffic_only_for_the_current_kernels(tmp_path, monkeypatch):
+    # A traffic record counts only when workload, batch width and the hash of
+    # the kernel sources all match; any kernel edit makes it stale (None).
+    h = bench.kernel_source_hash()
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "t.md").write_text(
+        "# capture\n"
+        f"traffic-record: workload=w1 width=128 sources={h} dram_bytes=1.5e11\n"
+        "traffic-record: workload=w1 width=256 sources=0000000000000000 dram_bytes=9e9\n")
+    csrc = os.path.join(bench.ROOT, "paper_2401_02472_gb300")
+    os.symlink(csrc, tmp_path / "paper_2401_02472_gb300")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_traffic("w1", 128) == 1.5e11
+    assert bench.recorded_traffic("w1", 256) is None
+    assert bench.recorded_traffic("w2", 128) is None
