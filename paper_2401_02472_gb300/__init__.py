@@ -23,7 +23,7 @@ SP_OK, SP_NOT_READY = 0, 1
 SP_ERR_INVALID_ARG, SP_ERR_OOM, SP_ERR_CUDA, SP_ERR_TOO_LARGE = -1, -2, -3, -4
 SP_ERR_RANGE, SP_ERR_TIMEOUT, SP_ERR_CANCELLED, SP_ERR_BAD_GRAPH, SP_ERR_NO_DEVICE = -5, -6, -7, -8, -9
 SP_FP64, SP_FP32_DELTA = 0, 1
-SP_FORM_AUTO, SP_FORM_PLAIN, SP_FORM_BATCHED = 0, 1, 2
+SP_FORM_AUTO, SP_FORM_PLAIN, SP_FORM_BATCHED, SP_FORM_SMALL = 0, 1, 2, 3
 SP_DRIVER_AUTO, SP_DRIVER_PERSISTENT, SP_DRIVER_GRAPH = 0, 1, 2
 SP_GRAPH_CHECK_SYMMETRIC = 0x1
 SP_DEBUG_SKIP_BARRIER = 0x1

@@ -98,6 +98,20 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result);
 sp_status run_plain_graph(const PlainLaunch& L, LaunchResult* result);
 void destroy_step_cache(Graph* g);
 
+struct SmallLaunch {
+    const Graph* g;
+    const int32_t* d_sources;
+    int32_t nsrc;
+    double* d_bc;
+    bool theta_f32;
+    int max_ctas;
+    cudaStream_t stream;
+};
+
+// Small-graph form: one block per source, per-source state in shared memory.
+sp_status run_small(const SmallLaunch& L, LaunchResult* result);
+int64_t small_form_max_n(int device);  // largest n whose state fits one block's shared memory
+
 struct BatchedLaunch {
     const Graph* g;
     const int32_t* d_sources;

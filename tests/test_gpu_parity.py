@@ -171,7 +171,7 @@ def test_er2000_all_sources_both_forms():
     assert abs(got.sum() - bf.pair_distance_excess(g, srcs)) <= 1e-9 * got.sum()
 
 
-@pytest.mark.parametrize("form", [sp.SP_FORM_PLAIN, sp.SP_FORM_BATCHED])
+@pytest.mark.parametrize("form", [sp.SP_FORM_PLAIN, sp.SP_FORM_BATCHED, sp.SP_FORM_SMALL])
 @pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
 def test_hubs_split_into_segments(form, precision):
     g, G = hub_graph()
@@ -224,6 +224,39 @@ def test_run_to_run_bit_identical(form, batch):
     for _ in range(3):
         b, _ = gpu_bc(G, srcs, sp.SP_FP32_DELTA, form, batch)
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_bc_small(name, precision):
+    # One block per source with the per-source state in shared memory.
+    g, G = graph(name)
+    srcs = gen.sources(g, min(40, int((g.degrees() > 0).sum())), 8)
+    got, st = gpu_bc(G, srcs, precision, sp.SP_FORM_SMALL)
+    want, ost = oracle.bc(g, srcs)
+    assert_bc_close(got, want, RTOL[precision], f"{name} small")
+    assert st["form"] == sp.SP_FORM_SMALL
+    assert st["traversed_arcs"] == int(ost["arcs"].sum())
+    assert st["max_levels"] == int(ost["levels"].max())
+    again, _ = gpu_bc(G, srcs, precision, sp.SP_FORM_SMALL)
+    assert np.array_equal(got, again)
+
+
+def test_small_form_limits_and_fallback():
+    # Path counts past 2^64 on an 80 x 80 grid (C(158, 79) ~ 2^154): the small
+    # form stops and the call reruns in the plain form with FP64 counts.
+    g = gen.grid(80, 80)
+    G = device_graph(g)
+    srcs = np.array([0, 79, 6399, 3240], np.int32)
+    got, st = gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_SMALL)
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(got, want, 1e-9, "grid80 small -> plain")
+    assert st["form"] == sp.SP_FORM_PLAIN and st["sigma_float"] == 1
+    # too many vertices for one block's shared memory
+    big = gen.rmat(15, 4, 3)
+    with pytest.raises(sp.StarbcError) as e:
+        gpu_bc(device_graph(big), [1, 2], sp.SP_FP64, sp.SP_FORM_SMALL)
+    assert e.value.status == sp.SP_ERR_TOO_LARGE
 
 
 @pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
