@@ -75,6 +75,7 @@ typedef int64_t sp_request;
 
 /* Flags for sp_graph_create. */
 #define SP_GRAPH_CHECK_SYMMETRIC 0x1u /* also verify every arc (u,v) has its reverse (v,u) */
+#define SP_GRAPH_SORT_ROWS 0x2u       /* sort every row by neighbour id on the GPU (after the copy) */
 
 typedef struct {
     int32_t n;
@@ -93,11 +94,28 @@ typedef struct {
  * The inputs are copied before return (the caller may free them); the graph
  * owns its device memory until sp_graph_destroy.  Blocks until done.
  * n >= 0; nnz < 2^31.  Returns SP_ERR_BAD_GRAPH on a CSR that fails, with the
- * first offending index in sp_last_error().
+ * first offending index in sp_last_error().  With SP_GRAPH_SORT_ROWS the rows
+ * of the copy are sorted (deterministically, on the GPU) before the checks.
  */
 SP_API sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
                           uint32_t flags, sp_stream stream, sp_graph* out);
 SP_API sp_status sp_graph_destroy(sp_graph g);
+
+/*
+ * Build a graph from an undirected edge list on the GPU (the CSR offset array
+ * and edge list of Section 3.1): for every edge i with src[i] != dst[i] both
+ * arcs are stored, rows are sorted by neighbour id and repeated arcs are kept
+ * once; self-loops are dropped.  src, dst: int32 [m], host or device, copied
+ * before return.  n >= 0 vertices; 2 m < 2^31.  flags: 0 or
+ * SP_GRAPH_CHECK_SYMMETRIC.  An endpoint outside [0, n) gives
+ * SP_ERR_BAD_GRAPH with the edge index in sp_last_error().  Blocks until done.
+ */
+SP_API sp_status sp_graph_from_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, uint32_t flags,
+                                     sp_stream stream, sp_graph* out);
+
+/* Copy the graph's CSR out: row_ptr_out int32 [n+1], col_idx_out int32 [nnz],
+   host or device.  Returns when the copy is complete. */
+SP_API sp_status sp_graph_get_csr(sp_graph g, int32_t* row_ptr_out, int32_t* col_idx_out, sp_stream stream);
 SP_API sp_status sp_graph_get_info(sp_graph g, sp_graph_info* out);
 
 /* ------------------------------------------------------------------------ */
@@ -132,7 +150,8 @@ typedef struct {
    source at a time over the whole GPU, no device-side waits.
    AUTO: PERSISTENT, unless a timing trial on the first eight sources of a
    call with at least 16 sources, run once per graph shape and cached, finds
-   GRAPH faster. */
+   GRAPH faster.  With bottom_up = 0 the same trial also picks the bottom-up
+   threshold (never, n/100 or n/20). */
 enum { SP_DRIVER_AUTO = 0, SP_DRIVER_PERSISTENT = 1, SP_DRIVER_GRAPH = 2 };
 
 /* flags: run the batched form's sources in the caller's order.  By default
@@ -160,8 +179,8 @@ typedef struct {
     int32_t sigma_float;    /* 1 when path counts needed FP64 with per-level rescaling (above 2^64) */
     int32_t launches;       /* kernel launches of the call, including reruns and autotuning trials */
     int32_t tuned;          /* 1 when this call ran an autotuner (batch width, or the plain form's driver) */
-    int32_t driver;         /* plain form: SP_DRIVER_PERSISTENT or SP_DRIVER_GRAPH; 0 for the batched form */
-    int32_t reserved;
+    int32_t driver;         /* plain form: SP_DRIVER_PERSISTENT or SP_DRIVER_GRAPH; 0 for the other forms */
+    int32_t bottom_up;      /* plain form: levels wider than n / bottom_up were discovered bottom-up; 0 = never */
 } sp_bc_stats;
 
 SP_API void sp_bc_opts_default(sp_bc_opts* o);

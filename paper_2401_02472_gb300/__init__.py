@@ -25,7 +25,7 @@ SP_ERR_RANGE, SP_ERR_TIMEOUT, SP_ERR_CANCELLED, SP_ERR_BAD_GRAPH, SP_ERR_NO_DEVI
 SP_FP64, SP_FP32_DELTA = 0, 1
 SP_FORM_AUTO, SP_FORM_PLAIN, SP_FORM_BATCHED, SP_FORM_SMALL = 0, 1, 2, 3
 SP_DRIVER_AUTO, SP_DRIVER_PERSISTENT, SP_DRIVER_GRAPH = 0, 1, 2
-SP_GRAPH_CHECK_SYMMETRIC = 0x1
+SP_GRAPH_CHECK_SYMMETRIC, SP_GRAPH_SORT_ROWS = 0x1, 0x2
 SP_DEBUG_SKIP_BARRIER = 0x1
 SP_BC_KEEP_ORDER = 0x1
 
@@ -43,10 +43,10 @@ class sp_bc_stats(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("batches", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("promoted", ctypes.c_int32), ("sigma_float", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("tuned", ctypes.c_int32), ("driver", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("bottom_up", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class sp_graph_info(ctypes.Structure):
@@ -70,6 +70,8 @@ SIGNATURES = {
     "sp_graph_create": ([_P, _P, _I32, _I64, _U32, _P, _P], ctypes.c_int),
     "sp_graph_destroy": ([_P], ctypes.c_int),
     "sp_graph_get_info": ([_P, _P], ctypes.c_int),
+    "sp_graph_from_edges": ([_P, _P, _I64, _I32, _U32, _P, _P], ctypes.c_int),
+    "sp_graph_get_csr": ([_P, _P, _P, _P], ctypes.c_int),
     "sp_bc_opts_default": ([_P], None),
     "sp_bc": ([_P, _P, _I32, _P, _P], ctypes.c_int),
     "sp_bc_ex": ([_P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
@@ -171,6 +173,24 @@ def sp_graph_create(row_ptr, col_idx, n: int | None = None, nnz: int | None = No
 
 def sp_graph_destroy(g: int):
     _check(lib.sp_graph_destroy(g), "sp_graph_destroy")
+
+
+def sp_graph_from_edges(src, dst, n: int, flags: int = 0, stream=None) -> int:
+    _check_dtype(src, "int32", "src")
+    _check_dtype(dst, "int32", "dst")
+    m = _count(src)
+    if _count(dst) != m:
+        raise ValueError("src and dst differ in length")
+    h = ctypes.c_void_p()
+    _check(lib.sp_graph_from_edges(_ptr(src) if m else None, _ptr(dst) if m else None, m, n, flags,
+                                   _stream(stream), ctypes.byref(h)), "sp_graph_from_edges")
+    return h.value
+
+
+def sp_graph_get_csr(g: int, row_ptr_out, col_idx_out, stream=None):
+    _check_dtype(row_ptr_out, "int32", "row_ptr_out")
+    _check_dtype(col_idx_out, "int32", "col_idx_out")
+    _check(lib.sp_graph_get_csr(g, _ptr(row_ptr_out), _ptr(col_idx_out), _stream(stream)), "sp_graph_get_csr")
 
 
 def sp_graph_get_info(g: int) -> dict:
@@ -303,6 +323,23 @@ class Graph:
         self.info = sp_graph_get_info(self.handle)
         self.n = self.info["n"]
         self.nnz = self.info["nnz"]
+
+    @classmethod
+    def from_edges(cls, src, dst, n: int, flags: int = 0, stream=None) -> "Graph":
+        """Symmetric, deduplicated graph built on the GPU from an edge list."""
+        self = cls.__new__(cls)
+        self.handle = sp_graph_from_edges(src, dst, n, flags, stream)
+        self.info = sp_graph_get_info(self.handle)
+        self.n = self.info["n"]
+        self.nnz = self.info["nnz"]
+        return self
+
+    def csr(self):
+        """The resident CSR as numpy arrays (row_ptr, col_idx)."""
+        rp = np.empty(self.n + 1, np.int32)
+        ci = np.empty(max(self.nnz, 1), np.int32)
+        sp_graph_get_csr(self.handle, rp, ci)
+        return rp, ci[: self.nnz]
 
     def close(self):
         if getattr(self, "handle", None):

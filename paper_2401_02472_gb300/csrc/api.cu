@@ -219,36 +219,51 @@ static sp_status autotune_width(Graph* g, const int32_t* d_src, int32_t nsrc, co
 
 int default_batch_width(int32_t nsrc) { return nsrc > 32 ? 64 : 32; }
 
-// Plain-form level-loop drivers chosen by timing, keyed like the widths.
-static std::map<std::tuple<int32_t, int64_t, int32_t, int32_t>, int> g_driver;
+// Plain-form choices made by timing, keyed like the widths: the level-loop
+// driver and the bottom-up threshold (a value for sp_bc_opts.bottom_up).
+struct PlainTune {
+    int driver;
+    int bottom_up;
+};
+static std::map<std::tuple<int32_t, int64_t, int32_t, int32_t>, PlainTune> g_plain_tune;
 
-// Time both drivers of the plain form on the call's first eight sources and
-// keep the one with the most traversed arcs per second of kernel time.
-static sp_status autotune_driver(Graph* g, const int32_t* d_src, const sp_bc_opts& o, cudaStream_t st, int* driver,
-                                 int* launches) {
+// Time the plain form on the call's first eight sources: the persistent
+// driver with bottom-up discovery off, at n/100 and at n/20 (unless the
+// caller fixed the threshold), then the graph driver with the best threshold;
+// keep the pair with the most traversed arcs per second of kernel time.
+static sp_status autotune_plain(Graph* g, const int32_t* d_src, const sp_bc_opts& o, cudaStream_t st,
+                                PlainTune* out, int* launches) {
     double* scratch = nullptr;
     SP_CUDA(cudaMallocAsync((void**)&scratch, sizeof(double) * (size_t)g->n, st));
     double best_rate = -1.0;
-    int best = SP_DRIVER_PERSISTENT;
-    for (int drv : {SP_DRIVER_PERSISTENT, SP_DRIVER_GRAPH}) {
+    PlainTune best{SP_DRIVER_PERSISTENT, o.bottom_up};
+    auto trial = [&](int drv, int bu) -> sp_status {
         sp_bc_opts t = o;
         t.form = SP_FORM_PLAIN;
         t.driver = drv;
+        t.bottom_up = bu;
         sp_bc_stats ts;
         sp_status rc = bc_device(g, d_src, 8, t, scratch, &ts, st);
         *launches += ts.launches;
-        if (rc != SP_OK) {
-            cudaFreeAsync(scratch, st);
-            return rc;
-        }
-        double rate = ts.kernel_ms > 0 ? (double)ts.traversed_arcs / ts.kernel_ms : 0.0;
+        if (rc != SP_OK) return rc;
+        const double rate = ts.kernel_ms > 0 ? (double)ts.traversed_arcs / ts.kernel_ms : 0.0;
         if (rate > best_rate) {
             best_rate = rate;
-            best = drv;
+            best = PlainTune{drv, bu};
         }
+        return SP_OK;
+    };
+    sp_status rc = SP_OK;
+    if (o.bottom_up != 0) {
+        rc = trial(SP_DRIVER_PERSISTENT, o.bottom_up);
+    } else {
+        for (int bu : {-1, 100, 20})
+            if (rc == SP_OK) rc = trial(SP_DRIVER_PERSISTENT, bu);
     }
+    if (rc == SP_OK) rc = trial(SP_DRIVER_GRAPH, best.bottom_up);
     cudaFreeAsync(scratch, st);
-    *driver = best;
+    if (rc != SP_OK) return rc;
+    *out = best;
     return SP_OK;
 }
 
@@ -384,22 +399,22 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         if (g->theta_f64) theta_f32 = false;
         sigma_float = g->sigma_float;
     }
-    {
-        sp_status rc = ensure_top_bfs(g, st);
-        if (rc != SP_OK) return rc;
-    }
     int form = o.form;
     // Automatic form: graphs whose per-source state fits in shared memory run
     // one block per source; otherwise many narrow levels (high diameter)
     // favour small block groups, one source each, and wide levels with many
     // sources favour batches.  Path counts past 64 bits need the plain or
-    // batched form's FP64 representation.
-    if (form == SP_FORM_AUTO) {
-        if (!sigma_float && (int64_t)g->n <= small_form_max_n(g->device)) form = SP_FORM_SMALL;
-        else form = (nsrc >= 2 && g->top_levels <= 64) ? SP_FORM_BATCHED : SP_FORM_PLAIN;
-    }
-    if (form == SP_FORM_SMALL && (int64_t)g->n > small_form_max_n(g->device))
+    // batched form's FP64 representation.  Only the latter two need the
+    // eccentricity BFS (diameter estimate, group sizes, source regrouping).
+    const bool small_fits = (int64_t)g->n <= small_form_max_n(g->device);
+    if (form == SP_FORM_AUTO && !sigma_float && small_fits) form = SP_FORM_SMALL;
+    if (form == SP_FORM_SMALL && !small_fits)
         return fail(SP_ERR_TOO_LARGE, "graph too large for the small form (" + std::to_string(g->n) + " vertices)");
+    if (form != SP_FORM_SMALL) {
+        sp_status rc = ensure_top_bfs(g, st);
+        if (rc != SP_OK) return rc;
+    }
+    if (form == SP_FORM_AUTO) form = (nsrc >= 2 && g->top_levels <= 64) ? SP_FORM_BATCHED : SP_FORM_PLAIN;
     int width = 1, launches = 0, tuned = 0;
     if (form == SP_FORM_BATCHED) {
         if (o.batch > 0) {
@@ -423,22 +438,31 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         }
     }
     int driver = 0;
+    int bottom_up = o.bottom_up;
     if (form == SP_FORM_PLAIN) {
         driver = o.driver;
         if (o.debug_flags & SP_DEBUG_SKIP_BARRIER) driver = SP_DRIVER_PERSISTENT;
         if (driver == SP_DRIVER_AUTO) {
             auto key = tune_key(g, o.precision);
+            bool have = false;
             {
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                auto it = g_driver.find(key);
-                if (it != g_driver.end()) driver = it->second;
+                auto it = g_plain_tune.find(key);
+                if (it != g_plain_tune.end() && (o.bottom_up == 0 || it->second.bottom_up == o.bottom_up)) {
+                    driver = it->second.driver;
+                    bottom_up = it->second.bottom_up;
+                    have = true;
+                }
             }
-            if (driver == SP_DRIVER_AUTO && nsrc >= 16) {
-                sp_status trc = autotune_driver(g, d_src, o, st, &driver, &launches);
+            if (!have && nsrc >= 16) {
+                PlainTune t{};
+                sp_status trc = autotune_plain(g, d_src, o, st, &t, &launches);
                 if (trc != SP_OK) return trc;
                 tuned = 1;
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                driver = g_driver.emplace(key, driver).first->second;
+                if (o.bottom_up == 0) t = g_plain_tune.emplace(key, t).first->second;
+                driver = t.driver;
+                bottom_up = t.bottom_up;
             }
             if (driver == SP_DRIVER_AUTO) driver = SP_DRIVER_PERSISTENT;
         }
@@ -489,7 +513,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             L.stream = st;
             L.group_blocks = plain_group_blocks(g);
             L.level_cap = plain_lcap;
-            L.bottom_up_den = plain_bottom_up(g, o.bottom_up);
+            L.bottom_up_den = plain_bottom_up(g, bottom_up);
             rc = driver == SP_DRIVER_GRAPH ? run_plain_graph(L, &r) : run_plain(L, &r);
         } else {
             BatchedLaunch L{};
@@ -514,6 +538,8 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         launches += r.launches;
         if (r.err == kErrSigmaOverflow && form == SP_FORM_SMALL) {
             // the small form holds exact counts only: rerun in the plain form
+            sp_status trc = ensure_top_bfs(g, st);
+            if (trc != SP_OK) return trc;
             form = SP_FORM_PLAIN;
             driver = SP_DRIVER_PERSISTENT;
             sigma_float = true;
@@ -570,6 +596,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         stats->launches = launches;
         stats->tuned = tuned;
         stats->driver = form == SP_FORM_PLAIN ? driver : 0;
+        stats->bottom_up = form == SP_FORM_PLAIN ? plain_bottom_up(g, bottom_up) : 0;
     }
     return SP_OK;
 }
@@ -620,7 +647,7 @@ sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_
     if (nnz >= (int64_t)INT32_MAX) return fail(SP_ERR_TOO_LARGE, "nnz must be below 2^31 (int32 row_ptr)");
     if (!row_ptr) return fail(SP_ERR_INVALID_ARG, "row_ptr is NULL");
     if (nnz > 0 && !col_idx) return fail(SP_ERR_INVALID_ARG, "col_idx is NULL");
-    if (flags & ~(uint32_t)SP_GRAPH_CHECK_SYMMETRIC) return fail(SP_ERR_INVALID_ARG, "unknown flag");
+    if (flags & ~(uint32_t)(SP_GRAPH_CHECK_SYMMETRIC | SP_GRAPH_SORT_ROWS)) return fail(SP_ERR_INVALID_ARG, "unknown flag");
     sp_status rc = check_device();
     if (rc != SP_OK) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -646,10 +673,82 @@ sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_
                             is_device_ptr(col_idx) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "copying the graph"));
     std::string detail;
-    rc = validate_graph(g, flags, st, &detail);
+    if (flags & SP_GRAPH_SORT_ROWS) {
+        // row offsets and ids are checked before the sort reads them
+        rc = validate_graph(g, 0, st, &detail);
+        if (rc == SP_ERR_BAD_GRAPH) return cleanup(fail(rc, detail));
+        if (rc != SP_OK) return cleanup(rc);
+        rc = sort_rows_device(g->d_rp, g->d_ci, n, nnz, st);
+        if (rc != SP_OK) return cleanup(rc);
+    }
+    rc = validate_graph(g, flags & SP_GRAPH_CHECK_SYMMETRIC, st, &detail);
     if (rc == SP_ERR_BAD_GRAPH) return cleanup(fail(rc, detail));
     if (rc != SP_OK) return cleanup(rc);
     *out = reinterpret_cast<sp_graph>(g);
+    return SP_OK;
+}
+
+sp_status sp_graph_from_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, uint32_t flags,
+                              sp_stream stream, sp_graph* out) {
+    set_last_error("");
+    if (!out) return fail(SP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || m < 0) return fail(SP_ERR_INVALID_ARG, "negative size");
+    if (m > 0 && (!src || !dst)) return fail(SP_ERR_INVALID_ARG, "edge arrays are NULL");
+    if (2 * m >= (int64_t)INT32_MAX) return fail(SP_ERR_TOO_LARGE, "2 m must be below 2^31 (int32 row_ptr)");
+    if (flags & ~(uint32_t)SP_GRAPH_CHECK_SYMMETRIC) return fail(SP_ERR_INVALID_ARG, "unknown flag");
+    sp_status rc = check_device();
+    if (rc != SP_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int32_t* d_src = nullptr;
+    int32_t* d_dst = nullptr;
+    auto stage = [&](const int32_t* p, int32_t** d) -> sp_status {
+        if (m == 0) return SP_OK;
+        if (is_device_ptr(p)) { *d = const_cast<int32_t*>(p); return SP_OK; }
+        SP_CUDA(cudaMallocAsync((void**)d, sizeof(int32_t) * (size_t)m, st));
+        SP_CUDA(cudaMemcpyAsync(*d, p, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, st));
+        return SP_OK;
+    };
+    struct Free {
+        const int32_t *hs, *hd;
+        int32_t *ds, *dd;
+        cudaStream_t s;
+        ~Free() {
+            if (ds && ds != hs) cudaFreeAsync(ds, s);
+            if (dd && dd != hd) cudaFreeAsync(dd, s);
+        }
+    };
+    rc = stage(src, &d_src);
+    if (rc == SP_OK) rc = stage(dst, &d_dst);
+    Free fr{src, dst, d_src, d_dst, st};
+    if (rc != SP_OK) return rc;
+    Graph* g = new Graph();
+    cudaGetDevice(&g->device);
+    g->n = n;
+    std::string detail;
+    rc = csr_from_edges(d_src, d_dst, m, n, st, &g->d_rp, &g->d_ci, &g->nnz, &detail);
+    if (rc == SP_OK) rc = validate_graph(g, flags, st, &detail);
+    if (rc != SP_OK) {
+        if (g->d_rp) cudaFree(g->d_rp);
+        if (g->d_ci) cudaFree(g->d_ci);
+        delete g;
+        return rc == SP_ERR_BAD_GRAPH ? fail(rc, detail) : rc;
+    }
+    *out = reinterpret_cast<sp_graph>(g);
+    return SP_OK;
+}
+
+sp_status sp_graph_get_csr(sp_graph gh, int32_t* row_ptr_out, int32_t* col_idx_out, sp_stream stream) {
+    set_last_error("");
+    if (!gh || !row_ptr_out || !col_idx_out) return fail(SP_ERR_INVALID_ARG, "NULL argument");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    auto kind = [](const void* p) { return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; };
+    cudaError_t e = cudaMemcpyAsync(row_ptr_out, g->d_rp, sizeof(int32_t) * ((size_t)g->n + 1), kind(row_ptr_out), st);
+    if (e == cudaSuccess && g->nnz > 0)
+        e = cudaMemcpyAsync(col_idx_out, g->d_ci, sizeof(int32_t) * (size_t)g->nnz, kind(col_idx_out), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "copying the CSR");
     return SP_OK;
 }
 

@@ -123,11 +123,20 @@ __global__ void __launch_bounds__(kSmallThreads, 2) small_kernel(SmallArgs a) {
                     return 0ull;
                 };
                 if (deg <= 32) {
-                    for (int k = 0; k < deg; ++k) {
-                        const unsigned long long c = visit(__ldg(&a.ci[beg + k]));
-                        const unsigned long long s = acc + c;
-                        ovf |= s < acc;
-                        acc = s;
+                    // column ids eight at a time (independent cached loads), then
+                    // the shared-memory visits in CSR order
+                    for (int k0 = 0; k0 < deg; k0 += 8) {
+                        int u[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) u[i] = k0 + i < deg ? __ldg(&a.ci[beg + k0 + i]) : -1;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            if (u[i] < 0) continue;
+                            const unsigned long long c = visit(u[i]);
+                            const unsigned long long s = acc + c;
+                            ovf |= s < acc;
+                            acc = s;
+                        }
                     }
                 }
                 unsigned big = __ballot_sync(kFull, deg > 32);
@@ -184,9 +193,13 @@ __global__ void __launch_bounds__(kSmallThreads, 2) small_kernel(SmallArgs a) {
                 }
                 double acc = 0.0;
                 if (deg <= 32) {
-                    for (int k = 0; k < deg; ++k) {
-                        const int w = __ldg(&a.ci[beg + k]);
-                        if (lvl[w] == dd + 1) acc += theta_of(w);
+                    for (int k0 = 0; k0 < deg; k0 += 8) {
+                        int w[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) w[i] = k0 + i < deg ? __ldg(&a.ci[beg + k0 + i]) : -1;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (w[i] >= 0 && lvl[w[i]] == dd + 1) acc += theta_of(w[i]);
                     }
                 }
                 unsigned big = __ballot_sync(kFull, deg > 32);
@@ -253,13 +266,18 @@ static __global__ void small_sum_kernel(const double* __restrict__ part, int npa
 }
 
 int64_t small_form_max_n(int device) {
-    int optin = 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
+    static int64_t cache[64] = {0};
+    if (device < 0 || device >= 64) return 0;
+    if (cache[device] == 0) {
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        // the kernel's static shared memory is a few dozen bytes
+        cache[device] = std::max<int64_t>(1, ((int64_t)optin - 256 - 64) / 16);
     }
-    // static shared memory of the kernel is a few dozen bytes
-    return std::max<int64_t>(0, ((int64_t)optin - 256 - 64) / 16);
+    return cache[device];
 }
 
 sp_status run_small(const SmallLaunch& L, LaunchResult* result) {

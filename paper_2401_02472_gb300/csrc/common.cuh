@@ -206,6 +206,10 @@ __device__ __forceinline__ float warp_sum_f32(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
+__device__ __forceinline__ int warp_sum_i32(int v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
 __device__ __forceinline__ int warp_max_i32(int v) {
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
     return v;

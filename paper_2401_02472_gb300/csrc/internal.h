@@ -133,6 +133,12 @@ sp_status run_batched(const BatchedLaunch& L, LaunchResult* result);
 template <int W>
 sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result);
 
+// CSR construction (graph_build.cu): sort every row in place; build a
+// symmetric, deduplicated CSR from an edge list (device arrays).
+sp_status sort_rows_device(const int32_t* d_rp, int32_t* d_ci, int32_t n, int64_t nnz, cudaStream_t st);
+sp_status csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, cudaStream_t st,
+                         int32_t** d_rp_out, int32_t** d_ci_out, int64_t* nnz_out, std::string* detail);
+
 // Graph validation kernels.
 sp_status validate_graph(Graph* g, uint32_t flags, cudaStream_t stream, std::string* detail);
 
