@@ -132,10 +132,14 @@ def run_serving(args, world):
     sub0 = times[0][0]
     lat, arcs = [], 0
     first_sub, last_done = None, 0
+    service, kernel, per_graph = [], [], {}
     for (ta, gi, srcs), (ts, tb, td), st in zip(reqs, times, stats):
         if ta < warm:
             continue
         lat.append((td - ts) / 1e6)
+        service.append((td - tb) / 1e6)
+        kernel.append(st["kernel_ms"])
+        per_graph.setdefault(gi, []).append((td - tb) / 1e6)
         arcs += st["traversed_arcs"]
         first_sub = ts if first_sub is None else min(first_sub, ts)
         last_done = max(last_done, td)
@@ -179,6 +183,10 @@ def run_serving(args, world):
                    "rate_per_s": args.rate, "duration_s": args.duration, "warmup_s": warm, "slots": args.slots,
                    "budget_gib": args.serve_budget, "requests": len(reqs)},
         "serving": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "requests_measured": len(lat),
+                    # time a slot spent on a request (start to done), and the kernels' share of it
+                    "service_ms_mean": float(np.mean(service)) if service else None,
+                    "kernel_ms_mean": float(np.mean(kernel)) if kernel else None,
+                    "service_ms_mean_per_graph": {str(k): round(float(np.mean(v)), 3) for k, v in sorted(per_graph.items())},
                     "one_at_a_time_plain": {"p50_ms": pct(base_lat, 50), "p99_ms": pct(base_lat, 99),
                                             "gteps": base_arcs / max(base_window, 1e-9) / 1e9,
                                             "requests_measured": len(base_lat)},

@@ -217,7 +217,7 @@ SP_API sp_status sp_sigma(sp_graph g, int32_t src, double* mant_out, int64_t* ex
  * framework that owns all device memory, real-time or serving loops that
  * must not call an allocator mid-run, and runtimes with a fixed memory plan).
  * It runs the plain form with all of its scratch in one static device array
- * of about 16 MB, reserved on every GPU that loads the library until the
+ * of about 18 MB, reserved on every GPU that loads the library until the
  * process exits, and calls no allocator.
  *   row_ptr[n+1], col_idx[nnz], sources[nsrc], bc_out[n]: device memory of
  *   the current device; the same CSR rules as sp_graph_create, checked on

@@ -136,9 +136,25 @@ struct BatchKernel {
     bool ovf = false;
     unsigned long long my_smax = 0;  // largest integer path count this thread stored at this level
     unsigned long long st_arcs = 0, st_reached = 0, st_entries = 0, st_scanned = 0, st_dag = 0;
+#ifdef SP_PROFILE
+    // SM cycles by kind of work: 0-3 chunk / segment work (forward, backward),
+    // 4 barrier, 5 other, 6 discovery, 7 parent/child pulls
+    unsigned long long prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long prof_t = 0;
+    __device__ __forceinline__ void mark(int cat) {
+        const unsigned long long t = clock64();
+        prof[cat] += t - prof_t;
+        prof_t = t;
+    }
+#else
+    __device__ __forceinline__ void mark(int) {}
+#endif
 
     // Arcs whose row loads a warp issues together: chunks, and segments of long rows.
-    static constexpr int kGChunk = W >= 8 ? 2 : 8 / W;
+#ifndef SP_GCHUNK
+#define SP_GCHUNK 8
+#endif
+    static constexpr int kGChunk = (SP_GCHUNK / W) > 0 ? SP_GCHUNK / W : 1;
 #ifndef SP_GSEG
 #define SP_GSEG 16
 #endif
@@ -390,13 +406,16 @@ struct BatchKernel {
 #pragma unroll
                     for (int k = 0; k < W; ++k) { m[k] = Fj[k] & p[k]; st_dag += __popc(m[k]); }
                 }
+                mark(0);
                 discover(u, Fj);
+                mark(6);
             }
             if (d > 0) {
                 uint32_t anym = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) anym |= m[k];
                 const unsigned pend = __ballot_sync(kFull, anym != 0u);
+                mark(0);
                 pull_window<kGChunk>(sig(), u, j, m, pend, acc, [&](int ej) {
                     if (ej != cur_e) {
                         flush_current();
@@ -405,6 +424,7 @@ struct BatchKernel {
                         for (int k = 0; k < W; ++k) acc[k] = 0;
                     }
                 });
+                mark(7);
             }
         }
         flush_current();
@@ -448,14 +468,18 @@ struct BatchKernel {
 #pragma unroll
                     for (int k = 0; k < W; ++k) { m[k] = F[k] & p[k]; st_dag += __popc(m[k]); }
                 }
+                mark(1);
                 discover(u, F);
+                mark(6);
             }
             if (d > 0) {
                 uint32_t anym = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) anym |= m[k];
                 const unsigned pend = __ballot_sync(kFull, anym != 0u);
+                mark(1);
                 pull_window<kGSeg>(sig(), u, 0, m, pend, acc, [](int) {});
+                mark(7);
             }
         }
         if (lane == 0) st_scanned += (unsigned long long)(end - beg);
@@ -558,9 +582,11 @@ struct BatchKernel {
                 anym |= m[k];
             }
             const unsigned pend = __ballot_sync(kFull, has && anym != 0u);
+            mark(2);
             pull_window<kGChunk>(th(), w, j, m, pend, acc, [&](int ej) {
                 if (ej > next_flush) flush_upto(ej);
             });
+            mark(7);
         }
         flush_upto(32);
     }
@@ -605,7 +631,9 @@ struct BatchKernel {
                 for (int k = 0; k < W; ++k) { m[k] = c[k] & F[k]; anym |= m[k]; }
             }
             const unsigned pend = __ballot_sync(kFull, anym != 0u);
+            mark(3);
             pull_window<kGSeg>(th(), w, 0, m, pend, acc, [](int) {});
+            mark(7);
         }
         if (lane == 0) st_scanned += (unsigned long long)(end - beg);
         if (nseg == 1) {
@@ -678,17 +706,9 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
     int levels_max = 0;
     int stamp_base = 1;
 #ifdef SP_PROFILE
-    unsigned long long prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    unsigned long long prof_t = clock64();
-#define SP_PROF_MARK(cat)                        \
-    do {                                         \
-        unsigned long long t_ = clock64();       \
-        prof[(cat)] += t_ - prof_t;              \
-        prof_t = t_;                             \
-    } while (0)
-#else
-#define SP_PROF_MARK(cat) do {} while (0)
+    K.prof_t = clock64();
 #endif
+#define SP_PROF_MARK(cat) K.mark(cat)
     auto sync = [&]() -> bool {
         bool skip = (a.debug_flags & SP_DEBUG_SKIP_BARRIER) && blockIdx.x == 0 && phase == 1;
         SP_PROF_MARK(5);
@@ -923,7 +943,7 @@ out:
         }
 #ifdef SP_PROFILE
         if ((threadIdx.x & 31) == 0)
-            for (int c = 0; c < 8; ++c) atomicAdd(&ctl->prof[c], prof[c]);
+            for (int c = 0; c < 8; ++c) atomicAdd(&ctl->prof[c], K.prof[c]);
 #endif
     }
 }

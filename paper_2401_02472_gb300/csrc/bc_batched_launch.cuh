@@ -143,11 +143,11 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
 #ifdef SP_PROFILE
     {
         const char* names[8] = {"fwd chunks", "fwd segments", "bwd chunks", "bwd segments", "barrier", "other",
-                                "-", "-"};
+                                "discovery", "pulls"};
         unsigned long long tot = 0;
-        for (int c = 0; c < 6; ++c) tot += h.prof[c];
+        for (int c = 0; c < 8; ++c) tot += h.prof[c];
         fprintf(stderr, "profile W=%d grid=%d kernel %.3f ms, levels %d\n", W, grid, result->kernel_ms, h.max_levels);
-        for (int c = 0; c < 6; ++c)
+        for (int c = 0; c < 8; ++c)
             fprintf(stderr, "  %-13s %6.2f%%\n", names[c], tot ? 100.0 * (double)h.prof[c] / (double)tot : 0.0);
         fprintf(stderr, "  phase ms:");
         for (int p = 2; p < 256 && h.phase_ns[p]; ++p)

@@ -52,7 +52,8 @@ constexpr size_t kOffLvl = kOffCheck + align256(sizeof(NoallocCheck));
 constexpr size_t kOffSig = kOffLvl + align256(4 * kNoallocMaxN);
 constexpr size_t kOffTh = kOffSig + align256(8 * kNoallocMaxN);
 constexpr size_t kOffQ = kOffTh + align256(8 * kNoallocMaxN);
-constexpr size_t kOffQoff = kOffQ + align256(4 * kNoallocMaxN);
+constexpr size_t kOffQrow = kOffQ + align256(4 * kNoallocMaxN);
+constexpr size_t kOffQoff = kOffQrow + align256(8 * kNoallocMaxN);
 constexpr size_t kOffHubs = kOffQoff + align256(4 * kLevels);
 constexpr size_t kOffHoff = kOffHubs + align256(sizeof(HubRec) * kHcap);
 constexpr size_t kOffHcnt = kOffHoff + align256(4 * kLevels);
@@ -61,7 +62,7 @@ constexpr size_t kOffPart = kOffHdone + align256(4 * 2 * kHcap);
 constexpr size_t kOffEmax = kOffPart + align256(8 * kSegcap);
 constexpr size_t kOffEmin = kOffEmax + align256(4 * kLevels);
 constexpr size_t kOffFexp = kOffEmin + align256(4 * kLevels);
-constexpr size_t kScratchBytes = kOffFexp + align256(8 * kLevels);  // about 16 MB
+constexpr size_t kScratchBytes = kOffFexp + align256(8 * kLevels);  // about 18 MB
 
 static_assert(kLevels < INT32_MAX, "level capacity");
 
@@ -186,6 +187,7 @@ extern "C" sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_id
     a.sig = ws + kOffSig;
     a.th = ws + kOffTh;
     a.q = reinterpret_cast<int32_t*>(ws + kOffQ);
+    a.qrow = reinterpret_cast<int2*>(ws + kOffQrow);
     a.qoff = reinterpret_cast<int32_t*>(ws + kOffQoff);
     a.hubs = reinterpret_cast<HubRec*>(ws + kOffHubs);
     a.hcap = (int32_t)kHcap;

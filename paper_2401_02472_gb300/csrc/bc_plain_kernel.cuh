@@ -72,6 +72,7 @@ struct PlainArgs {
     void* sig;              // [n] 8-byte elements
     void* th;               // [n] 8-byte slots
     int32_t* q;             // [n] level stack
+    int2* qrow;             // [n] row start and degree of each level-stack entry
     int32_t* qoff;          // [lcap]
     int32_t* hoff;          // [lcap]
     unsigned long long* hcnt;  // [lcap]: records << 32 | segments, per level
@@ -102,13 +103,13 @@ struct PlainArgs {
 // with the group's own counters; the last block to arrive snapshots the
 // group's level-stack fill.  A group of one block needs only __syncthreads.
 static __device__ __noinline__ bool group_sync(Ctl* ctl, GroupCtl* gc, unsigned nblocks, uint64_t timeout_ns,
-                                               int phase, bool skip, int* qtail_snap) {
+                                               int phase, bool skip, int* qtail_snap, const int* block_qtail) {
     __shared__ int s_ok, s_snap;
     __syncthreads();
     if (nblocks == 1) {
         if (threadIdx.x == 0) {
             if (blockIdx.x < 1024) ctl->block_phase[blockIdx.x] = phase;
-            s_snap = ld_volatile(&gc->qtail);
+            s_snap = ld_volatile(block_qtail);
             s_ok = (ld_volatile(&ctl->err) == 0 && !skip) ? 1 : 0;
         }
         __syncthreads();
@@ -189,6 +190,7 @@ struct PlainKernel {
     Ctl* ctl;
     GroupCtl* gc;
     int lane;
+    int* qtail;  // level-stack fill: shared memory for a one-block group, else the group's counter
     int grp;     // group index
     size_t gn;   // group offset into [n] arrays
     size_t gl;   // group offset into [lcap] arrays
@@ -206,13 +208,15 @@ struct PlainKernel {
     unsigned long long st_arcs = 0, st_reached = 0, st_scanned = 0, st_dag = 0;
 
     __device__ PlainKernel(const PlainArgs& args, int g)
-        : a(args), ctl(args.ctl), gc(args.gctl + g), lane(lane_id()), grp(g), gn((size_t)g * (size_t)args.n),
+        : a(args), ctl(args.ctl), gc(args.gctl + g), lane(lane_id()), qtail(&(args.gctl + g)->qtail), grp(g),
+          gn((size_t)g * (size_t)args.n),
           gl((size_t)g * (size_t)args.lcap), gh((size_t)g * (size_t)args.hcap) {}
 
     __device__ __forceinline__ int32_t* lvl() const { return a.lvl + gn; }
     __device__ __forceinline__ SigT* sig() const { return reinterpret_cast<SigT*>(a.sig) + gn; }
     __device__ __forceinline__ ThT* th() const { return reinterpret_cast<ThT*>(reinterpret_cast<double*>(a.th) + gn); }
     __device__ __forceinline__ int32_t* q() const { return a.q + gn; }
+    __device__ __forceinline__ int2* qrow() const { return a.qrow + gn; }
     __device__ __forceinline__ int32_t* qoff() const { return a.qoff + gl; }
     __device__ __forceinline__ int32_t* hoff() const { return a.hoff + gl; }
     __device__ __forceinline__ unsigned long long* hcnt() const { return a.hcnt + gl; }
@@ -227,9 +231,11 @@ struct PlainKernel {
     // Level stack of a new source: src alone on level 0, sigma[src] = 1, and
     // src's hub record when its row is split into segments.  One thread.
     __device__ void start_source(int src) {
-        int du = a.rp[src + 1] - a.rp[src];
+        const int rb = a.rp[src];
+        int du = a.rp[src + 1] - rb;
         q()[0] = src;
-        gc->qtail = 1;
+        qrow()[0] = make_int2(rb, du);
+        *qtail = 1;
         qoff()[0] = 0;
         hoff()[0] = 0;
         hcnt()[0] = 0ull;
@@ -266,11 +272,13 @@ struct PlainKernel {
 
     // A vertex claimed for level `nl`: append to the level stack (and the hub list).
     __device__ void push(int u, int nl) {
-        int du = __ldg(&a.rp[u + 1]) - __ldg(&a.rp[u]);
+        const int rb = __ldg(&a.rp[u]);
+        int du = __ldg(&a.rp[u + 1]) - rb;
         bool hub = du > a.t_hub;
-        int pos = aggregated_slot(&gc->qtail);
+        int pos = aggregated_slot(qtail);
         if (pos >= a.n) { set_error(ctl, kErrCapacity); return; }
         q()[pos] = hub ? (int)((unsigned)u | kHubFlag) : u;
+        qrow()[pos] = make_int2(rb, du);
         if (hub) {
             int nseg = (du + a.seg - 1) / a.seg;
             unsigned long long old = atomicAdd(&hcnt()[nl], (1ull << 32) | (unsigned long long)(unsigned)nseg);
@@ -342,14 +350,24 @@ struct PlainKernel {
     __device__ void chunk(int e0, int qe, bool skip_arcs) {
         int e = e0 + lane;
         bool valid = e < qe;
-        unsigned qv = valid ? (unsigned)__ldcg(&q()[e]) : kHubFlag;
+        unsigned qv = kHubFlag;
+        int2 rw = make_int2(0, 0);
+        if (valid) {  // the entry and its row, stored together when it was pushed
+            qv = (unsigned)__ldcg(&q()[e]);
+            rw = __ldcg(&qrow()[e]);
+        }
         bool hubent = (qv & kHubFlag) != 0;
         int v = (int)(qv & kVertexMask);
-        if (valid && v >= a.n) { set_error(ctl, kErrCorrupt); valid = false; hubent = true; v = 0; }
+        if (valid && (v >= a.n || rw.x < 0 || rw.y < 0)) {
+            set_error(ctl, kErrCorrupt);
+            valid = false;
+            hubent = true;
+            v = 0;
+        }
         int beg = 0, deg = 0;
         if (!hubent) {
-            beg = __ldg(&a.rp[v]);
-            deg = __ldg(&a.rp[v + 1]) - beg;
+            beg = rw.x;
+            deg = rw.y;
         }
         int walk = skip_arcs ? 0 : deg;
         SigT sacc = 0;
@@ -526,6 +544,8 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
     const int g = blockIdx.x / a.gblocks;
     if (g >= a.ngroups) return;  // the host sizes the grid to ngroups * gblocks
     PlainKernel<SigT, ThT> K(a, g);
+    __shared__ int s_qtail;
+    if (a.gblocks == 1) K.qtail = &s_qtail;  // the whole group is this block
     Ctl* ctl = a.ctl;
     GroupCtl* gc = K.gc;
     const int tid = (blockIdx.x % a.gblocks) * blockDim.x + threadIdx.x;  // rank in the group
@@ -537,7 +557,7 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
     // Barrier between phases; the work counter of phase p+2 is cleared in phase p.
     auto sync = [&]() -> bool {
         bool skip = (a.debug_flags & SP_DEBUG_SKIP_BARRIER) && blockIdx.x == 0 && phase == 1;
-        bool ok = group_sync(ctl, gc, a.gblocks, a.timeout_ns, phase++, skip, &qsnap);
+        bool ok = group_sync(ctl, gc, a.gblocks, a.timeout_ns, phase++, skip, &qsnap, K.qtail);
         if (tid == 0) gc->work[(phase + 2) & 3] = 0u;
         return ok;
     };
@@ -673,8 +693,8 @@ out:
 // Offsets of the plain form's arrays inside its one workspace allocation
 // (per-group copies of every per-source array, 256-byte aligned).
 struct PlainLayout {
-    size_t ctl, gctl, zero_end, lvl, sig, th, q, qoff, hoff, hcnt, emax, emin, fexp, hubs, hdone, part, bcpart,
-        trace, bytes;
+    size_t ctl, gctl, zero_end, lvl, sig, th, q, qrow, qoff, hoff, hcnt, emax, emin, fexp, hubs, hdone, part,
+        bcpart, trace, bytes;
 };
 
 inline PlainLayout plain_layout(int64_t n, int64_t lcap, int64_t hcap, int64_t segcap, int ngroups, int grid,
@@ -690,6 +710,7 @@ inline PlainLayout plain_layout(int64_t n, int64_t lcap, int64_t hcap, int64_t s
     o.sig = take(8 * (size_t)n * G);
     o.th = take(8 * (size_t)n * G);
     o.q = take(sizeof(int32_t) * (size_t)n * G);
+    o.qrow = take(sizeof(int2) * (size_t)n * G);
     o.qoff = take(sizeof(int32_t) * (size_t)lcap * G);
     o.hoff = take(sizeof(int32_t) * (size_t)lcap * G);
     o.hcnt = take(sizeof(unsigned long long) * (size_t)lcap * G);
@@ -711,6 +732,7 @@ inline void plain_bind(PlainArgs& a, char* ws, const PlainLayout& o) {
     a.sig = ws + o.sig;
     a.th = ws + o.th;
     a.q = reinterpret_cast<int32_t*>(ws + o.q);
+    a.qrow = reinterpret_cast<int2*>(ws + o.qrow);
     a.qoff = reinterpret_cast<int32_t*>(ws + o.qoff);
     a.hoff = reinterpret_cast<int32_t*>(ws + o.hoff);
     a.hcnt = reinterpret_cast<unsigned long long*>(ws + o.hcnt);

@@ -162,9 +162,11 @@ def test_er2000_all_sources_both_forms():
     g, G = graph("er2000")
     srcs = np.arange(g.n, dtype=np.int32)
     want, _ = oracle.bc(g, srcs)
-    for form, batch in [(sp.SP_FORM_PLAIN, 0), (sp.SP_FORM_BATCHED, 64)]:
-        got, _ = gpu_bc(G, srcs, sp.SP_FP64, form, batch)
+    for form, batch in [(sp.SP_FORM_PLAIN, 0), (sp.SP_FORM_BATCHED, 64), (sp.SP_FORM_SMALL, 0), (sp.SP_FORM_AUTO, 0)]:
+        got, st = gpu_bc(G, srcs, sp.SP_FP64, form, batch)
         assert_bc_close(got, want, 1e-9, f"er2000 all sources form={form}")
+        if form == sp.SP_FORM_AUTO:
+            assert st["form"] == sp.SP_FORM_SMALL  # the benchmark configuration
     # the invariant: sum of BC = sum over reached ordered pairs of (d - 1)
     from tests import bruteforce as bf
 
@@ -190,14 +192,15 @@ def test_edge_cases():
     z, _ = gpu_bc(G, iso * 20, sp.SP_FP64, sp.SP_FORM_BATCHED, 32)
     assert np.array_equal(z, np.zeros(g.n))
     dup = [0, 0, 0, 41, 41, 50] * 7
-    for form in (sp.SP_FORM_PLAIN, sp.SP_FORM_BATCHED):
+    for form in (sp.SP_FORM_PLAIN, sp.SP_FORM_BATCHED, sp.SP_FORM_SMALL):
         got, _ = gpu_bc(G, dup, sp.SP_FP64, form, 32)
         want, _ = oracle.bc(g, dup)
         assert_bc_close(got, want, 1e-9, "duplicates")
     one = gen.from_edges(1, [])
     G1 = device_graph(one)
-    got, _ = gpu_bc(G1, [0, 0], sp.SP_FP64)
-    assert np.array_equal(got, np.zeros(1))
+    for form in (sp.SP_FORM_AUTO, sp.SP_FORM_PLAIN, sp.SP_FORM_SMALL):
+        got, _ = gpu_bc(G1, [0, 0], sp.SP_FP64, form)
+        assert np.array_equal(got, np.zeros(1))
     two = gen.path(2)
     G2 = device_graph(two)
     got, _ = gpu_bc(G2, [0, 1] * 20, sp.SP_FP64, sp.SP_FORM_BATCHED, 32)
