@@ -135,7 +135,12 @@ struct BatchKernel {
     int my_emax[W], my_emin[W];
     bool ovf = false;
     unsigned long long my_smax = 0;  // largest integer path count this thread stored at this level
-    unsigned long long st_arcs = 0, st_reached = 0, st_entries = 0, st_scanned = 0, st_dag = 0;
+    // Statistics live in this thread's slots of a shared-memory table (stride
+    // kBatchThreads): 0 traversed (arc, source), 1 reached (vertex, source),
+    // 2 entries, 3 scanned arcs, 4 DAG (arc, source) pairs.  Keeping them out
+    // of registers leaves more registers to the pull's loads in flight.
+    unsigned long long* sst = nullptr;
+    __device__ __forceinline__ void stat(int i, unsigned long long x) { sst[i * kBatchThreads] += x; }
 #ifdef SP_PROFILE
     // SM cycles by kind of work: 0-3 chunk / segment work (forward, backward),
     // 4 barrier, 5 other, 6 discovery, 7 parent/child pulls
@@ -350,6 +355,7 @@ struct BatchKernel {
     // ---------------- forward ----------------
     // Chunk of level-stack entries [e0, qe), at most 32.
     __device__ void fwd_chunk(int e0, int qe) {
+        unsigned dag = 0;  // DAG (arc, source) pairs seen by this lane
         const int e = e0 + lane;
         bool valid, hubent;
         int v;
@@ -361,16 +367,16 @@ struct BatchKernel {
         if (valid) {
             load_mask<W>(cur + (size_t)v * W, F);
             store_mask<W>(a.emask + (size_t)e * W, F);
-            st_entries += 1;
+            stat(2, 1);
             if (!hubent) {
                 beg = __ldg(&a.rp[v]);
                 deg = __ldg(&a.rp[v + 1]) - beg;
                 int pc = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) pc += __popc(F[k]);
-                st_arcs += (unsigned long long)deg * (unsigned long long)pc;
-                st_reached += (unsigned long long)pc;
-                st_scanned += (unsigned long long)deg;
+                stat(0, (unsigned long long)deg * (unsigned long long)pc);
+                stat(1, (unsigned long long)pc);
+                stat(3, (unsigned long long)deg);
             }
         }
         const int incl = warp_incl_scan(deg);
@@ -404,7 +410,7 @@ struct BatchKernel {
                     uint32_t p[W];
                     load_mask<W>(prev + (size_t)u * W, p);
 #pragma unroll
-                    for (int k = 0; k < W; ++k) { m[k] = Fj[k] & p[k]; st_dag += __popc(m[k]); }
+                    for (int k = 0; k < W; ++k) { m[k] = Fj[k] & p[k]; dag += __popc(m[k]); }
                 }
                 mark(0);
                 discover(u, Fj);
@@ -428,10 +434,12 @@ struct BatchKernel {
             }
         }
         flush_current();
+        stat(4, dag);
     }
 
     // One segment of a long row (forward).  g: segment index within level d.
     __device__ void fwd_hub_segment(int g) {
+        unsigned dag = 0;  // DAG (arc, source) pairs seen by this lane
         const int r = __ldcg(&a.segrec[soff_d + g]);
         if (r < hoff_d || r >= hoff_d + nrec_d) {
             if (lane == 0) set_error(ctl, kErrCorrupt);
@@ -466,7 +474,7 @@ struct BatchKernel {
                     uint32_t p[W];
                     load_mask<W>(prev + (size_t)u * W, p);
 #pragma unroll
-                    for (int k = 0; k < W; ++k) { m[k] = F[k] & p[k]; st_dag += __popc(m[k]); }
+                    for (int k = 0; k < W; ++k) { m[k] = F[k] & p[k]; dag += __popc(m[k]); }
                 }
                 mark(1);
                 discover(u, F);
@@ -482,14 +490,15 @@ struct BatchKernel {
                 mark(7);
             }
         }
-        if (lane == 0) st_scanned += (unsigned long long)(end - beg);
+        if (lane == 0) stat(3, (unsigned long long)(end - beg));
+        stat(4, dag);
         auto count_entry = [&]() {
             if (lane == 0) {
                 int pc = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) pc += __popc(F[k]);
-                st_arcs += (unsigned long long)(re - rb) * (unsigned long long)pc;
-                st_reached += (unsigned long long)pc;
+                stat(0, (unsigned long long)(re - rb) * (unsigned long long)pc);
+                stat(1, (unsigned long long)pc);
             }
         };
         if (nseg == 1) {  // the whole row in one segment: no partial sums
@@ -538,7 +547,7 @@ struct BatchKernel {
             load_mask<W>(a.emask + (size_t)e * W, F);
             beg = __ldg(&a.rp[v]);
             deg = skip_arcs ? 0 : __ldg(&a.rp[v + 1]) - beg;
-            st_scanned += (unsigned long long)deg;
+            stat(3, (unsigned long long)deg);
         }
         const int incl = warp_incl_scan(deg);
         const int excl = incl - deg;
@@ -635,7 +644,7 @@ struct BatchKernel {
             pull_window<kGSeg>(th(), w, 0, m, pend, acc, [](int) {});
             mark(7);
         }
-        if (lane == 0) st_scanned += (unsigned long long)(end - beg);
+        if (lane == 0) stat(3, (unsigned long long)(end - beg));
         if (nseg == 1) {
             delta_flush(hv, F, acc);
             return;
@@ -696,6 +705,10 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
     constexpr int B = K_t::B;
     constexpr bool kFloatSig = K_t::kFloatSig;
     K_t K(a);
+    __shared__ unsigned long long s_tstat[5 * kBatchThreads];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) s_tstat[i * kBatchThreads + threadIdx.x] = 0ull;
+    K.sst = s_tstat + threadIdx.x;
     Ctl* ctl = a.ctl;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
@@ -925,11 +938,8 @@ out:
         __shared__ unsigned long long s_st[5];
         if (threadIdx.x == 0) { s_st[0] = 0; s_st[1] = 0; s_st[2] = 0; s_st[3] = 0; s_st[4] = 0; }
         __syncthreads();
-        atomicAdd(&s_st[4], K.st_dag);
-        atomicAdd(&s_st[0], K.st_arcs);
-        atomicAdd(&s_st[1], K.st_reached);
-        atomicAdd(&s_st[2], K.st_entries);
-        atomicAdd(&s_st[3], K.st_scanned);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) atomicAdd(&s_st[i], s_tstat[i * kBatchThreads + threadIdx.x]);
         __syncthreads();
         if (threadIdx.x == 0) {
             atomicAdd(&ctl->traversed_arcs, s_st[0]);
