@@ -267,21 +267,22 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(st: dict, n: int, form: str, theta_bytes: int, width: int) -> int:
+def algorithmic_bytes(st: dict, n: int, form: str, theta_bytes: int, width: int, sigma_bytes: int = 8) -> int:
     """HBM bytes the method must move for one launch, from the launch's own counts.
 
     adjacency   4 B per scanned arc (forward + backward) + row_ptr pair per entry and pass
     masks       batched: W words per entry, read in the forward, stored, read again backward
-    DAG state   per (arc, source) on a shortest-path DAG: the parent's sigma (8 B) in the
-                forward pull and the child's theta in the backward pull
-    per (v, s)  sigma written and re-read (8 + 8 B), theta written
+    DAG state   per (arc, source) on a shortest-path DAG: the parent's sigma in the forward
+                pull and the child's theta in the backward pull
+    per (v, s)  sigma written and re-read, theta written
     BC          zeroed once (8 B per vertex), read-modify-write per entry (16 B)
+    sigma_bytes is the stored path-count width (4 for the batched form's u32 rows).
     """
     words = max(width // 32, 0)
     b = 4 * st["scanned_arcs"] + 16 * st["entries"]
     b += 3 * 4 * words * st["entries"]
-    b += st["dag_arcs"] * (8 + theta_bytes)
-    b += st["reached"] * (8 + 8 + theta_bytes)
+    b += st["dag_arcs"] * (sigma_bytes + theta_bytes)
+    b += st["reached"] * (2 * sigma_bytes + theta_bytes)
     b += 8 * n + 16 * st["entries"]
     return int(b)
 
@@ -526,7 +527,10 @@ def run_ours(args, rank, world, dist):
     s = stats[-1]
     peak, peak_kind = load_peaks()
     kernel_ms = s["kernel_ms"]
-    alg = algorithmic_bytes(s, g.n, w["form"], theta_bytes, s["batch"] if s["form"] == sp.SP_FORM_BATCHED else 0)
+    sigma_bytes = 4 if (s["form"] == sp.SP_FORM_BATCHED and not s["sigma_float"]) else 8
+    theta_bytes = 8 if s["promoted"] else theta_bytes
+    alg = algorithmic_bytes(s, g.n, w["form"], theta_bytes, s["batch"] if s["form"] == sp.SP_FORM_BATCHED else 0,
+                            sigma_bytes)
     achieved = alg / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0
     launches_per_step = s["launches"] + 3  # + graph validation (row_ptr, rows) + eccentricity BFS
     base = cpu_baseline(g, srcs, args.cpu_budget) if not args.no_cpu_baseline else None
@@ -541,7 +545,8 @@ def run_ours(args, rank, world, dist):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "u64-sigma/f32-delta/f64-bc" if prec == sp.SP_FP32_DELTA else "u64-sigma/f64",
+        "dtype": ("f64" if s["sigma_float"] else ("u32" if s["form"] == sp.SP_FORM_BATCHED else "u64")) + "-sigma/"
+                 + ("f32-delta" if prec == sp.SP_FP32_DELTA and not s["promoted"] else "f64-delta") + "/f64-bc",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "n": g.n, "arcs": g.nnz,
                    "sources": int(len(srcs)), "batch": s["batch"],

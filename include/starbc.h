@@ -176,7 +176,9 @@ typedef struct {
     int32_t batch;          /* sources per batch used (1 for the plain form) */
     int32_t form;           /* SP_FORM_PLAIN, SP_FORM_BATCHED or SP_FORM_SMALL */
     int32_t promoted;       /* 1 when FP32 dependencies left the FP32 range and the call reran with FP64 */
-    int32_t sigma_float;    /* 1 when path counts needed FP64 with per-level rescaling (above 2^64) */
+    int32_t sigma_float;    /* 1 when path counts needed FP64 with per-level rescaling (a count above
+                               2^32 in the batched form, above 2^64 in the plain form, any carry in the
+                               small form) */
     int32_t launches;       /* kernel launches of the call, including reruns and autotuning trials */
     int32_t tuned;          /* 1 when this call ran an autotuner (batch width, or the plain form's driver) */
     int32_t driver;         /* plain form: SP_DRIVER_PERSISTENT or SP_DRIVER_GRAPH; 0 for the other forms */

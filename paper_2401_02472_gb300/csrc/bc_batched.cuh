@@ -66,8 +66,6 @@ struct BatchArgs {
     int32_t* hdone;           // [2*hcap]
     void* part;               // [segcap][B] 8-byte slots
     int32_t segcap;
-    unsigned long long* smax; // [lcap] largest integer path count of each level
-    unsigned long long sig_limit;  // counts above this could overflow 64 bits in a sum of max-degree terms
     int32_t* emax;            // [lcap][B]
     int32_t* emin;            // [lcap][B]
     int32_t lcap;
@@ -117,6 +115,10 @@ struct BatchKernel {
     static constexpr int B = 32 * W;
     static constexpr bool kFloatSig = !std::is_integral<SigT>::value;
     static constexpr bool kTh32 = sizeof(ThT) == 4;
+    // Path counts: stored rows are SigT (u32 exact counts, or FP64 with a
+    // per-level exponent); sums and partial rows are 64-bit (a sum of at most
+    // 2^31 u32 counts cannot wrap, so a count past 2^32 is caught exactly).
+    using SigAcc = typename std::conditional<kFloatSig, double, unsigned long long>::type;
     // dependency accumulator: FP32 for FP32 dependencies, FP64 otherwise
     using AccT = typename std::conditional<kTh32, float, double>::type;
 
@@ -134,7 +136,6 @@ struct BatchKernel {
     int cshift[W];             // per-source shift between level d-1 and d (forward) / d and d+1 (backward)
     int my_emax[W], my_emin[W];
     bool ovf = false;
-    unsigned long long my_smax = 0;  // largest integer path count this thread stored at this level
     // Statistics live in this thread's slots of a shared-memory table (stride
     // kBatchThreads): 0 traversed (arc, source), 1 reached (vertex, source),
     // 2 entries, 3 scanned arcs, 4 DAG (arc, source) pairs.  Keeping them out
@@ -242,7 +243,7 @@ struct BatchKernel {
                 jj[i] = pend ? __ffs(pend) - 1 : -1;
                 pend &= pend - 1;
             }
-            AccType x[G][W];
+            RowT x[G][W];
             int oi[G];
             uint32_t wi[G];
 #pragma unroll
@@ -255,10 +256,10 @@ struct BatchKernel {
                 const RowT* row = base + (size_t)ui * B + lane;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
-                    x[i][k] = (AccType)0;
+                    x[i][k] = (RowT)0;
                     if ((wi[i] >> k) & 1u) {
                         const uint32_t mk = __shfl_sync(kFull, m[k], srcl);
-                        if ((mk >> lane) & 1u) x[i][k] = (AccType)__ldcg(row + k * 32);
+                        if ((mk >> lane) & 1u) x[i][k] = __ldcg(row + k * 32);
                     }
                 }
             }
@@ -268,13 +269,13 @@ struct BatchKernel {
                 on_owner(oi[i]);
 #pragma unroll
                 for (int k = 0; k < W; ++k)
-                    if ((wi[i] >> k) & 1u) acc[k] += x[i][k];
+                    if ((wi[i] >> k) & 1u) acc[k] += (AccType)x[i][k];
             }
         }
     }
 
     // Store the new path counts of entry (v, F) from the per-lane sums.
-    __device__ __forceinline__ void sigma_flush(int v, const uint32_t (&F)[W], const SigT (&acc)[W]) {
+    __device__ __forceinline__ void sigma_flush(int v, const uint32_t (&F)[W], const SigAcc (&acc)[W]) {
 #pragma unroll
         for (int k = 0; k < W; ++k) {
             if ((F[k] >> lane) & 1u) {
@@ -287,8 +288,8 @@ struct BatchKernel {
                     my_emax[k] = max(my_emax[k], e);
                     my_emin[k] = min(my_emin[k], e);
                 } else {
-                    sig()[idx] = acc[k];
-                    my_smax = acc[k] > my_smax ? acc[k] : my_smax;
+                    if (acc[k] > 0xFFFFFFFFull) set_error(ctl, kErrSigmaOverflow);
+                    sig()[idx] = (SigT)acc[k];
                 }
             }
         }
@@ -307,7 +308,7 @@ struct BatchKernel {
                     if constexpr (kFloatSig) {
                         sf = (float)sv;
                     } else {
-                        sf = u64_to_f32(sv);
+                        sf = __uint2float_rn(sv);
                     }
                     float delta = sf * acc[k];
                     if constexpr (kFloatSig) delta = (float)scale2((double)delta, -cshift[k]);
@@ -382,7 +383,7 @@ struct BatchKernel {
         const int incl = warp_incl_scan(deg);
         const int excl = incl - deg;
         const int total = __shfl_sync(kFull, incl, 31);
-        SigT acc[W];
+        SigAcc acc[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[k] = 0;
         int cur_e = -1;  // lane index of the entry whose sums are in acc
@@ -458,7 +459,7 @@ struct BatchKernel {
         const int end = min(re, beg + a.seg);
         uint32_t F[W];
         load_mask<W>(cur + (size_t)hv * W, F);
-        SigT acc[W];
+        SigAcc acc[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[k] = 0;
         for (int cb = beg; cb < end; cb += kWarp) {
@@ -506,7 +507,7 @@ struct BatchKernel {
             if (d > 0) sigma_flush(hv, F, acc);
             return;
         }
-        SigT* prow = reinterpret_cast<SigT*>(a.part) + (size_t)g * B + lane;
+        SigAcc* prow = reinterpret_cast<SigAcc*>(a.part) + (size_t)g * B + lane;
 #pragma unroll
         for (int k = 0; k < W; ++k) prow[k * 32] = acc[k];
         int old = 0;
@@ -519,11 +520,11 @@ struct BatchKernel {
         if (old != nseg - 1) return;
         __threadfence();
         // last segment: sum partial rows in segment order
-        SigT tot[W];
+        SigAcc tot[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) tot[k] = 0;
         for (int q = 0; q < nseg; ++q) {
-            const SigT* pr = reinterpret_cast<const SigT*>(a.part) + (size_t)(sb + q) * B + lane;
+            const SigAcc* pr = reinterpret_cast<const SigAcc*>(a.part) + (size_t)(sb + q) * B + lane;
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 tot[k] += __ldcg(pr + k * 32);
@@ -774,8 +775,6 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
             a.eoff[0] = 0;
             a.hoff[0] = 0;
             a.soff[0] = 0;
-            a.smax[0] = 1ull;
-            a.smax[1] = 0ull;
         }
         if constexpr (kFloatSig) {
             for (int i = tid; i < B; i += nthr) {
@@ -831,13 +830,6 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
                 a.hoff[d] = hoff_d;
                 a.soff[d] = soff_d;
                 if (d + 2 < a.lcap + 2) a.hcnt[d + 2] = 0ull;
-                if (d + 1 < a.lcap) a.smax[d + 1] = 0ull;
-            }
-            // Integer path counts: level d sums at most max-degree counts of
-            // level d-1, so they cannot overflow while level d-1 stays below
-            // the limit; past it the call reruns with FP64 counts.
-            if constexpr (!kFloatSig) {
-                if (d > 0 && tid == 0 && ld_volatile(&a.smax[d - 1]) > a.sig_limit) set_error(ctl, kErrSigmaOverflow);
             }
             // clear dense F_{d-2}
             if (d >= 2) {
@@ -850,15 +842,6 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
             }
             work(K.nseg_d, qb, qe, [&](int g) { K.fwd_hub_segment(g); }, [&](int e0, int e1) { K.fwd_chunk(e0, e1); });
             K.flush_exponents(d);
-            if constexpr (!kFloatSig) {
-                unsigned long long mx = K.my_smax;
-                for (int o = 16; o > 0; o >>= 1) {
-                    unsigned long long y = shfl_u64(kFull, mx, lane ^ o);
-                    mx = y > mx ? y : mx;
-                }
-                if (lane == 0 && mx > 0 && d < a.lcap) atomicMax(&a.smax[d], mx);
-                K.my_smax = 0;
-            }
             if (!sync()) goto out;
             const int nq = qsnap;
             hoff_d = K.hoff_next;

@@ -17,12 +17,15 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     cudaStream_t st = L.stream;
     const int t_hub = 64, seg = 256;
 
+    // path-count rows: exact u32 counts, or FP64 with per-level exponents once
+    // a count passes 2^32
     const void* fn;
     if (L.sigma_float)
         fn = L.theta_f32 ? (const void*)&batched_kernel<W, double, float> : (const void*)&batched_kernel<W, double, double>;
     else
-        fn = L.theta_f32 ? (const void*)&batched_kernel<W, unsigned long long, float>
-                         : (const void*)&batched_kernel<W, unsigned long long, double>;
+        fn = L.theta_f32 ? (const void*)&batched_kernel<W, unsigned int, float>
+                         : (const void*)&batched_kernel<W, unsigned int, double>;
+    const size_t sig_size = L.sigma_float ? 8 : 4;
     int per_sm = 0;
     SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, 0));
     if (per_sm < 1) return fail(SP_ERR_CUDA, "batched kernel cannot be resident");
@@ -47,7 +50,7 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     size_t o_seen = take(sizeof(uint32_t) * (size_t)n * W);
     size_t o_ptag = take(sizeof(int32_t) * (size_t)n);
     size_t zero_end = bytes;  // everything above starts at zero
-    size_t o_sig = take(8 * (size_t)n * B);
+    size_t o_sig = take(sig_size * (size_t)n * B);
     size_t o_th = take(th_size * (size_t)n * B);
     size_t o_ent = take(sizeof(int32_t) * (size_t)ecap);
     size_t o_emask = take(sizeof(uint32_t) * (size_t)ecap * W);
@@ -59,7 +62,6 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     size_t o_hubs = take(sizeof(HubRec) * (size_t)hcap);
     size_t o_hdone = take(sizeof(int32_t) * 2 * (size_t)hcap);
     size_t o_part = take(8 * (size_t)segcap * B);
-    size_t o_smax = take(sizeof(unsigned long long) * (size_t)lcap);
     size_t o_emax = take(sizeof(int32_t) * (size_t)lcap * B);
     size_t o_emin = take(sizeof(int32_t) * (size_t)lcap * B);
 
@@ -98,8 +100,6 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.hdone = reinterpret_cast<int32_t*>(ws + o_hdone);
     a.part = ws + o_part;
     a.segcap = (int32_t)segcap;
-    a.smax = reinterpret_cast<unsigned long long*>(ws + o_smax);
-    a.sig_limit = ~0ull / (unsigned long long)std::max(1, g->info.max_degree);
     a.emax = reinterpret_cast<int32_t*>(ws + o_emax);
     a.emin = reinterpret_cast<int32_t*>(ws + o_emin);
     a.lcap = (int32_t)lcap;
