@@ -33,7 +33,10 @@
 
 namespace sp {
 
-constexpr int kSmallThreads = 512;
+constexpr int kSmallThreads = 512;  // largest block; small graphs use 256 (below)
+#ifndef SP_SMALL_BLOCK_MAXN
+#define SP_SMALL_BLOCK_MAXN 3500
+#endif
 
 struct SmallArgs {
     const int32_t* rp;
@@ -289,7 +292,11 @@ sp_status run_small(const SmallLaunch& L, LaunchResult* result) {
     const size_t smem = small_smem_bytes(n);
     SP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSmallThreads, smem));
+    // Blocks of 256 threads when four fit an SM's shared memory (more sources
+    // side by side; a level of a graph this small rarely needs more warps),
+    // else 512.
+    const int threads = n <= SP_SMALL_BLOCK_MAXN ? 256 : kSmallThreads;
+    SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
     if (per_sm < 1) return fail(SP_ERR_TOO_LARGE, "small form cannot be resident");
     int grid = per_sm * device_sm_count(g->device);
     if (L.max_ctas > 0 && L.max_ctas < grid) grid = L.max_ctas;
@@ -327,7 +334,7 @@ sp_status run_small(const SmallLaunch& L, LaunchResult* result) {
     cudaEventCreate(&ev1);
     cudaEventRecord(ev0, st);
     void* args[] = {&a};
-    cudaError_t ce = cudaLaunchKernel(fn, dim3(grid), dim3(kSmallThreads), args, smem, st);
+    cudaError_t ce = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st);
     if (ce == cudaSuccess) {
         const int rgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count(g->device) * 8);
         small_sum_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(a.bcpart, grid, n, L.d_bc);
