@@ -47,8 +47,9 @@ WORKLOADS = {
                                   desc="RMAT scale 21, edge factor 16, 128 sources (profiling case)"),
     "rmat20_64src_batched": dict(graph="rmat20", nsrc=64, seed=12, precision="fp32_delta", form="batched",
                                  desc="RMAT scale 20, edge factor 16, 64 sources"),
-    "knn4_1m_256src_batched": dict(graph="knn4_1m", nsrc=256, seed=13, precision="fp32_delta", form="batched",
-                                   desc="2-D 4-NN graph of 10^6 uniform points, 256 sources"),
+    "knn4_1m_256src": dict(graph="knn4_1m", nsrc=256, seed=13, precision="fp32_delta", form="auto",
+                           desc="2-D 4-NN graph of 10^6 uniform points, 256 sources in one persistent launch "
+                                "(automatic form: 256 block groups of the plain form)"),
     "er2000_all": dict(graph="er2000", nsrc=2000, seed=None, precision="fp64", form="auto",
                        desc="Erdos-Renyi n=2,000 m=10,000, all 2,000 sources, exact FP64 "
                             "(automatic form: one block per source, state in shared memory)"),
@@ -268,22 +269,41 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(st: dict, n: int, form: str, theta_bytes: int, width: int, sigma_bytes: int = 8) -> int:
-    """HBM bytes the method must move for one launch, from the launch's own counts.
+    """HBM bytes this design must move for one launch, from the launch's own counts.
 
-    adjacency   4 B per scanned arc (forward + backward) + row_ptr pair per entry and pass
-    masks       batched: W words per entry, read in the forward, stored, read again backward
-    DAG state   per (arc, source) on a shortest-path DAG: the parent's sigma in the forward
-                pull and the child's theta in the backward pull
-    per (v, s)  sigma written and re-read, theta written
-    BC          zeroed once (8 B per vertex), read-modify-write per entry (16 B)
-    sigma_bytes is the stored path-count width (4 for the batched form's u32 rows).
+    Per scanned adjacency entry (forward and backward, about half each):
+      4 B column id; batched form: the neighbour's mask words read to test its
+      level (forward: previous level + seen bits, 8W B; backward: next level,
+      4W B), 6W B on average; plain form: its level (4 B).
+    Per level-stack entry: its row_ptr pair in each pass (16 B); batched: its
+      own mask read, stored and re-read (12W B) and its discovery updates
+      (seen bits + next level, 8W B); the BC read-modify-write (16 B).
+    Per (arc, source) pair on a shortest-path DAG: the parent's path count in
+      the forward pull and the child's theta in the backward pull.
+    Per reached (vertex, source): its path count written and read back, its
+      theta written.
+    Per vertex: BC zeroed (8 B).
+    sigma_bytes / theta_bytes are the stored widths (4 for u32 counts / FP32).
     """
     words = max(width // 32, 0)
-    b = 4 * st["scanned_arcs"] + 16 * st["entries"]
-    b += 3 * 4 * words * st["entries"]
+    per_arc = 4 + (6 * words if words else 4)        # mask of W words = 4W bytes
+    per_entry = 16 + 16 + (20 * words if words else 0)
+    b = per_arc * st["scanned_arcs"] + per_entry * st["entries"]
     b += st["dag_arcs"] * (sigma_bytes + theta_bytes)
     b += st["reached"] * (2 * sigma_bytes + theta_bytes)
-    b += 8 * n + 16 * st["entries"]
+    b += 8 * n
+    return int(b)
+
+
+def survey_model_bytes(st: dict, n: int, theta_bytes: int, width: int, batches: int) -> int:
+    """The reference per-unit model of the batched method (level and path count read
+    per (arc, source), 2 + 8 B forward and 2 + theta B backward, adjacency once per
+    active level and batch, ~40 B of per-(vertex, source) state per batch slot);
+    it counts bytes this design does not move (its level tests read one mask word
+    for 32 sources)."""
+    b = 4 * st["scanned_arcs"]
+    b += st["traversed_arcs"] * (2 + 8 + 2 + theta_bytes)
+    b += n * max(width, 1) * max(batches, 1) * 40
     return int(b)
 
 
@@ -532,6 +552,8 @@ def run_ours(args, rank, world, dist):
     alg = algorithmic_bytes(s, g.n, w["form"], theta_bytes, s["batch"] if s["form"] == sp.SP_FORM_BATCHED else 0,
                             sigma_bytes)
     achieved = alg / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0
+    survey_alg = survey_model_bytes(s, g.n, theta_bytes, s["batch"], s["batches"])
+    survey_achieved = survey_alg / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0
     launches_per_step = s["launches"] + 3  # + graph validation (row_ptr, rows) + eccentricity BFS
     base = cpu_baseline(g, srcs, args.cpu_budget) if not args.no_cpu_baseline else None
     line = {
@@ -560,7 +582,9 @@ def run_ours(args, rank, world, dist):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None,
                      "traffic": args.traffic if args.traffic is not None else recorded_traffic(args.workload, s["batch"]),
-                     "peak_kind": peak_kind, "kernel_ms": kernel_ms, "algorithmic_bytes": alg},
+                     "peak_kind": peak_kind, "kernel_ms": kernel_ms, "algorithmic_bytes": alg,
+                     "survey_model": {"bytes": survey_alg, "achieved": survey_achieved,
+                                      "frac": survey_achieved / peak if peak else None}},
         "cpu_baseline": base,
         "clocks": clk,
         "detail": {"traversed_arcs_per_step": arcs, "dag_arcs": s["dag_arcs"], "entries": s["entries"],
