@@ -267,16 +267,21 @@ static sp_status autotune_plain(Graph* g, const int32_t* d_src, const sp_bc_opts
     return SP_OK;
 }
 
-// Sort key of each source: (hop distance from a maximum-degree vertex, the
-// smallest neighbour one hop closer to it).  Sources with equal keys tend to
-// sit at the same BFS level for most vertices, so batching them in adjacent
-// bit positions packs the per-(vertex, source) rows the kernels gather.
+// Sort key of each source: its hop distances from three landmarks (the three
+// vertices of largest degree; distances clamped to 255), then the smallest
+// neighbour one hop closer to the first landmark.  Sources with equal
+// distances to the hubs through which most shortest paths run sit at the same
+// BFS level for most vertices, so batching them in adjacent bit positions
+// fills mask words and shares the 32-byte sectors of the per-(vertex, source)
+// rows the kernels gather.
 __global__ void source_keys_kernel(const int32_t* __restrict__ src, int32_t nsrc, const int32_t* __restrict__ rp,
                                    const int32_t* __restrict__ ci, const int32_t* __restrict__ dist,
+                                   const int32_t* __restrict__ dist2, const int32_t* __restrict__ dist3,
                                    unsigned long long* __restrict__ keys) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    auto clamp8 = [](int d) -> unsigned long long { return d < 0 || d > 255 ? 255ull : (unsigned long long)d; };
     for (int i = warp; i < nsrc; i += nwarp) {
         const int s = src[i];
         const int ds = dist[s];
@@ -288,10 +293,27 @@ __global__ void source_keys_kernel(const int32_t* __restrict__ src, int32_t nsrc
             }
         best = warp_min_i32(best);
         if (lane == 0) {
-            unsigned dk = ds < 0 ? 0xFFFFFFFFu : (unsigned)ds;
-            keys[i] = ((unsigned long long)dk << 32) | (unsigned)(best == INT_MAX ? s : best);
+            unsigned long long k = clamp8(ds) << 56;
+            if (dist2) k |= clamp8(dist2[s]) << 48 | clamp8(dist3[s]) << 40;
+            keys[i] = k | (unsigned)(best == INT_MAX ? s : best);
         }
     }
+}
+
+// The vertex of largest degree (smallest id among equals) other than a and b.
+__global__ void landmark_kernel(const int32_t* __restrict__ rp, int32_t n, int32_t a, int32_t b,
+                                unsigned long long* __restrict__ out) {
+    unsigned long long best = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (v == a || v == b) continue;
+        const unsigned long long key = ((unsigned long long)(unsigned)(rp[v + 1] - rp[v]) << 32) | (unsigned)~(unsigned)v;
+        best = key > best ? key : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = shfl_u64(kFull, best, lane_id() ^ o);
+        best = y > best ? y : best;
+    }
+    if (lane_id() == 0) atomicMax(out, best);
 }
 
 // A copy of the call's sources in key order (stable), or nullptr to keep the
@@ -328,6 +350,49 @@ static sp_status ensure_top_bfs(Graph* g, cudaStream_t st) {
     return SP_OK;
 }
 
+// Distances from the second and third landmarks (plain-form BFS, kept with
+// the graph; computed on the first batched call that regroups sources).
+static sp_status ensure_landmarks(Graph* g, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->d_land_dist || g->n < 3) return SP_OK;
+    unsigned long long* d_key = nullptr;
+    int32_t* d_two = nullptr;
+    int32_t* d_dist = nullptr;
+    SP_CUDA(cudaMallocAsync((void**)&d_key, sizeof(unsigned long long), st));
+    int32_t land[2] = {0, 0};
+    const int grid = device_sm_count(g->device) * 4;
+    for (int k = 0; k < 2; ++k) {
+        SP_CUDA(cudaMemsetAsync(d_key, 0, sizeof(unsigned long long), st));
+        landmark_kernel<<<grid, 256, 0, st>>>(g->d_rp, g->n, g->top_vertex, k == 0 ? g->top_vertex : land[0], d_key);
+        unsigned long long h = 0;
+        SP_CUDA(cudaMemcpyAsync(&h, d_key, sizeof(h), cudaMemcpyDeviceToHost, st));
+        SP_CUDA(cudaStreamSynchronize(st));
+        land[k] = (int32_t)~(unsigned)(h & 0xFFFFFFFFull);
+    }
+    cudaFreeAsync(d_key, st);
+    SP_CUDA(cudaMalloc((void**)&d_dist, sizeof(int32_t) * 2 * (size_t)g->n));
+    SP_CUDA(cudaMallocAsync((void**)&d_two, sizeof(int32_t) * 2, st));
+    SP_CUDA(cudaMemcpyAsync(d_two, land, sizeof(land), cudaMemcpyHostToDevice, st));
+    PlainLaunch L{};
+    L.g = g;
+    L.d_sources = d_two;
+    L.nsrc = 2;
+    L.d_dist = d_dist;
+    L.mode = PlainMode::BFS;
+    L.timeout_ns = bfs_timeout_ns();
+    L.stream = st;
+    LaunchResult r;
+    sp_status rc = run_plain(L, &r);
+    cudaFreeAsync(d_two, st);
+    if (rc == SP_OK) rc = map_device_error(r.err, "landmark BFS", r.diag);
+    if (rc != SP_OK) {
+        cudaFree(d_dist);
+        return rc;
+    }
+    g->d_land_dist = d_dist;
+    return SP_OK;
+}
+
 // Blocks per group of the plain form: about 8,192 arcs of an average level
 // per block, from the estimated number of levels.
 static int plain_group_blocks(const Graph* g) {
@@ -352,10 +417,16 @@ static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cud
         sp_status rc = ensure_top_bfs(g, st);
         if (rc != SP_OK) return rc;
     }
+    {
+        sp_status rc = ensure_landmarks(g, st);
+        if (rc != SP_OK) return rc;
+    }
+    const int32_t* d2 = g->d_land_dist;
+    const int32_t* d3 = d2 ? d2 + g->n : nullptr;
     unsigned long long* d_keys = nullptr;
     SP_CUDA(cudaMallocAsync((void**)&d_keys, sizeof(unsigned long long) * (size_t)nsrc, st));
     source_keys_kernel<<<std::min(1024, (nsrc + 7) / 8), 256, 0, st>>>(d_src, nsrc, g->d_rp, g->d_ci, g->d_top_dist,
-                                                                          d_keys);
+                                                                          d2, d3, d_keys);
     std::vector<unsigned long long> keys(nsrc);
     std::vector<int32_t> srcs(nsrc);
     cudaError_t e = cudaGetLastError();
@@ -756,6 +827,7 @@ sp_status sp_graph_destroy(sp_graph gh) {
     if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
     Graph* g = reinterpret_cast<Graph*>(gh);
     if (g->d_top_dist) cudaFree(g->d_top_dist);
+    if (g->d_land_dist) cudaFree(g->d_land_dist);
     destroy_step_cache(g);
     cudaFree(g->d_rp);
     cudaFree(g->d_ci);

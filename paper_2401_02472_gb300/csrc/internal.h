@@ -30,6 +30,7 @@ struct Graph {
     int32_t top_vertex = 0;     // a vertex of maximum degree
     int32_t* d_top_dist = nullptr;  // BFS distances from top_vertex (computed on first use)
     int32_t top_levels = 0;     // 1 + eccentricity of top_vertex (0 until computed)
+    int32_t* d_land_dist = nullptr;  // [2][n] BFS distances from the 2nd and 3rd largest-degree vertices
     bool theta_f64 = false;     // FP32 dependencies of this graph left the FP32 range before
     void* step_cache = nullptr; // graph-driven plain form: device state block and instantiated CUDA graphs
 };
