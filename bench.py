@@ -133,13 +133,14 @@ def run_serving(args, world):
     sub0 = times[0][0]
     lat, arcs = [], 0
     first_sub, last_done = None, 0
-    service, kernel, per_graph = [], [], {}
+    service, kernel, per_graph, shared = [], [], {}, []
     for (ta, gi, srcs), (ts, tb, td), st in zip(reqs, times, stats):
         if ta < warm:
             continue
         lat.append((td - ts) / 1e6)
         service.append((td - tb) / 1e6)
         kernel.append(st["kernel_ms"])
+        shared.append(st["shared"])
         per_graph.setdefault(gi, []).append((td - tb) / 1e6)
         arcs += st["traversed_arcs"]
         first_sub = ts if first_sub is None else min(first_sub, ts)
@@ -187,6 +188,8 @@ def run_serving(args, world):
                     # time a slot spent on a request (start to done), and the kernels' share of it
                     "service_ms_mean": float(np.mean(service)) if service else None,
                     "kernel_ms_mean": float(np.mean(kernel)) if kernel else None,
+                    # requests per launch, seen from each request (1 = ran alone)
+                    "shared_launch_mean": float(np.mean(shared)) if shared else None,
                     "service_ms_mean_per_graph": {str(k): round(float(np.mean(v)), 3) for k, v in sorted(per_graph.items())},
                     "one_at_a_time_plain": {"p50_ms": pct(base_lat, 50), "p99_ms": pct(base_lat, 99),
                                             "gteps": base_arcs / max(base_window, 1e-9) / 1e9,

@@ -183,6 +183,8 @@ typedef struct {
     int32_t tuned;          /* 1 when this call ran an autotuner (batch width, or the plain form's driver) */
     int32_t driver;         /* plain form: SP_DRIVER_PERSISTENT or SP_DRIVER_GRAPH; 0 for the other forms */
     int32_t bottom_up;      /* plain form: levels wider than n / bottom_up were discovered bottom-up; 0 = never */
+    int32_t shared;         /* serving: requests that shared this request's launch (itself included) */
+    int32_t reserved;
 } sp_bc_stats;
 
 SP_API void sp_bc_opts_default(sp_bc_opts* o);
@@ -259,7 +261,10 @@ SP_API sp_status sp_bc_wait(sp_server s, sp_request req, int64_t timeout_ns); /*
 SP_API sp_status sp_bc_cancel(sp_server s, sp_request req);
 /* Host steady-clock times in ns: submission, first batch start, completion (0 if not yet). */
 SP_API sp_status sp_request_times(sp_server s, sp_request req, int64_t* submit_ns, int64_t* start_ns, int64_t* done_ns);
-/* Statistics of a request, summed over its batches (valid once it is done). */
+/* Statistics of a request (valid once it is done).  traversed_arcs and reached
+   are the request's own; when requests shared a launch (shared > 1), entries,
+   scanned_arcs and dag_arcs are the launch's, split in proportion to
+   traversed_arcs, and kernel_ms is the launch's time. */
 SP_API sp_status sp_request_stats(sp_server s, sp_request req, sp_bc_stats* out);
 SP_API sp_status sp_server_destroy(sp_server s); /* waits for running requests */
 

@@ -43,10 +43,10 @@ class sp_bc_stats(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("batches", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("promoted", ctypes.c_int32), ("sigma_float", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("tuned", ctypes.c_int32), ("driver", ctypes.c_int32),
-                ("bottom_up", ctypes.c_int32)]
+                ("bottom_up", ctypes.c_int32), ("shared", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class sp_graph_info(ctypes.Structure):

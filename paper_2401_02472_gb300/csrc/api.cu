@@ -672,6 +672,223 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
     return SP_OK;
 }
 
+// Sum of a request's per-word partial BC vectors, in word order.
+__global__ void sum_words_kernel(const double* __restrict__ word_bc, int64_t w0, int nw, int64_t n,
+                                 double* __restrict__ out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < nw; ++k) s += word_bc[(w0 + k) * n + v];
+        out[v] = s;
+    }
+}
+
+bool request_is_batched(Graph* g, int32_t nsrc, const sp_bc_opts& o, cudaStream_t st) {
+    if (o.form == SP_FORM_BATCHED) return true;
+    if (o.form != SP_FORM_AUTO || nsrc < 2 || o.debug_flags != 0) return false;
+    bool sigma_float;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        sigma_float = g->sigma_float;
+    }
+    if (!sigma_float && (int64_t)g->n <= small_form_max_n(g->device)) return false;
+    if (ensure_top_bfs(g, st) != SP_OK) return false;
+    return g->top_levels <= 64;
+}
+
+sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts& o, cudaStream_t st) {
+    const int64_t n = g->n;
+    int64_t total = 0;
+    for (int p = 0; p < nparts; ++p) {
+        std::memset(&parts[p].stats, 0, sizeof(sp_bc_stats));
+        total += parts[p].nsrc;
+    }
+    if (n == 0 || total == 0) {
+        for (int p = 0; p < nparts; ++p)
+            if (n > 0) SP_CUDA(cudaMemsetAsync(parts[p].d_out, 0, sizeof(double) * (size_t)n, st));
+        SP_CUDA(cudaStreamSynchronize(st));
+        return SP_OK;
+    }
+    bool sigma_float, theta_f32 = o.precision == SP_FP32_DELTA;
+    {
+        const int hints = range_hints(g);
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (hints & 1) g->sigma_float = true;
+        if (hints & 2) g->theta_f64 = true;
+        if (g->theta_f64) theta_f32 = false;
+        sigma_float = g->sigma_float;
+    }
+    {
+        sp_status rc = ensure_top_bfs(g, st);
+        if (rc == SP_OK) rc = ensure_landmarks(g, st);
+        if (rc != SP_OK) return rc;
+    }
+    // Width: the one tuned for the graph, else by the launch's size.  A
+    // request's result does not depend on it (per-word partial vectors).
+    int width = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key(g, o.precision));
+        if (it != g_tuned.end()) width = it->second;
+    }
+    if (width == 0) width = total >= 128 ? 128 : default_batch_width((int32_t)total);
+    const int W = width / 32;
+
+    // Each request's sources regrouped among themselves (same keys as a
+    // single call), then laid out request after request in whole words.
+    std::vector<int32_t> all((size_t)total);
+    {
+        int64_t at = 0;
+        for (int p = 0; p < nparts; ++p) {
+            std::memcpy(all.data() + at, parts[p].h_sources, sizeof(int32_t) * (size_t)parts[p].nsrc);
+            at += parts[p].nsrc;
+        }
+    }
+    int32_t* d_all = nullptr;
+    unsigned long long* d_keys = nullptr;
+    SP_CUDA(cudaMallocAsync((void**)&d_all, sizeof(int32_t) * (size_t)total, st));
+    SP_CUDA(cudaMallocAsync((void**)&d_keys, sizeof(unsigned long long) * (size_t)total, st));
+    SP_CUDA(cudaMemcpyAsync(d_all, all.data(), sizeof(int32_t) * (size_t)total, cudaMemcpyHostToDevice, st));
+    {
+        sp_status rc = check_sources(d_all, (int32_t)total, g->n, st);
+        if (rc != SP_OK) { cudaFreeAsync(d_all, st); cudaFreeAsync(d_keys, st); return rc; }
+    }
+    const int32_t* d2 = g->d_land_dist;
+    source_keys_kernel<<<std::min<int64_t>(1024, (total + 7) / 8), 256, 0, st>>>(
+        d_all, (int32_t)total, g->d_rp, g->d_ci, g->d_top_dist, d2, d2 ? d2 + g->n : nullptr, d_keys);
+    std::vector<unsigned long long> keys((size_t)total);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned long long) * (size_t)total, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d_keys, st);
+    cudaFreeAsync(d_all, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "request source ordering");
+    std::vector<int64_t> wfirst(nparts), wcount(nparts);
+    int64_t words = 0;
+    for (int p = 0; p < nparts; ++p) {
+        wfirst[p] = words;
+        wcount[p] = (parts[p].nsrc + 31) / 32;
+        words += wcount[p];
+    }
+    const int64_t words_pad = (words + W - 1) / W * W;
+    std::vector<int32_t> lanes((size_t)words_pad * 32, -1);
+    {
+        int64_t at = 0;
+        for (int p = 0; p < nparts; ++p) {
+            const int m = parts[p].nsrc;
+            std::vector<int32_t> idx(m);
+            for (int i = 0; i < m; ++i) idx[i] = i;
+            std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return keys[at + x] < keys[at + y]; });
+            for (int i = 0; i < m; ++i) lanes[(size_t)wfirst[p] * 32 + i] = all[at + idx[i]];
+            at += m;
+        }
+    }
+    if (words_pad * 32 > INT32_MAX) return fail(SP_ERR_TOO_LARGE, "too many sources in one launch");
+    int32_t* d_lanes = nullptr;
+    double* d_wbc = nullptr;
+    unsigned long long* d_wst = nullptr;
+    struct Free {
+        std::vector<void*> p;
+        cudaStream_t s;
+        ~Free() { for (void* x : p) if (x) cudaFreeAsync(x, s); }
+    } fr{{}, st};
+    SP_CUDA(cudaMallocAsync((void**)&d_lanes, sizeof(int32_t) * lanes.size(), st));
+    fr.p.push_back(d_lanes);
+    if (cudaMallocAsync((void**)&d_wbc, sizeof(double) * (size_t)words_pad * (size_t)n, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SP_ERR_OOM, "per-word BC vectors");
+    }
+    fr.p.push_back(d_wbc);
+    SP_CUDA(cudaMallocAsync((void**)&d_wst, sizeof(unsigned long long) * 2 * (size_t)words_pad, st));
+    fr.p.push_back(d_wst);
+    SP_CUDA(cudaMemcpyAsync(d_lanes, lanes.data(), sizeof(int32_t) * lanes.size(), cudaMemcpyHostToDevice, st));
+
+    int promoted = 0, launches = 2;
+    int64_t ecap = 0, hcap = 0, lcap = 0;
+    double kernel_ms = 0.0;
+    LaunchResult r;
+    for (int attempt = 0; attempt < 16; ++attempt) {
+        SP_CUDA(cudaMemsetAsync(d_wbc, 0, sizeof(double) * (size_t)words_pad * (size_t)n, st));
+        SP_CUDA(cudaMemsetAsync(d_wst, 0, sizeof(unsigned long long) * 2 * (size_t)words_pad, st));
+        BatchedLaunch L{};
+        L.g = g;
+        L.d_sources = d_lanes;
+        L.nsrc = (int32_t)(words_pad * 32);
+        L.d_bc = nullptr;
+        L.width = width;
+        L.sigma_float = sigma_float;
+        L.theta_f32 = theta_f32;
+        L.max_ctas = o.max_ctas;
+        L.timeout_ns = timeout_of(o);
+        L.stream = st;
+        L.entry_cap = ecap;
+        L.hub_cap = hcap;
+        L.level_cap = lcap;
+        L.d_word_bc = d_wbc;
+        L.d_word_stats = d_wst;
+        r = LaunchResult{};
+        sp_status rc = run_batched(L, &r);
+        if (rc != SP_OK) return rc;
+        kernel_ms += r.kernel_ms;
+        launches += r.launches;
+        if (r.err == kErrSigmaOverflow && !sigma_float) {
+            sigma_float = true;
+            add_range_hint(g, 1);
+            std::lock_guard<std::mutex> lk(g->mu);
+            g->sigma_float = true;
+            continue;
+        }
+        if (r.err == kErrThetaRange32 && theta_f32) {
+            theta_f32 = false;
+            promoted = 1;
+            add_range_hint(g, 2);
+            std::lock_guard<std::mutex> lk(g->mu);
+            g->theta_f64 = true;
+            continue;
+        }
+        if (r.err == kErrCapEntries) { ecap = 2 * r.ecap; continue; }
+        if (r.err == kErrCapHubs) { hcap = 2 * r.hcap; continue; }
+        if (r.err == kErrCapLevels && r.lcap < n + 2) { lcap = n + 2; continue; }
+        break;
+    }
+    sp_status rc = map_device_error(r.err, "batched form (requests)", r.diag);
+    if (rc != SP_OK) return rc;
+    std::vector<unsigned long long> wst((size_t)words_pad * 2);
+    SP_CUDA(cudaMemcpyAsync(wst.data(), d_wst, sizeof(unsigned long long) * wst.size(), cudaMemcpyDeviceToHost, st));
+    const int rgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count(g->device) * 8);
+    for (int p = 0; p < nparts; ++p) {
+        sum_words_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(d_wbc, wfirst[p], (int)wcount[p], n, parts[p].d_out);
+        SP_CUDA(cudaGetLastError());
+    }
+    SP_CUDA(cudaStreamSynchronize(st));
+    // traversed and reached pairs per request from its words; the launch's
+    // other counts split in proportion to traversed pairs
+    const double all_arcs = (double)std::max<unsigned long long>(r.traversed_arcs, 1);
+    for (int p = 0; p < nparts; ++p) {
+        sp_bc_stats& st_p = parts[p].stats;
+        unsigned long long arcs = 0, reached = 0;
+        for (int64_t k = wfirst[p]; k < wfirst[p] + wcount[p]; ++k) {
+            arcs += wst[2 * k];
+            reached += wst[2 * k + 1];
+        }
+        const double share = (double)arcs / all_arcs;
+        st_p.traversed_arcs = (int64_t)arcs;
+        st_p.reached = (int64_t)reached;
+        st_p.entries = (int64_t)(share * (double)r.entries);
+        st_p.scanned_arcs = (int64_t)(share * (double)r.scanned_arcs);
+        st_p.dag_arcs = (int64_t)(share * (double)r.dag_arcs);
+        st_p.kernel_ms = kernel_ms;
+        st_p.max_levels = r.levels;
+        st_p.batches = (int32_t)(words_pad / W);
+        st_p.batch = width;
+        st_p.form = SP_FORM_BATCHED;
+        st_p.promoted = promoted || (o.precision == SP_FP32_DELTA && !theta_f32);
+        st_p.sigma_float = sigma_float ? 1 : 0;
+        st_p.launches = launches + nparts;
+    }
+    return SP_OK;
+}
+
 sp_status bc_device_entry(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
                           sp_bc_stats* stats, cudaStream_t st) {
     return bc_device(g, d_src, nsrc, o, d_bc, stats, st);

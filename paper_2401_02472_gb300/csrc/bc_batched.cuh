@@ -74,6 +74,14 @@ struct BatchArgs {
     int debug_flags;
     unsigned long long timeout_ns;
     int t_hub, seg;
+    // Request mode (serving): sources are laid out in 32-lane words, each
+    // word belonging to one request (-1 marks an empty lane); instead of one
+    // BC vector the kernel keeps one partial BC vector per word and counts
+    // traversed (arc, source) pairs and reached (vertex, source) pairs per
+    // word, so that each request's result and statistics can be assembled
+    // from its own words whatever else shares the launch.
+    double* word_bc;                 // [nsrc / 32][n], zeroed by the host; null outside request mode
+    unsigned long long* word_stats;  // [nsrc / 32][2]
 };
 
 template <int W>
@@ -126,6 +134,8 @@ struct BatchKernel {
     Ctl* ctl;
     int lane;
     int d = 0;
+    int word0 = 0;  // request mode: global index of the current batch's first word
+    unsigned long long* wst = nullptr;  // request mode: the block's per-word counts [W][2]
     int hoff_d = 0, nrec_d = 0, nseg_d = 0, hoff_next = 0;  // hub records of level d / d+1
     int soff_d = 0, soff_next = 0;                            // segments of level d / d+1
     int stamp_next = 0;
@@ -298,8 +308,10 @@ struct BatchKernel {
     // Backward: from the per-lane sums of theta over children, delta, theta(v), BC.
     __device__ __forceinline__ void delta_flush(int v, const uint32_t (&F)[W], const AccT (&acc)[W]) {
         AccT bcsum = 0;
+        AccT dk[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
+            dk[k] = 0;
             if ((F[k] >> lane) & 1u) {
                 size_t idx = (size_t)v * B + k * 32 + lane;
                 SigT sv = __ldcg(&sig()[idx]);
@@ -316,6 +328,7 @@ struct BatchKernel {
                     if (!normal_finite_f(t) || !normal_finite_f(sf)) set_error(ctl, kErrThetaRange32);
                     th()[idx] = t;
                     bcsum += delta;
+                    dk[k] = delta;
                 } else {
                     double s = (double)sv;
                     double delta = s * acc[k];
@@ -324,12 +337,40 @@ struct BatchKernel {
                     if (!normal_finite(t)) set_error(ctl, SP_ERR_RANGE);
                     th()[idx] = t;
                     bcsum += delta;
+                    dk[k] = delta;
                 }
             }
+        }
+        if (a.word_bc != nullptr) {
+            // request mode: each word's fixed-order sum into that word's vector
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (F[k] == 0u) continue;  // the entry's mask: the same in every lane
+                AccT x = dk[k];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+                if (lane == 0) {
+                    double* p = a.word_bc + (size_t)(word0 + k) * (size_t)a.n + v;
+                    *p = __ldcg(p) + (double)x;
+                }
+            }
+            return;
         }
         // fixed-order reduction over the sources of this entry
         for (int o = 16; o > 0; o >>= 1) bcsum += __shfl_xor_sync(kFull, bcsum, o);
         if (lane == 0) a.bc[v] = __ldcg(&a.bc[v]) + (double)bcsum;
+    }
+
+    // Request mode: per-word counts of traversed (arc, source) pairs and
+    // reached (vertex, source) pairs for one entry of degree deg and mask F.
+    __device__ __forceinline__ void count_words(unsigned long long deg, const uint32_t (&F)[W]) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const unsigned pc = __popc(F[k]);
+            if (pc) {
+                atomicAdd(&wst[2 * k], deg * pc);
+                atomicAdd(&wst[2 * k + 1], (unsigned long long)pc);
+            }
+        }
     }
 
     // Owner lane of window position ai: the largest j with excl_j <= ai.
@@ -378,6 +419,7 @@ struct BatchKernel {
                 stat(0, (unsigned long long)deg * (unsigned long long)pc);
                 stat(1, (unsigned long long)pc);
                 stat(3, (unsigned long long)deg);
+                if (wst != nullptr) count_words((unsigned long long)deg, F);
             }
         }
         const int incl = warp_incl_scan(deg);
@@ -500,6 +542,7 @@ struct BatchKernel {
                 for (int k = 0; k < W; ++k) pc += __popc(F[k]);
                 stat(0, (unsigned long long)(re - rb) * (unsigned long long)pc);
                 stat(1, (unsigned long long)pc);
+                if (wst != nullptr) count_words((unsigned long long)(re - rb), F);
             }
         };
         if (nseg == 1) {  // the whole row in one segment: no partial sums
@@ -710,6 +753,11 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
 #pragma unroll
     for (int i = 0; i < 5; ++i) s_tstat[i * kBatchThreads + threadIdx.x] = 0ull;
     K.sst = s_tstat + threadIdx.x;
+    __shared__ unsigned long long s_wst[2 * 8];
+    if (a.word_stats != nullptr) {
+        if (threadIdx.x < 2 * W) s_wst[threadIdx.x] = 0ull;
+        K.wst = s_wst;
+    }
     Ctl* ctl = a.ctl;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
@@ -760,7 +808,8 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
         }
     };
 
-    for (int i = tid; i < n; i += nthr) a.bc[i] = 0.0;
+    if (a.word_bc == nullptr)
+        for (int i = tid; i < n; i += nthr) a.bc[i] = 0.0;
     if (!sync()) goto out;
 
     for (int b0 = 0; b0 < a.nsrc; b0 += B) {
@@ -784,7 +833,8 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
                 a.emin[B + i] = INT_MAX;
             }
         }
-        if (tid < nb) {
+        K.word0 = b0 / 32;
+        if (tid < nb && __ldg(&a.sources[b0 + tid]) >= 0) {  // request mode leaves empty lanes (-1)
             const int s = tid;
             const int x = __ldg(&a.sources[b0 + s]);
             const uint32_t bit = 1u << (s & 31);
@@ -898,6 +948,14 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
         }
 
         K.backward = false;
+        if (a.word_stats != nullptr) {  // this batch's per-word counts
+            __syncthreads();
+            if (threadIdx.x < 2 * W) {
+                if (s_wst[threadIdx.x]) atomicAdd(&a.word_stats[2 * (size_t)K.word0 + threadIdx.x], s_wst[threadIdx.x]);
+                s_wst[threadIdx.x] = 0ull;
+            }
+            __syncthreads();
+        }
         // ---- cleanup: dense levels 0..2, seen of the sources; reset the stack ----
         for (int j = 0; j < 3 && j < L; ++j) {
             const int cb = ld_volatile(&a.eoff[j]), ce = ld_volatile(&a.eoff[j + 1]);

@@ -109,6 +109,8 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.timeout_ns = L.timeout_ns;
     a.t_hub = t_hub;
     a.seg = seg;
+    a.word_bc = L.d_word_bc;
+    a.word_stats = L.d_word_stats;
 
     void* args[] = {&a};
     cudaEvent_t ev0, ev1;

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -290,7 +291,22 @@ sp_status run_small(const SmallLaunch& L, LaunchResult* result) {
     if (n > small_form_max_n(g->device)) return fail(SP_ERR_TOO_LARGE, "graph too large for the small form");
     const void* fn = L.theta_f32 ? (const void*)&small_kernel<float> : (const void*)&small_kernel<double>;
     const size_t smem = small_smem_bytes(n);
-    SP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        // Raise the kernels' dynamic shared-memory limit once per device to
+        // the largest size any graph of this form needs (never per call:
+        // calls on other host threads may be launching with larger sizes).
+        static std::mutex mu;
+        static bool done[64] = {false};
+        std::lock_guard<std::mutex> lk(mu);
+        const int dev = g->device;
+        if (dev < 0 || dev >= 64) return fail(SP_ERR_INVALID_ARG, "device id");
+        if (!done[dev]) {
+            const int lim = (int)small_smem_bytes(small_form_max_n(dev));
+            SP_CUDA(cudaFuncSetAttribute((const void*)&small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+            SP_CUDA(cudaFuncSetAttribute((const void*)&small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+            done[dev] = true;
+        }
+    }
     int per_sm = 0;
     // Blocks of 256 threads when four fit an SM's shared memory (more sources
     // side by side; a level of a graph this small rarely needs more warps),

@@ -128,7 +128,22 @@ struct BatchedLaunch {
     int64_t entry_cap;      // level-stack capacity (entries); 0 = default estimate
     int64_t hub_cap;        // hub records; 0 = default estimate
     int64_t level_cap;      // BFS levels per batch; 0 = default (16384)
+    double* d_word_bc;                 // request mode: [nsrc/32][n] per-word partial BC (else null)
+    unsigned long long* d_word_stats;  // request mode: [nsrc/32][2]
 };
+
+// Serving: several requests on one graph in one batched launch, each
+// request's sources in 32-lane words of its own; results and traversal
+// counts are assembled per request from its words.
+struct RequestPart {
+    const int32_t* h_sources;  // host, nsrc entries
+    int32_t nsrc;
+    double* d_out;             // device [n]
+    sp_bc_stats stats;         // filled on return
+};
+sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts& o, cudaStream_t st);
+// Whether a request of nsrc sources with these options runs in the batched form.
+bool request_is_batched(Graph* g, int32_t nsrc, const sp_bc_opts& o, cudaStream_t st);
 
 sp_status run_batched(const BatchedLaunch& L, LaunchResult* result);
 template <int W>

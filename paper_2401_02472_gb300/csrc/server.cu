@@ -9,20 +9,26 @@
 //              the batched launch it will run) fits in what is left of the
 //              memory budget; otherwise it waits in arrival order.
 //   slots      `max_slots` worker threads, each with its own CUDA stream, take
-//              the oldest admitted request as soon as they are free and run
-//              it as one call: its sources are regrouped and cut into batches
-//              of the width tuned for the graph, all batches in one persistent
-//              launch.  With several slots each launch is capped to its share
-//              of the SMs, so requests that arrive while others run start at
-//              once and their launches overlap on the device.
-// A request's batches, their order and the order in which their BC is added
-// depend only on the request (and the width tuned for the graph), so its
-// result is bit-identical alone or in any mix of other requests.
+//              the oldest admitted request as soon as they are free.  With
+//              several slots each launch is capped to its share of the SMs, so
+//              requests that arrive while others run start at once and their
+//              launches overlap on the device.
+//   batching   a request the batched form serves takes along every admitted
+//              request on the same graph with the same options (up to 1,024
+//              sources in all): one persistent launch runs them together, each
+//              request's sources regrouped among themselves and laid out in
+//              32-lane words of its own.  The kernel keeps one partial BC
+//              vector per word; each request's result is the sum of its words'
+//              vectors in word order.  Other requests run alone.
+// A request's words, the order of their lanes and the order in which its BC
+// is added depend only on the request, so its result is bit-identical alone
+// or in any mix of other requests.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <memory>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -52,9 +58,12 @@ struct Request {
     size_t footprint = 0;
     sp_status status = SP_NOT_READY;
     bool admitted = false, taken = false, cancelled = false, finished = false;
+    std::string err_text;  // the worker's error description when status is an error
     int64_t t_submit = 0, t_start = 0, t_done = 0;
     sp_bc_stats stats{};
 };
+
+constexpr size_t kMergeSources = 1024;  // sources of all requests sharing one launch, at most
 
 struct Server {
     size_t budget = 0, used = 0;
@@ -91,12 +100,20 @@ struct Server {
 
     void finish_locked(const std::shared_ptr<Request>& r, sp_status st) {
         r->status = st;
+        if (st != SP_OK) r->err_text = sp_last_error();
         r->finished = true;
         r->t_done = now_ns();
         used -= r->footprint;
         admit_locked();
         cv_done.notify_all();
         cv_work.notify_all();
+    }
+
+    // Requests that can share r's launch: same graph, same options, batched.
+    static bool compatible(const Request& r, const Request& x) {
+        return x.g == r.g && !x.cancelled && x.sources.size() >= 2 && x.opts.precision == r.opts.precision &&
+               x.opts.form == r.opts.form && x.opts.flags == r.opts.flags && x.opts.max_ctas == r.opts.max_ctas &&
+               x.opts.batch == r.opts.batch && x.opts.debug_flags == 0 && r.opts.debug_flags == 0;
     }
 
     void worker(int slot) {
@@ -113,30 +130,68 @@ struct Server {
             admitted.pop_front();
             r->taken = true;
             r->t_start = now_ns();
-            const bool skip = r->cancelled;
             lk.unlock();
+            sp_bc_opts o = r->opts;
+            if (slots > 1 && o.max_ctas == 0) o.max_ctas = std::max(1, (sms * 4) / slots);
+            const bool batched = !r->cancelled && request_is_batched(r->g, (int32_t)r->sources.size(), o, st);
+            std::vector<std::shared_ptr<Request>> group{r};
+            if (batched) {
+                // continuous batching: admitted requests on the same graph join
+                // this launch, each in words of its own
+                lk.lock();
+                size_t total = r->sources.size();
+                for (auto it = admitted.begin(); it != admitted.end();) {
+                    if (compatible(*r, **it) && total + (*it)->sources.size() <= kMergeSources) {
+                        total += (*it)->sources.size();
+                        (*it)->taken = true;
+                        (*it)->t_start = now_ns();
+                        group.push_back(*it);
+                        it = admitted.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                lk.unlock();
+            }
 
-            sp_status rc = SP_OK;
-            sp_bc_stats bst{};
-            if (!skip) {
+            std::vector<sp_status> rcs(group.size(), SP_OK);
+            std::vector<sp_bc_stats> sts(group.size());
+            if (!r->cancelled && batched) {
+                std::vector<RequestPart> parts(group.size());
+                for (size_t i = 0; i < group.size(); ++i) {
+                    parts[i].h_sources = group[i]->sources.data();
+                    parts[i].nsrc = (int32_t)group[i]->sources.size();
+                    parts[i].d_out = group[i]->bc_out;
+                }
+                sp_status rc = bc_requests(r->g, parts.data(), (int)parts.size(), o, st);
+                for (size_t i = 0; i < group.size(); ++i) {
+                    rcs[i] = rc;
+                    sts[i] = parts[i].stats;
+                }
+            } else if (!r->cancelled) {
                 const int cnt = (int)r->sources.size();
                 int32_t* d_src = nullptr;
+                sp_status rc = SP_OK;
                 cudaError_t e = cudaMallocAsync((void**)&d_src, sizeof(int32_t) * cnt, st);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(d_src, r->sources.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st);
                 if (e != cudaSuccess) rc = cuda_fail(e, "server request sources");
-                if (rc == SP_OK) {
-                    sp_bc_opts o = r->opts;
-                    if (slots > 1 && o.max_ctas == 0) o.max_ctas = std::max(1, (sms * 4) / slots);
-                    rc = bc_device_entry(r->g, d_src, cnt, o, r->bc_out, &bst, st);
-                }
+                if (rc == SP_OK) rc = bc_device_entry(r->g, d_src, cnt, o, r->bc_out, &sts[0], st);
                 if (d_src) cudaFreeAsync(d_src, st);
-                cudaStreamSynchronize(st);
+                rcs[0] = rc;
             }
+            cudaStreamSynchronize(st);
 
             lk.lock();
-            if (rc == SP_OK && !skip) r->stats = bst;
-            finish_locked(r, skip ? SP_ERR_CANCELLED : rc);
+            for (size_t i = 0; i < group.size(); ++i) {
+                auto& x = group[i];
+                const bool skip = x->cancelled && i == 0;
+                if (rcs[i] == SP_OK && !skip) {
+                    x->stats = sts[i];
+                    x->stats.shared = (int32_t)group.size();
+                }
+                finish_locked(x, skip ? SP_ERR_CANCELLED : rcs[i]);
+            }
         }
         lk.unlock();
         cudaStreamSynchronize(st);
@@ -245,7 +300,9 @@ sp_status sp_bc_poll(sp_server sh, sp_request req) {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->reqs.find(req);
     if (it == s->reqs.end()) return fail(SP_ERR_INVALID_ARG, "unknown request");
-    return it->second->finished ? it->second->status : SP_NOT_READY;
+    if (!it->second->finished) return SP_NOT_READY;
+    if (it->second->status != SP_OK) set_last_error(it->second->err_text);
+    return it->second->status;
 }
 
 sp_status sp_bc_wait(sp_server sh, sp_request req, int64_t timeout_ns) {
@@ -260,6 +317,7 @@ sp_status sp_bc_wait(sp_server sh, sp_request req, int64_t timeout_ns) {
     } else if (!s->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), [&] { return r->finished; })) {
         return SP_NOT_READY;
     }
+    if (r->status != SP_OK) set_last_error(r->err_text);
     return r->status;
 }
 

@@ -107,3 +107,41 @@ def test_poll_cancel_and_empty_requests(graphs):
             sp.sp_bc_submit(s2, 5, np.array([0], np.int32), empty_out)
         finally:
             sp.sp_server_destroy(s2)
+
+
+def test_requests_on_one_graph_share_launches():
+    # Graphs too large for the shared-memory form run in the batched form;
+    # requests queued behind a long one on the same graph join one launch,
+    # each in source words of its own.  Every result matches the oracle and
+    # is bit-identical to the request served alone; traversal counts are the
+    # request's own.
+    g1, g2 = gen.rmat(15, 8, 6), gen.er(20000, 80000, 9)
+    G1, G2 = sp.Graph(g1.row_ptr, g1.col_idx), sp.Graph(g2.row_ptr, g2.col_idx)
+    gs, Gs = [g1, g2], [G1, G2]
+    sizes = [300, 5, 80, 33, 2, 64, 17, 40]
+    reqs = []
+    for i, k in enumerate(sizes):
+        gi = 0 if i % 3 != 2 else 1
+        prec = sp.SP_FP32_DELTA if i % 4 else sp.SP_FP64
+        reqs.append((gi, gen.sources(gs[gi], k, 500 + i), prec))
+    s = sp.sp_server_create(8 << 30, 1)
+    ids = [sp.sp_server_add_graph(s, G.handle) for G in Gs]
+    outs, handles = [], []
+    for gi, srcs, prec in reqs:
+        out = torch.full((Gs[gi].n,), -1.0, dtype=torch.float64, device=DEV)
+        handles.append(sp.sp_bc_submit(s, ids[gi], srcs, out, sp.make_opts(precision=prec)))
+        outs.append(out)
+    for h in handles:
+        assert sp.sp_bc_wait(s, h) == sp.SP_OK
+    stats = [sp.sp_request_stats(s, h) for h in handles]
+    sp.sp_server_destroy(s)
+    torch.cuda.synchronize()
+    assert max(st["shared"] for st in stats) > 1  # at least one launch was shared
+    for (gi, srcs, prec), out, st in zip(reqs, outs, stats):
+        got = out.cpu().numpy()
+        want, ost = oracle.bc(gs[gi], srcs)
+        assert close(got, want, RTOL[prec]), (gi, len(srcs), prec)
+        assert st["traversed_arcs"] == int(ost["arcs"].sum())
+        assert st["form"] == sp.SP_FORM_BATCHED
+        alone, _, _ = serve(Gs, [(gi, srcs, prec)], slots=1)
+        assert np.array_equal(alone[0], got), (gi, len(srcs))
