@@ -135,9 +135,11 @@ typedef struct {
     int64_t barrier_timeout_ns; /* per device-side wait; 0 = 20 s */
     int32_t debug_flags;        /* SP_DEBUG_* (tests only) */
     int32_t flags;              /* SP_BC_* */
-    int32_t bottom_up;          /* plain form: discover bottom-up on levels holding more than n / bottom_up
-                                   vertices (direction-optimising BFS); 0 = default (100 on graphs of
-                                   2^20 or more vertices, else never), -1 = never */
+    int32_t bottom_up;          /* discover bottom-up on levels holding more than n / bottom_up vertices
+                                   (direction-optimising BFS; results do not change).  Plain form: 0 =
+                                   chosen by the plain-form trial (or 100 on graphs of 2^20+ vertices),
+                                   -1 = never.  Batched form (per-source bitmaps): 0 = 100 on graphs of
+                                   2^20 or more vertices, else never; -1 = never. */
     int32_t driver;             /* plain form's level loop: SP_DRIVER_AUTO, _PERSISTENT or _GRAPH */
 } sp_bc_opts;
 

@@ -82,6 +82,7 @@ struct BatchArgs {
     // from its own words whatever else shares the launch.
     double* word_bc;                 // [nsrc / 32][n], zeroed by the host; null outside request mode
     unsigned long long* word_stats;  // [nsrc / 32][2]
+    int bu_den;  // bottom-up discovery on levels with more than n / bu_den entries (0 = never)
 };
 
 template <int W>
@@ -135,6 +136,8 @@ struct BatchKernel {
     int lane;
     int d = 0;
     int word0 = 0;  // request mode: global index of the current batch's first word
+    bool discover_on = true;  // top-down discovery by the level's entries (off on bottom-up levels)
+    uint32_t active[W];       // bits of the batch's sources (lanes with a source)
     unsigned long long* wst = nullptr;  // request mode: the block's per-word counts [W][2]
     int hoff_d = 0, nrec_d = 0, nseg_d = 0, hoff_next = 0;  // hub records of level d / d+1
     int soff_d = 0, soff_next = 0;                            // segments of level d / d+1
@@ -456,7 +459,7 @@ struct BatchKernel {
                     for (int k = 0; k < W; ++k) { m[k] = Fj[k] & p[k]; dag += __popc(m[k]); }
                 }
                 mark(0);
-                discover(u, Fj);
+                if (discover_on) discover(u, Fj);
                 mark(6);
             }
             if (d > 0) {
@@ -520,7 +523,7 @@ struct BatchKernel {
                     for (int k = 0; k < W; ++k) { m[k] = F[k] & p[k]; dag += __popc(m[k]); }
                 }
                 mark(1);
-                discover(u, F);
+                if (discover_on) discover(u, F);
                 mark(6);
             }
             if (d > 0) {
@@ -575,6 +578,74 @@ struct BatchKernel {
         }
         count_entry();
         if (d > 0) sigma_flush(hv, F, tot);
+    }
+
+    // Bottom-up discovery of level d+1 (direction-optimising BFS, Beamer et
+    // al., SC 2012, on per-source bitmaps): each vertex of a range of 32 that
+    // some source of the batch has not reached ORs the level-d masks of its
+    // neighbours into its unseen bits, stopping once every unseen bit is
+    // found; one lane owns the vertex (a warp for rows above 32 arcs), so its
+    // seen bits, its level-(d+1) mask and its level-stack entry are written
+    // without atomics.  Path counts are pulled as usual when level d+1 runs.
+    __device__ void bottom_up_range(int base) {
+        const int u = base + lane;
+        uint32_t sn[W], unseen[W], got[W];
+        uint32_t any = 0;
+        int rb = 0, deg = 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k) { sn[k] = 0u; unseen[k] = 0u; got[k] = 0u; }
+        if (u < a.n) {
+            load_mask<W>(a.seen + (size_t)u * W, sn);
+#pragma unroll
+            for (int k = 0; k < W; ++k) { unseen[k] = ~sn[k] & active[k]; any |= unseen[k]; }
+            if (any) {
+                rb = __ldg(&a.rp[u]);
+                deg = __ldg(&a.rp[u + 1]) - rb;
+            }
+        }
+        if (any && deg <= 32) {
+            for (int e = 0; e < deg; ++e) {
+                uint32_t f[W];
+                load_mask<W>(cur + (size_t)__ldg(&a.ci[rb + e]) * W, f);
+                bool done = true;
+#pragma unroll
+                for (int k = 0; k < W; ++k) { got[k] |= f[k] & unseen[k]; done &= got[k] == unseen[k]; }
+                if (done) break;
+            }
+        }
+        unsigned big = __ballot_sync(kFull, any != 0u && deg > 32);
+        while (big) {
+            const int j = __ffs(big) - 1;
+            big &= big - 1;
+            const int bj = __shfl_sync(kFull, rb, j), dj = __shfl_sync(kFull, deg, j);
+            uint32_t uns[W], g2[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) { uns[k] = __shfl_sync(kFull, unseen[k], j); g2[k] = 0u; }
+            for (int e = lane; e < dj; e += kWarp) {
+                uint32_t f[W];
+                load_mask<W>(cur + (size_t)__ldg(&a.ci[bj + e]) * W, f);
+#pragma unroll
+                for (int k = 0; k < W; ++k) g2[k] |= f[k] & uns[k];
+            }
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                for (int o = 16; o > 0; o >>= 1) g2[k] |= __shfl_xor_sync(kFull, g2[k], o);
+            if (lane == j) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) got[k] = g2[k];
+            }
+        }
+        uint32_t anyg = 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k) anyg |= got[k];
+        if (anyg) {
+            uint32_t ns[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) ns[k] = sn[k] | got[k];
+            store_mask<W>(a.seen + (size_t)u * W, ns);
+            store_mask<W>(next + (size_t)u * W, got);
+            push(u, d + 1);
+        }
     }
 
     // ---------------- backward ----------------
@@ -787,19 +858,22 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
     // level with fewer items than warps costs no atomics.
     const int nwarps = nthr / kWarp;
     const int gwarp = tid / kWarp;
-    auto work = [&](int nitems_hub, int qb, int qe, auto&& on_hub, auto&& on_chunk) {
+    auto work = [&](int nitems_hub, int qb, int qe, auto&& on_hub, auto&& on_chunk, int bu_items = 0) {
         const int c = entries_per_item(qe - qb, nwarps);
         const int nchunks = (qe - qb + c - 1) / c;
-        const int total = nitems_hub + nchunks;
+        const int total = nitems_hub + nchunks + bu_items;
         for (int item = gwarp; item < total;) {
             SP_PROF_MARK(5);
             if (item < nitems_hub) {
                 on_hub(item);
                 SP_PROF_MARK(K.d >= 0 && !K.backward ? 1 : 3);
-            } else {
+            } else if (item < nitems_hub + nchunks) {
                 const int e0 = qb + (item - nitems_hub) * c;
                 on_chunk(e0, min(e0 + c, qe));
                 SP_PROF_MARK(K.d >= 0 && !K.backward ? 0 : 2);
+            } else {
+                K.bottom_up_range((item - nitems_hub - nchunks) * kWarp);
+                SP_PROF_MARK(6);
             }
             if (nwarps >= total) break;
             int next = 0;
@@ -834,6 +908,11 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
             }
         }
         K.word0 = b0 / 32;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const int sl = k * 32 + lane;
+            K.active[k] = __ballot_sync(kFull, sl < nb && __ldg(&a.sources[b0 + sl]) >= 0);
+        }
         if (tid < nb && __ldg(&a.sources[b0 + tid]) >= 0) {  // request mode leaves empty lanes (-1)
             const int s = tid;
             const int x = __ldg(&a.sources[b0 + s]);
@@ -890,7 +969,12 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
                     zero_mask<W>(clr + (size_t)v * W);
                 }
             }
-            work(K.nseg_d, qb, qe, [&](int g) { K.fwd_hub_segment(g); }, [&](int e0, int e1) { K.fwd_chunk(e0, e1); });
+            // Direction: levels with many entries discover bottom-up.
+            const bool bu = a.bu_den > 0 && d > 0 && (int64_t)(qe - qb) * a.bu_den > (int64_t)n;
+            K.discover_on = !bu;
+            work(K.nseg_d, qb, qe, [&](int g) { K.fwd_hub_segment(g); }, [&](int e0, int e1) { K.fwd_chunk(e0, e1); },
+                 bu ? (n + kWarp - 1) / kWarp : 0);
+            K.discover_on = true;
             K.flush_exponents(d);
             if (!sync()) goto out;
             const int nq = qsnap;

@@ -110,6 +110,7 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.t_hub = t_hub;
     a.seg = seg;
     a.word_bc = L.d_word_bc;
+    a.bu_den = L.bottom_up_den;
     a.word_stats = L.d_word_stats;
 
     void* args[] = {&a};

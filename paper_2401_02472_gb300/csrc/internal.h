@@ -128,6 +128,7 @@ struct BatchedLaunch {
     int64_t entry_cap;      // level-stack capacity (entries); 0 = default estimate
     int64_t hub_cap;        // hub records; 0 = default estimate
     int64_t level_cap;      // BFS levels per batch; 0 = default (16384)
+    int bottom_up_den;                 // bottom-up discovery on levels with more than n / this entries (0 = never)
     double* d_word_bc;                 // request mode: [nsrc/32][n] per-word partial BC (else null)
     unsigned long long* d_word_stats;  // request mode: [nsrc/32][2]
 };

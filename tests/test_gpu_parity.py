@@ -330,6 +330,24 @@ def test_plain_direction_does_not_change_results(name):
     assert_bc_close(runs[0], want, 1e-9)
 
 
+@pytest.mark.parametrize("name", ["rmat12", "er2000", "knn5000", "mixed"])
+def test_batched_direction_does_not_change_results(name):
+    # Bottom-up discovery on the per-source bitmaps (levels above n/2, n/20,
+    # or never) finds the same levels, so BC is bit-identical.
+    g, G = graph(name)
+    srcs = gen.sources(g, min(100, int((g.degrees() > 0).sum())), 32)
+    runs = [gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_BATCHED, 64, bottom_up=bu)[0] for bu in (-1, 2, 20)]
+    for r in runs[1:]:
+        assert np.array_equal(r, runs[0])
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(runs[0], want, 1e-9)
+    gh, GH = hub_graph()
+    hs = np.array([0, 1, 2, 3, 4095, 17, 1000] * 5, np.int32)
+    a, _ = gpu_bc(GH, hs, sp.SP_FP32_DELTA, sp.SP_FORM_BATCHED, 128, bottom_up=-1)
+    b, _ = gpu_bc(GH, hs, sp.SP_FP32_DELTA, sp.SP_FORM_BATCHED, 128, bottom_up=3)
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
 def test_source_order_only_changes_rounding(precision):
     # The batched form regroups sources by distance from a maximum-degree
