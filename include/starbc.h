@@ -184,7 +184,8 @@ typedef struct {
     int32_t launches;       /* kernel launches of the call, including reruns and autotuning trials */
     int32_t tuned;          /* 1 when this call ran an autotuner (batch width, or the plain form's driver) */
     int32_t driver;         /* plain form: SP_DRIVER_PERSISTENT or SP_DRIVER_GRAPH; 0 for the other forms */
-    int32_t bottom_up;      /* plain form: levels wider than n / bottom_up were discovered bottom-up; 0 = never */
+    int32_t bottom_up;      /* plain and batched forms: levels wider than n / bottom_up were discovered
+                               bottom-up; 0 = never */
     int32_t shared;         /* serving: requests that shared this request's launch (itself included) */
     int32_t reserved;
 } sp_bc_stats;

@@ -161,7 +161,13 @@ size_t batched_workspace_bytes(const Graph* g, int width, bool theta_f32) {
 // Autotuned batch widths, keyed by graph signature (n, nnz, max degree) and
 // precision, so that a graph re-created from the same CSR reuses the choice.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int32_t, int64_t, int32_t, int32_t>, int> g_tuned;
+// Batched-form choices made by timing: width and bottom-up threshold (a
+// value for sp_bc_opts.bottom_up).
+struct BatchTune {
+    int width;
+    int bottom_up;
+};
+static std::map<std::tuple<int32_t, int64_t, int32_t, int32_t>, BatchTune> g_tuned;
 
 static std::tuple<int32_t, int64_t, int32_t, int32_t> tune_key(const Graph* g, int precision) {
     return std::make_tuple(g->n, g->nnz, g->info.max_degree, (int32_t)precision);
@@ -186,34 +192,47 @@ static void add_range_hint(const Graph* g, int bit) {
 static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
                            sp_bc_stats* stats, cudaStream_t st);
 
-// Time one batch at each width on the call's own first sources and keep the
-// width with the most traversed arcs per second of kernel time.
-static sp_status autotune_width(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, cudaStream_t st,
-                                int* width, int* launches) {
+// Time the batched form on the call's first min(nsrc, 256) sources at each
+// width 32 / 64 / 128 / 256 — the same sources for every width — with
+// bottom-up discovery off and at n/100 (unless the caller fixed it; graphs
+// below 2^18 vertices only off), and keep the pair with the most traversed
+// arcs per second of kernel time.
+static sp_status autotune_batched(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, cudaStream_t st,
+                                  BatchTune* out, int* launches) {
     double* scratch = nullptr;
     SP_CUDA(cudaMallocAsync((void**)&scratch, sizeof(double) * (size_t)g->n, st));
+    const int32_t sample = std::min<int32_t>(nsrc, 256);
     double best_rate = -1.0;
-    int best = default_batch_width(nsrc);
+    BatchTune best{default_batch_width(nsrc), o.bottom_up};
+    std::vector<int> bus;
+    if (o.bottom_up != 0) bus.push_back(o.bottom_up);
+    else {
+        bus.push_back(-1);
+        if (g->n >= (1 << 18)) bus.push_back(100);
+    }
     for (int w : {32, 64, 128, 256}) {
-        if (w > nsrc) break;
-        sp_bc_opts t = o;
-        t.form = SP_FORM_BATCHED;
-        t.batch = w;
-        sp_bc_stats ts;
-        sp_status rc = bc_device(g, d_src, w, t, scratch, &ts, st);
-        *launches += ts.launches;
-        if (rc != SP_OK) {
-            cudaFreeAsync(scratch, st);
-            return rc;
-        }
-        double rate = ts.kernel_ms > 0 ? (double)ts.traversed_arcs / ts.kernel_ms : 0.0;
-        if (rate > best_rate) {
-            best_rate = rate;
-            best = w;
+        if (w > sample) break;
+        for (int bu : bus) {
+            sp_bc_opts t = o;
+            t.form = SP_FORM_BATCHED;
+            t.batch = w;
+            t.bottom_up = bu;
+            sp_bc_stats ts;
+            sp_status rc = bc_device(g, d_src, sample, t, scratch, &ts, st);
+            *launches += ts.launches;
+            if (rc != SP_OK) {
+                cudaFreeAsync(scratch, st);
+                return rc;
+            }
+            const double rate = ts.kernel_ms > 0 ? (double)ts.traversed_arcs / ts.kernel_ms : 0.0;
+            if (rate > best_rate) {
+                best_rate = rate;
+                best = BatchTune{w, bu};
+            }
         }
     }
     cudaFreeAsync(scratch, st);
-    *width = best;
+    *out = best;
     return SP_OK;
 }
 
@@ -401,13 +420,14 @@ static int plain_group_blocks(const Graph* g) {
     return (int)std::min<int64_t>((per_level + 8191) / 8192, 1 << 20);
 }
 
-// Bottom-up discovery threshold of the batched form: the caller's, else n/100
-// on graphs of 2^20 or more vertices (RMAT scale 22, width 128: 328 -> 291 ms
-// per launch; RMAT scale 20: no change), else never.
+// Bottom-up discovery threshold of the batched form without a trial: the
+// caller's, else n/100 on graphs of 750,000 or more vertices (RMAT scale 22,
+// width 128: 328 -> 291 ms per launch; ER n = 10^6 / 2·10^6: -9% / -16%;
+// RMAT scale 19: +7%), else never.
 static int batched_bottom_up(const Graph* g, int32_t opt) {
     if (opt < 0) return 0;
     if (opt > 0) return opt;
-    return g->n >= (1 << 20) ? 100 : 0;
+    return g->n >= 750000 ? 100 : 0;
 }
 
 // Bottom-up discovery threshold of the plain form without a trial: levels
@@ -496,25 +516,34 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
     }
     if (form == SP_FORM_AUTO) form = (nsrc >= 2 && g->top_levels <= 64) ? SP_FORM_BATCHED : SP_FORM_PLAIN;
     int width = 1, launches = 0, tuned = 0;
+    int batch_bu = batched_bottom_up(g, o.bottom_up);
     if (form == SP_FORM_BATCHED) {
         if (o.batch > 0) {
             width = o.batch;
         } else {
             auto key = tune_key(g, o.precision);
+            bool have = false;
+            BatchTune t{};
             {
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 auto it = g_tuned.find(key);
-                if (it != g_tuned.end()) width = it->second;
+                if (it != g_tuned.end()) { t = it->second; have = true; }
             }
-            if (width == 1 && nsrc >= 128) {
-                sp_status trc = autotune_width(g, d_src, nsrc, o, st, &width, &launches);
+            if (!have && nsrc >= 128) {
+                sp_status trc = autotune_batched(g, d_src, nsrc, o, st, &t, &launches);
                 if (trc != SP_OK) return trc;
                 tuned = 1;
-                // first result wins, so that concurrent calls agree on one width
+                // first result wins, so that concurrent calls agree
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                width = g_tuned.emplace(key, width).first->second;
+                t = g_tuned.emplace(key, t).first->second;
+                have = true;
             }
-            if (width == 1) width = default_batch_width(nsrc);
+            if (have) {
+                width = t.width;
+                if (o.bottom_up == 0) batch_bu = batched_bottom_up(g, t.bottom_up);
+            } else {
+                width = default_batch_width(nsrc);
+            }
         }
     }
     int driver = 0;
@@ -611,7 +640,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             L.entry_cap = ecap;
             L.hub_cap = hcap;
             L.level_cap = lcap;
-            L.bottom_up_den = batched_bottom_up(g, o.bottom_up);
+            L.bottom_up_den = batch_bu;
             rc = run_batched(L, &r);
         }
         if (rc != SP_OK) return rc;
@@ -677,7 +706,8 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         stats->launches = launches;
         stats->tuned = tuned;
         stats->driver = form == SP_FORM_PLAIN ? driver : 0;
-        stats->bottom_up = form == SP_FORM_PLAIN ? plain_bottom_up(g, bottom_up) : 0;
+        stats->bottom_up = form == SP_FORM_PLAIN ? plain_bottom_up(g, bottom_up)
+                                                 : (form == SP_FORM_BATCHED ? batch_bu : 0);
     }
     return SP_OK;
 }
@@ -735,10 +765,14 @@ sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts
     // Width: the one tuned for the graph, else by the launch's size.  A
     // request's result does not depend on it (per-word partial vectors).
     int width = 0;
+    int batch_bu = batched_bottom_up(g, o.bottom_up);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(tune_key(g, o.precision));
-        if (it != g_tuned.end()) width = it->second;
+        if (it != g_tuned.end()) {
+            width = it->second.width;
+            if (o.bottom_up == 0) batch_bu = batched_bottom_up(g, it->second.bottom_up);
+        }
     }
     if (width == 0) width = total >= 128 ? 128 : default_batch_width((int32_t)total);
     const int W = width / 32;
@@ -836,7 +870,7 @@ sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts
         L.level_cap = lcap;
         L.d_word_bc = d_wbc;
         L.d_word_stats = d_wst;
-        L.bottom_up_den = batched_bottom_up(g, o.bottom_up);
+        L.bottom_up_den = batch_bu;
         r = LaunchResult{};
         sp_status rc = run_batched(L, &r);
         if (rc != SP_OK) return rc;
