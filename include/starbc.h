@@ -165,6 +165,12 @@ enum { SP_DRIVER_AUTO = 0, SP_DRIVER_PERSISTENT = 1, SP_DRIVER_GRAPH = 2 };
 /* debug_flags: block 0 leaves at one grid barrier without arriving, so the
    other blocks' waits run out and the call returns SP_ERR_TIMEOUT. */
 #define SP_DEBUG_SKIP_BARRIER 0x1
+/* debug_flags: the plain form keeps each vertex's per-source state in one
+   32-byte record (RECORDS) or in separate arrays (ARRAYS) whatever the size of
+   the groups' state; by default records are used when there are several
+   groups and their state is more than twice the size of L2.  Results are the same bit for bit. */
+#define SP_DEBUG_PLAIN_RECORDS 0x2
+#define SP_DEBUG_PLAIN_ARRAYS 0x4
 
 typedef struct {
     int64_t traversed_arcs; /* sum over sources s of A_s = sum of degrees of vertices reached from s */

@@ -27,6 +27,8 @@ SP_FORM_AUTO, SP_FORM_PLAIN, SP_FORM_BATCHED, SP_FORM_SMALL = 0, 1, 2, 3
 SP_DRIVER_AUTO, SP_DRIVER_PERSISTENT, SP_DRIVER_GRAPH = 0, 1, 2
 SP_GRAPH_CHECK_SYMMETRIC, SP_GRAPH_SORT_ROWS = 0x1, 0x2
 SP_DEBUG_SKIP_BARRIER = 0x1
+SP_DEBUG_PLAIN_RECORDS = 0x2
+SP_DEBUG_PLAIN_ARRAYS = 0x4
 SP_BC_KEEP_ORDER = 0x1
 
 

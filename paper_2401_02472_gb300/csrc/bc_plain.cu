@@ -11,8 +11,9 @@
 namespace sp {
 
 template <typename SigT, typename ThT>
-static const void* plain_fn() {
-    return reinterpret_cast<const void*>(&plain_kernel<SigT, ThT>);
+static const void* plain_fn(bool rec) {
+    return rec ? reinterpret_cast<const void*>(&plain_kernel<SigT, ThT, true>)
+               : reinterpret_cast<const void*>(&plain_kernel<SigT, ThT, false>);
 }
 
 sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
@@ -20,9 +21,11 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     const int64_t n = g->n;
     cudaStream_t st = L.stream;
     Tiers tiers{16, 4096, 4096};
-    const void* fn;
-    if (L.sigma_float) fn = L.theta_f32 ? plain_fn<double, float>() : plain_fn<double, double>();
-    else fn = L.theta_f32 ? plain_fn<unsigned long long, float>() : plain_fn<unsigned long long, double>();
+    auto pick = [&](bool rec) {
+        if (L.sigma_float) return L.theta_f32 ? plain_fn<double, float>(rec) : plain_fn<double, double>(rec);
+        return L.theta_f32 ? plain_fn<unsigned long long, float>(rec) : plain_fn<unsigned long long, double>(rec);
+    };
+    const void* fn = pick(false);
 
     int dev = g->device;
     int per_sm = 0;
@@ -40,12 +43,28 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     int ngroups = std::max(1, std::min(grid / gblocks, std::max(1, L.nsrc)));
     grid = ngroups * gblocks;
 
+    // Vertex records instead of arrays when several groups' state (level,
+    // path count, theta, partial BC: 28 bytes a vertex) is more than twice L2:
+    // there each access misses, and a record puts a vertex's level test and
+    // its path count or theta in one sector.
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    bool rec = ngroups > 1 && L.mode == PlainMode::BC && (double)ngroups * (double)n * 28.0 > 2.0 * (double)l2;
+    if (L.debug_flags & SP_DEBUG_PLAIN_RECORDS) rec = true;
+    if (L.debug_flags & SP_DEBUG_PLAIN_ARRAYS) rec = false;
+    if (rec) {
+        int per_sm_rec = 0;
+        SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rec, pick(true), kPlainThreads, 0));
+        if (per_sm_rec < per_sm) rec = false;  // keep the grid co-resident
+        else fn = pick(true);
+    }
+
     // Workspace: one copy of the per-source arrays per group.
     const int64_t lcap = L.level_cap > 0 ? std::min<int64_t>(L.level_cap, n + 2)
                                          : (ngroups == 1 ? n + 2 : std::min<int64_t>(n + 2, 65536));
     const int64_t hcap = g->nnz / tiers.t_hub + 2;
     const int64_t segcap = g->nnz / tiers.seg + hcap + 2;
-    const PlainLayout lay = plain_layout(n, lcap, hcap, segcap, ngroups, grid, ngroups > 1 && L.mode == PlainMode::BC);
+    const PlainLayout lay = plain_layout(n, lcap, hcap, segcap, ngroups, grid, ngroups > 1 && L.mode == PlainMode::BC, rec);
     const size_t bytes = lay.bytes;
     char* ws = nullptr;
     cudaError_t ce = cudaMallocAsync((void**)&ws, bytes, st);
@@ -90,7 +109,8 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPlainThreads), args, 0, st);
     if (ce == cudaSuccess && ngroups > 1 && L.mode == PlainMode::BC) {
         int rgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count(dev) * 8);
-        sum_group_partials_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(a.bcpart, ngroups, n, L.d_bc);
+        const double* part = rec ? reinterpret_cast<const double*>(a.lvl) + 1 : a.bcpart;
+        sum_group_partials_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(part, ngroups, n, rec ? 4 : 1, L.d_bc);
         ce = cudaGetLastError();
     }
     cudaEventRecord(ev1, st);

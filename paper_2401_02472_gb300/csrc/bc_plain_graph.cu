@@ -64,7 +64,7 @@ constexpr int kUnroll = 4;  // step launches per WHILE iteration
 static __device__ __noinline__ void step_advance(StepBlock* blk, cudaGraphConditionalHandle cond) {
     const PlainArgs& a = blk->args;
     StepState s = blk->state;
-    PlainKernel<unsigned long long, double> K(a, 0);
+    PlainKernel<unsigned long long, double, false> K(a, 0);
     GroupCtl* gc = a.gctl;
     gc->work[0] = 0u;
     s.steps += 1;
@@ -139,7 +139,7 @@ static __device__ __noinline__ void step_advance(StepBlock* blk, cudaGraphCondit
 // One forward or backward level of the current source, then the block's
 // statistics.
 template <typename SigT, typename ThT>
-static __device__ __forceinline__ void step_work(PlainKernel<SigT, ThT>& K, const StepState& ss, int n) {
+static __device__ __forceinline__ void step_work(PlainKernel<SigT, ThT, false>& K, const StepState& ss, int n) {
     constexpr bool kFloatSig = !std::is_integral<SigT>::value;
     const PlainArgs& sa = K.a;
     const int d = ss.d;
@@ -206,13 +206,13 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_step_kernel(StepBlock*
         }
         return;
     }
-    PlainKernel<SigT, ThT> K(sa, 0);
+    PlainKernel<SigT, ThT, false> K(sa, 0);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
     const int n = sa.n;
     if (ss.stage == kStageInit) {
         const int src = __ldg(&sa.sources[ss.si]);
-        for (int i = tid; i < n; i += nthr) K.lvl()[i] = (i == src) ? 0 : -1;
+        for (int i = tid; i < n; i += nthr) K.lv(i) = (i == src) ? 0 : -1;
         if (ss.si == 0)
             for (int i = tid; i < n; i += nthr) sa.bc[i] = 0.0;
         if (tid == 0) K.start_source(src);

@@ -184,7 +184,11 @@ struct SigOps<double> {
     static __device__ __forceinline__ double warp_sum(double v, bool&) { return warp_sum_f64(v); }
 };
 
-template <typename SigT, typename ThT>
+// kRec: the per-(group, vertex) state is one 32-byte record (level @0, BC
+// partial @8, path count @16, theta @24) instead of separate arrays, so that a
+// vertex's level test and its path count or theta share one DRAM sector; used
+// when the groups' state is far larger than L2 and every access is a miss.
+template <typename SigT, typename ThT, bool kRec>
 struct PlainKernel {
     const PlainArgs& a;
     Ctl* ctl;
@@ -212,9 +216,26 @@ struct PlainKernel {
           gn((size_t)g * (size_t)args.n),
           gl((size_t)g * (size_t)args.lcap), gh((size_t)g * (size_t)args.hcap) {}
 
-    __device__ __forceinline__ int32_t* lvl() const { return a.lvl + gn; }
-    __device__ __forceinline__ SigT* sig() const { return reinterpret_cast<SigT*>(a.sig) + gn; }
-    __device__ __forceinline__ ThT* th() const { return reinterpret_cast<ThT*>(reinterpret_cast<double*>(a.th) + gn); }
+    static constexpr size_t kRecInts = 8;  // 32-byte vertex record
+    __device__ __forceinline__ int32_t& lv(int v) const {
+        if constexpr (kRec) return a.lvl[(gn + (size_t)v) * kRecInts];
+        else return a.lvl[gn + (size_t)v];
+    }
+    __device__ __forceinline__ SigT& sg(int v) const {
+        if constexpr (kRec) return *reinterpret_cast<SigT*>(a.lvl + (gn + (size_t)v) * kRecInts + 4);
+        else return reinterpret_cast<SigT*>(a.sig)[gn + (size_t)v];
+    }
+    __device__ __forceinline__ ThT& tt(int v) const {
+        if constexpr (kRec) return *reinterpret_cast<ThT*>(a.lvl + (gn + (size_t)v) * kRecInts + 6);
+        else return reinterpret_cast<ThT*>(reinterpret_cast<double*>(a.th) + gn)[v];
+    }
+    // BC of v: the output itself for one group, else the group's partial
+    __device__ __forceinline__ double& bb(int v) const {
+        if constexpr (kRec) {
+            if (a.ngroups > 1) return *reinterpret_cast<double*>(a.lvl + (gn + (size_t)v) * kRecInts + 2);
+        }
+        return a.ngroups == 1 ? a.bc[v] : a.bcpart[gn + (size_t)v];
+    }
     __device__ __forceinline__ int32_t* q() const { return a.q + gn; }
     __device__ __forceinline__ int2* qrow() const { return a.qrow + gn; }
     __device__ __forceinline__ int32_t* qoff() const { return a.qoff + gl; }
@@ -226,7 +247,6 @@ struct PlainKernel {
     __device__ __forceinline__ HubRec* hubs() const { return a.hubs + gh; }
     __device__ __forceinline__ int32_t* hdone() const { return a.hdone + 2 * gh; }
     __device__ __forceinline__ double* part() const { return a.part + (size_t)grp * (size_t)a.segcap; }
-    __device__ __forceinline__ double* bcv() const { return a.ngroups == 1 ? a.bc : a.bcpart + gn; }
 
     // Level stack of a new source: src alone on level 0, sigma[src] = 1, and
     // src's hub record when its row is split into segments.  One thread.
@@ -242,7 +262,7 @@ struct PlainKernel {
         hcnt()[1] = 0ull;
         emax()[0] = 0;
         emin()[0] = 0;
-        sig()[src] = (SigT)1;
+        sg(src) = (SigT)1;
         if (du > a.t_hub) {
             int nseg = (du + a.seg - 1) / a.seg;
             if (a.hcap < 1 || nseg > a.segcap) {
@@ -273,7 +293,10 @@ struct PlainKernel {
     // A vertex claimed for level `nl`: append to the level stack (and the hub list).
     __device__ void push(int u, int nl) {
         const int rb = __ldg(&a.rp[u]);
-        int du = __ldg(&a.rp[u + 1]) - rb;
+        push_row(u, nl, rb, __ldg(&a.rp[u + 1]) - rb);
+    }
+    // The same with u's row (start rb, degree du) already loaded.
+    __device__ void push_row(int u, int nl, int rb, int du) {
         bool hub = du > a.t_hub;
         int pos = aggregated_slot(qtail);
         if (pos >= a.n) { set_error(ctl, kErrCapacity); return; }
@@ -298,25 +321,25 @@ struct PlainKernel {
     __device__ __forceinline__ SigT fwd_visit(int u, int lu) {
         SigT c = 0;
         if (lu < 0) {
-            if (discover && atomicCAS(&lvl()[u], -1, d + 1) == -1) push(u, d + 1);
+            if (discover && atomicCAS(&lv(u), -1, d + 1) == -1) push(u, d + 1);
         } else if (lu == d - 1) {
-            c = __ldcg(&sig()[u]);
+            c = __ldcg(&sg(u));
             st_dag += 1;
         }
         return c;
     }
-    __device__ __forceinline__ SigT fwd_arc(int u) { return fwd_visit(u, __ldcg(&lvl()[u])); }
+    __device__ __forceinline__ SigT fwd_arc(int u) { return fwd_visit(u, __ldcg(&lv(u))); }
 
     __device__ void fwd_finalize(int v, SigT acc, int deg) {
         st_arcs += (unsigned long long)deg;
         st_reached += 1;
         if (d == 0) return;  // sigma[src] = 1 was set by the init phase
         if constexpr (std::is_integral<SigT>::value) {  // integer path counts
-            sig()[v] = acc;
+            sg(v) = acc;
         } else {
             double val = scale2((double)acc, -cshift_prev);
             if (!normal_finite(val)) set_error(ctl, SP_ERR_RANGE);
-            sig()[v] = (SigT)val;
+            sg(v) = (SigT)val;
             int e = exp_field(val) - 1023;
             my_emax = max(my_emax, e);
             my_emin = min(my_emin, e);
@@ -324,25 +347,25 @@ struct PlainKernel {
     }
 
     __device__ __forceinline__ double bwd_arc(int w) {
-        int lw = __ldcg(&lvl()[w]);
-        return lw == d + 1 ? (double)__ldcg(&th()[w]) : 0.0;
+        int lw = __ldcg(&lv(w));
+        return lw == d + 1 ? (double)__ldcg(&tt(w)) : 0.0;
     }
 
     __device__ void bwd_finalize(int v, double acc) {
-        double sv = (double)__ldcg(&sig()[v]);
+        double sv = (double)__ldcg(&sg(v));
         double delta = sv * acc;
         if constexpr (!std::is_integral<SigT>::value) delta = scale2(delta, -cshift_cur);
         double t = (1.0 + delta) / sv;
         if constexpr (sizeof(ThT) == 4) {
             float tf = (float)t;
             if (!normal_finite_f(tf)) set_error(ctl, kErrThetaRange32);
-            th()[v] = (ThT)tf;
+            tt(v) = (ThT)tf;
         } else {
             if (!normal_finite(t)) set_error(ctl, SP_ERR_RANGE);
-            th()[v] = (ThT)t;
+            tt(v) = (ThT)t;
         }
-        double* b = bcv();
-        b[v] = __ldcg(&b[v]) + delta;
+        double& b = bb(v);
+        b = __ldcg(&b) + delta;
     }
 
     // One chunk of level-stack entries [e0, qe), at most 32.
@@ -382,17 +405,40 @@ struct PlainKernel {
 #pragma unroll
                 for (int i = 0; i < G; ++i) u[i] = k0 + i < walk ? __ldg(&a.ci[beg + k0 + i]) : -1;
 #pragma unroll
-                for (int i = 0; i < G; ++i) lu[i] = u[i] >= 0 ? __ldcg(&lvl()[u[i]]) : INT_MIN;
+                for (int i = 0; i < G; ++i) lu[i] = u[i] >= 0 ? __ldcg(&lv(u[i])) : INT_MIN;
                 if constexpr (FWD) {
+                    // parents' path counts, the claims of unvisited
+                    // neighbours, and the rows of the claimed ones are each
+                    // issued for all G arcs before any result is used
                     SigT c[G];
+                    bool claim[G];
 #pragma unroll
-                    for (int i = 0; i < G; ++i) c[i] = u[i] >= 0 ? fwd_visit(u[i], lu[i]) : (SigT)0;
+                    for (int i = 0; i < G; ++i) {
+                        c[i] = (SigT)0;
+                        claim[i] = discover && u[i] >= 0 && lu[i] < 0;
+                        if (u[i] >= 0 && lu[i] == d - 1) {
+                            c[i] = __ldcg(&sg(u[i]));
+                            st_dag += 1;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < G; ++i)
+                        if (claim[i]) claim[i] = atomicCAS(&lv(u[i]), -1, d + 1) == -1;
+                    int rb[G], re[G];
+#pragma unroll
+                    for (int i = 0; i < G; ++i) {
+                        rb[i] = claim[i] ? __ldg(&a.rp[u[i]]) : 0;
+                        re[i] = claim[i] ? __ldg(&a.rp[u[i] + 1]) : 0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < G; ++i)
+                        if (claim[i]) push_row(u[i], d + 1, rb[i], re[i] - rb[i]);
 #pragma unroll
                     for (int i = 0; i < G; ++i) sacc = SigOps<SigT>::add(sacc, c[i], ovf);
                 } else {
                     double t[G];
 #pragma unroll
-                    for (int i = 0; i < G; ++i) t[i] = lu[i] == d + 1 ? (double)__ldcg(&th()[u[i]]) : 0.0;
+                    for (int i = 0; i < G; ++i) t[i] = lu[i] == d + 1 ? (double)__ldcg(&tt(u[i])) : 0.0;
 #pragma unroll
                     for (int i = 0; i < G; ++i) tacc += t[i];
                 }
@@ -491,12 +537,12 @@ struct PlainKernel {
 #pragma unroll 1
         for (int i = 0; i < 8; ++i) {
             const int u = base + i * kWarp + lane;
-            if (u < a.n && __ldcg(&lvl()[u]) < 0) {
+            if (u < a.n && __ldcg(&lv(u)) < 0) {
                 const int b = __ldg(&a.rp[u]), e = __ldg(&a.rp[u + 1]);
                 for (int k = b; k < e; ++k) {
                     st_scanned += 1;
-                    if (__ldcg(&lvl()[__ldg(&a.ci[k])]) == d) {
-                        lvl()[u] = d + 1;
+                    if (__ldcg(&lv(__ldg(&a.ci[k]))) == d) {
+                        lv(u) = d + 1;
                         push(u, d + 1);
                         break;
                     }
@@ -538,12 +584,12 @@ struct PlainKernel {
     }
 };
 
-template <typename SigT, typename ThT>
+template <typename SigT, typename ThT, bool kRec>
 __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
     constexpr bool kFloatSig = !std::is_integral<SigT>::value;
     const int g = blockIdx.x / a.gblocks;
     if (g >= a.ngroups) return;  // the host sizes the grid to ngroups * gblocks
-    PlainKernel<SigT, ThT> K(a, g);
+    PlainKernel<SigT, ThT, kRec> K(a, g);
     __shared__ int s_qtail;
     if (a.gblocks == 1) K.qtail = &s_qtail;  // the whole group is this block
     Ctl* ctl = a.ctl;
@@ -563,15 +609,14 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
     };
 
     if (a.mode == (int)PlainMode::BC) {
-        double* b = K.bcv();
-        for (int i = tid; i < n; i += nthr) b[i] = 0.0;
+        for (int i = tid; i < n; i += nthr) K.bb(i) = 0.0;
     }
     if (!sync()) goto out;
 
     for (int si = g; si < a.nsrc; si += a.ngroups) {
         const int src = __ldg(&a.sources[si]);
         // ---- init ----
-        for (int i = tid; i < n; i += nthr) K.lvl()[i] = (i == src) ? 0 : -1;
+        for (int i = tid; i < n; i += nthr) K.lv(i) = (i == src) ? 0 : -1;
         if (tid == 0) K.start_source(src);
         if (!sync()) goto out;
 
@@ -622,7 +667,7 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
 
         if (a.mode == (int)PlainMode::BFS) {
             int* row = a.dist_out + (size_t)si * (size_t)n;
-            for (int i = tid; i < n; i += nthr) row[i] = __ldcg(&K.lvl()[i]);
+            for (int i = tid; i < n; i += nthr) row[i] = __ldcg(&K.lv(i));
             if (!sync()) goto out;
             continue;
         }
@@ -636,11 +681,11 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
             }
             if (!sync()) goto out;
             for (int i = tid; i < n; i += nthr) {
-                int l = __ldcg(&K.lvl()[i]);
+                int l = __ldcg(&K.lv(i));
                 double m = 0.0;
                 long long e2 = 0;
                 if (l >= 0) {
-                    double s = (double)__ldcg(&K.sig()[i]);
+                    double s = (double)__ldcg(&K.sg(i));
                     int e = exp_field(s) - 1023;
                     m = scale2(s, -e);
                     e2 = (long long)e + __ldcg(&K.fexp()[l]);
@@ -697,8 +742,10 @@ struct PlainLayout {
         bcpart, trace, bytes;
 };
 
+// rec: one 32-byte record per (group, vertex) at `lvl` instead of the level,
+// path-count, theta and partial-BC arrays.
 inline PlainLayout plain_layout(int64_t n, int64_t lcap, int64_t hcap, int64_t segcap, int ngroups, int grid,
-                                bool bcpart) {
+                                bool bcpart, bool rec = false) {
     PlainLayout o{};
     const size_t G = (size_t)ngroups;
     size_t bytes = 0;
@@ -706,9 +753,9 @@ inline PlainLayout plain_layout(int64_t n, int64_t lcap, int64_t hcap, int64_t s
     o.ctl = take(sizeof(Ctl));
     o.gctl = take(sizeof(GroupCtl) * G);
     o.zero_end = bytes;
-    o.lvl = take(sizeof(int32_t) * (size_t)n * G);
-    o.sig = take(8 * (size_t)n * G);
-    o.th = take(8 * (size_t)n * G);
+    o.lvl = take((rec ? 32 : sizeof(int32_t)) * (size_t)n * G);
+    o.sig = take(rec ? 0 : 8 * (size_t)n * G);
+    o.th = take(rec ? 0 : 8 * (size_t)n * G);
     o.q = take(sizeof(int32_t) * (size_t)n * G);
     o.qrow = take(sizeof(int2) * (size_t)n * G);
     o.qoff = take(sizeof(int32_t) * (size_t)lcap * G);
@@ -720,7 +767,7 @@ inline PlainLayout plain_layout(int64_t n, int64_t lcap, int64_t hcap, int64_t s
     o.hubs = take(sizeof(HubRec) * (size_t)hcap * G);
     o.hdone = take(sizeof(int32_t) * 2 * (size_t)hcap * G);
     o.part = take(sizeof(double) * (size_t)segcap * G);
-    o.bcpart = take(bcpart ? sizeof(double) * (size_t)n * G : 0);
+    o.bcpart = take(bcpart && !rec ? sizeof(double) * (size_t)n * G : 0);
     o.trace = take(sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32));
     o.bytes = bytes;
     return o;
@@ -747,12 +794,14 @@ inline void plain_bind(PlainArgs& a, char* ws, const PlainLayout& o) {
     a.trace = reinterpret_cast<int*>(ws + o.trace);
 }
 
-// Sum of the groups' partial BC vectors, in group order.
+// Sum of the groups' partial BC vectors, in group order.  Partial of group
+// gi at vertex v: part[gi * n * vstride + v * vstride] (vstride 1 for the
+// partial-BC arrays, 4 for the BC field of 32-byte vertex records).
 static __global__ void sum_group_partials_kernel(const double* __restrict__ part, int ngroups, int64_t n,
-                                                 double* __restrict__ out) {
+                                                 int vstride, double* __restrict__ out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int gi = 0; gi < ngroups; ++gi) s += part[(int64_t)gi * n + v];
+        for (int gi = 0; gi < ngroups; ++gi) s += part[((int64_t)gi * n + v) * vstride];
         out[v] = s;
     }
 }

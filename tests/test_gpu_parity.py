@@ -330,6 +330,40 @@ def test_plain_direction_does_not_change_results(name):
     assert_bc_close(runs[0], want, 1e-9)
 
 
+@pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
+@pytest.mark.parametrize("name", ["rmat12", "knn5000", "grid30x41", "mixed", "hub"])
+def test_plain_records_match_arrays(name, precision):
+    # The plain form's per-(group, vertex) state as one 32-byte record or as
+    # separate arrays: the same arithmetic in the same order, so bit-identical
+    # results, with one group and with several.
+    g, G = hub_graph() if name == "hub" else graph(name)
+    srcs = gen.sources(g, min(24, int((g.degrees() > 0).sum())), 41)
+    for blocks in (0, 1):  # max_ctas = 1: a single group
+        kw = dict(driver=sp.SP_DRIVER_PERSISTENT, max_ctas=blocks)
+        rec, st_r = gpu_bc(G, srcs, precision, sp.SP_FORM_PLAIN, debug_flags=sp.SP_DEBUG_PLAIN_RECORDS, **kw)
+        arr, st_a = gpu_bc(G, srcs, precision, sp.SP_FORM_PLAIN, debug_flags=sp.SP_DEBUG_PLAIN_ARRAYS, **kw)
+        assert np.array_equal(rec, arr), name
+        assert st_r["traversed_arcs"] == st_a["traversed_arcs"]
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(rec, want, RTOL[precision], f"{name} records")
+
+
+def test_plain_records_rescaled_counts():
+    # Records with FP64 path counts and per-level exponents (a 600 x 600 grid
+    # from three corners: counts past 2^64), one block group per source.
+    g = gen.grid(600, 600)
+    G = device_graph(g)
+    srcs = np.array([0, 599, 600 * 600 - 1], np.int32)
+    got, st = gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_PLAIN, driver=sp.SP_DRIVER_PERSISTENT,
+                     debug_flags=sp.SP_DEBUG_PLAIN_RECORDS)
+    assert st["sigma_float"] == 1
+    arr, _ = gpu_bc(G, srcs, sp.SP_FP64, sp.SP_FORM_PLAIN, driver=sp.SP_DRIVER_PERSISTENT,
+                    debug_flags=sp.SP_DEBUG_PLAIN_ARRAYS)
+    assert np.array_equal(got, arr)
+    want, _ = oracle.bc(g, srcs)
+    assert_bc_close(got, want, 1e-9, "grid600 records")
+
+
 @pytest.mark.parametrize("name", ["rmat12", "er2000", "knn5000", "mixed"])
 def test_batched_direction_does_not_change_results(name):
     # Bottom-up discovery on the per-source bitmaps (levels above n/2, n/20,
