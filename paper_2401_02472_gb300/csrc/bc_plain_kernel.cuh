@@ -416,7 +416,7 @@ struct PlainKernel {
                     for (int i = 0; i < G; ++i) {
                         c[i] = (SigT)0;
                         claim[i] = discover && u[i] >= 0 && lu[i] < 0;
-                        if (u[i] >= 0 && lu[i] == d - 1) {
+                        if (u[i] >= 0 && lu[i] >= 0 && lu[i] == d - 1) {  // a parent (none on level 0)
                             c[i] = __ldcg(&sg(u[i]));
                             st_dag += 1;
                         }

@@ -330,6 +330,27 @@ def test_plain_direction_does_not_change_results(name):
     assert_bc_close(runs[0], want, 1e-9)
 
 
+@pytest.mark.parametrize("name", ["er2000", "rmat12", "path300", "mixed"])
+def test_dag_counts_and_no_false_overflow(name):
+    # Every form counts the shortest-path DAG arcs (v, u), d(u) = d(v) + 1,
+    # exactly, and none reports a path-count overflow on graphs whose counts
+    # are small (a fresh graph object: no remembered range flags).
+    g = GRAPHS[name]()
+    G = device_graph(g)
+    srcs = gen.sources(g, min(12, int((g.degrees() > 0).sum())), 7)
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    want_dag = 0
+    for s in srcs:
+        dist = oracle.bfs(g, int(s))
+        du, dv = dist[rows], dist[g.col_idx]
+        want_dag += int(np.sum((du >= 0) & (dv == du + 1)))
+    for form in (sp.SP_FORM_PLAIN, sp.SP_FORM_BATCHED, sp.SP_FORM_SMALL):
+        _, st = gpu_bc(G, srcs, sp.SP_FP64, form, driver=sp.SP_DRIVER_PERSISTENT)
+        assert st["sigma_float"] == 0, (name, form)
+        assert st["dag_arcs"] == want_dag, (name, form, st["dag_arcs"], want_dag)
+    G.close()
+
+
 @pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
 @pytest.mark.parametrize("name", ["rmat12", "knn5000", "grid30x41", "mixed", "hub"])
 def test_plain_records_match_arrays(name, precision):
