@@ -337,6 +337,8 @@ __global__ void landmark_kernel(const int32_t* __restrict__ rp, int32_t n, int32
 
 // A copy of the call's sources in key order (stable), or nullptr to keep the
 // caller's order (a single source, or the plain form).
+static int plain_bottom_up(const Graph* g, int32_t opt);
+
 // Hop distances from a maximum-degree vertex (one plain-form BFS per graph,
 // kept with the graph): they key the source regrouping, and their largest
 // value estimates the diameter, which sizes the plain form's block groups.
@@ -356,6 +358,7 @@ static sp_status ensure_top_bfs(Graph* g, cudaStream_t st) {
     L.mode = PlainMode::BFS;
     L.timeout_ns = bfs_timeout_ns();
     L.stream = st;
+    L.bottom_up_den = plain_bottom_up(g, 0);
     LaunchResult r;
     sp_status rc = run_plain(L, &r);
     cudaFreeAsync(d_one, st);
@@ -400,6 +403,7 @@ static sp_status ensure_landmarks(Graph* g, cudaStream_t st) {
     L.mode = PlainMode::BFS;
     L.timeout_ns = bfs_timeout_ns();
     L.stream = st;
+    L.bottom_up_den = plain_bottom_up(g, 0);
     LaunchResult r;
     sp_status rc = run_plain(L, &r);
     cudaFreeAsync(d_two, st);
