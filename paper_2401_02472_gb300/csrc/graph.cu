@@ -49,29 +49,51 @@ __global__ void rowptr_kernel(const int32_t* __restrict__ rp, int32_t n, int64_t
     }
 }
 
-// One warp per row: ids in range, strict order, self-loops, repeats.
+// Ids in range, strict order, self-loops, repeats.  A warp takes 32
+// consecutive rows: a lane walks its own row when it has at most 32 arcs
+// (most rows of sparse graphs), the whole warp walks each longer row.
 __global__ void rows_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
                             ValidateOut* out) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
-    for (int v = warp; v < n; v += nwarp) {
-        int a = rp[v], b = rp[v + 1];
-        bool unsorted = false, loop = false, dup = false;
-        for (int e = a + lane; e < b; e += 32) {
-            int c = ci[e];
-            if (c < 0 || c >= n) { atomicMin(&out->bad_col, e); continue; }
-            loop |= c == v;
-            if (e + 1 < b) {
-                int c2 = ci[e + 1];
-                unsorted |= c2 <= c;
-                dup |= c2 == c;
+    bool unsorted = false, loop = false, dup = false;
+    for (int64_t v0 = (int64_t)warp * 32; v0 < n; v0 += (int64_t)nwarp * 32) {
+        const int v = (int)(v0 + lane);
+        int a = 0, b = 0;
+        if (v < n) { a = rp[v]; b = rp[v + 1]; }
+        const bool mine = b - a <= 32;
+        if (v < n && mine) {
+            int prev = INT_MIN;
+            for (int e = a; e < b; ++e) {
+                const int c = ci[e];
+                if (c < 0 || c >= n) { atomicMin(&out->bad_col, e); prev = INT_MIN; continue; }
+                loop |= c == v;
+                if (prev != INT_MIN) { unsorted |= c <= prev; dup |= c == prev; }
+                prev = c;
             }
         }
-        if (__any_sync(kFull, unsorted) && lane == 0) out->unsorted = 1;
-        if (__any_sync(kFull, loop) && lane == 0) out->self_loops = 1;
-        if (__any_sync(kFull, dup) && lane == 0) out->duplicates = 1;
+        unsigned big = __ballot_sync(kFull, v < n && !mine);
+        while (big) {
+            const int j = __ffs(big) - 1;
+            big &= big - 1;
+            const int vj = (int)(v0 + j);
+            const int aj = __shfl_sync(kFull, a, j), bj = __shfl_sync(kFull, b, j);
+            for (int e = aj + lane; e < bj; e += 32) {
+                const int c = ci[e];
+                if (c < 0 || c >= n) { atomicMin(&out->bad_col, e); continue; }
+                loop |= c == vj;
+                if (e + 1 < bj) {
+                    const int c2 = ci[e + 1];
+                    unsorted |= c2 <= c;
+                    dup |= c2 == c;
+                }
+            }
+        }
     }
+    if (__any_sync(kFull, unsorted) && lane == 0) out->unsorted = 1;
+    if (__any_sync(kFull, loop) && lane == 0) out->self_loops = 1;
+    if (__any_sync(kFull, dup) && lane == 0) out->duplicates = 1;
 }
 
 // One warp per row: every arc (v, c) must have its reverse (c, v); rows sorted.
