@@ -79,14 +79,26 @@ __global__ void rows_kernel(const int32_t* __restrict__ rp, const int32_t* __res
             big &= big - 1;
             const int vj = (int)(v0 + j);
             const int aj = __shfl_sync(kFull, a, j), bj = __shfl_sync(kFull, b, j);
-            for (int e = aj + lane; e < bj; e += 32) {
-                const int c = ci[e];
-                if (c < 0 || c >= n) { atomicMin(&out->bad_col, e); continue; }
-                loop |= c == vj;
-                if (e + 1 < bj) {
-                    const int c2 = ci[e + 1];
-                    unsorted |= c2 <= c;
-                    dup |= c2 == c;
+            // eight coalesced loads per lane in flight: a hub row of 10^5
+            // arcs is not a chain of 3,000 dependent loads
+            for (int e0 = aj; e0 < bj; e0 += 8 * 32) {
+                int c[8], c2[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int e = e0 + k * 32 + lane;
+                    c[k] = e < bj ? ci[e] : 0;
+                    c2[k] = e + 1 < bj ? ci[e + 1] : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int e = e0 + k * 32 + lane;
+                    if (e >= bj) continue;
+                    if (c[k] < 0 || c[k] >= n) { atomicMin(&out->bad_col, e); continue; }
+                    loop |= c[k] == vj;
+                    if (e + 1 < bj) {
+                        unsorted |= c2[k] <= c[k];
+                        dup |= c2[k] == c[k];
+                    }
                 }
             }
         }
