@@ -301,12 +301,12 @@ def algorithmic_bytes(st: dict, n: int, form: str, theta_bytes: int, width: int,
     return int(b)
 
 
-def survey_model_bytes(st: dict, n: int, theta_bytes: int, width: int, batches: int) -> int:
-    """The reference per-unit model of the batched method (level and path count read
-    per (arc, source), 2 + 8 B forward and 2 + theta B backward, adjacency once per
-    active level and batch, ~40 B of per-(vertex, source) state per batch slot);
-    it counts bytes this design does not move (its level tests read one mask word
-    for 32 sources)."""
+def pair_model_bytes(st: dict, n: int, theta_bytes: int, width: int, batches: int) -> int:
+    """A per-(arc, source) model of the batched method (a 2-byte level and an 8-byte
+    path count read per traversed (arc, source) forward, level and theta backward,
+    adjacency once per active level and batch, ~40 B of per-(vertex, source) state
+    per batch slot); it counts bytes this design does not move (its level tests
+    read one mask word for 32 sources)."""
     b = 4 * st["scanned_arcs"]
     b += st["traversed_arcs"] * (2 + 8 + 2 + theta_bytes)
     b += n * max(width, 1) * max(batches, 1) * 40
@@ -578,8 +578,8 @@ def run_ours(args, rank, world, dist):
     alg = algorithmic_bytes(s, g.n, w["form"], theta_bytes, s["batch"] if s["form"] == sp.SP_FORM_BATCHED else 0,
                             sigma_bytes)
     achieved = alg / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0
-    survey_alg = survey_model_bytes(s, g.n, theta_bytes, s["batch"], s["batches"])
-    survey_achieved = survey_alg / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0
+    pair_alg = pair_model_bytes(s, g.n, theta_bytes, s["batch"], s["batches"])
+    pair_achieved = pair_alg / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0
     launches_per_step = s["launches"]
     base = cpu_baseline(g, srcs, args.cpu_budget) if not args.no_cpu_baseline else None
     line = {
@@ -610,8 +610,8 @@ def run_ours(args, rank, world, dist):
                      "frac": achieved / peak if peak else None,
                      "traffic": args.traffic if args.traffic is not None else recorded_traffic(args.workload, s["batch"]),
                      "peak_kind": peak_kind, "kernel_ms": kernel_ms, "algorithmic_bytes": alg,
-                     "survey_model": {"bytes": survey_alg, "achieved": survey_achieved,
-                                      "frac": survey_achieved / peak if peak else None}},
+                     "pair_model": {"bytes": pair_alg, "achieved": pair_achieved,
+                                      "frac": pair_achieved / peak if peak else None}},
         "cpu_baseline": base,
         "clocks": clk,
         "detail": {"traversed_arcs_per_step": arcs, "dag_arcs": s["dag_arcs"], "entries": s["entries"],
