@@ -9,10 +9,11 @@
 //              the batched launch it will run) fits in what is left of the
 //              memory budget; otherwise it waits in arrival order.
 //   slots      `max_slots` worker threads, each with its own CUDA stream, take
-//              the oldest admitted request as soon as they are free.  With
-//              several slots each launch is capped to its share of the SMs, so
-//              requests that arrive while others run start at once and their
-//              launches overlap on the device.
+//              the oldest admitted request as soon as they are free; their
+//              launches are sized for the whole GPU and overlap on the device
+//              as SMs free up.  (Capping each slot's grid to its share of the
+//              SMs made every launch slower than its share: 57 against 74
+//              GTEPS at 200 requests/s with two slots.)
 //   batching   a request the batched form serves takes along every admitted
 //              request on the same graph with the same options (up to 1,024
 //              sources in all): one persistent launch runs them together, each
@@ -121,7 +122,6 @@ struct Server {
         cudaSetDevice(device);
         cudaStream_t st;
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        const int sms = device_sm_count(device);
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
             cv_work.wait(lk, [&] { return stopping || !admitted.empty(); });
@@ -132,7 +132,7 @@ struct Server {
             r->t_start = now_ns();
             lk.unlock();
             sp_bc_opts o = r->opts;
-            if (slots > 1 && o.max_ctas == 0) o.max_ctas = std::max(1, (sms * 4) / slots);
+
             const bool batched = !r->cancelled && request_is_batched(r->g, (int32_t)r->sources.size(), o, st);
             std::vector<std::shared_ptr<Request>> group{r};
             if (batched) {
