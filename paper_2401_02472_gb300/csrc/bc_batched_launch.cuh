@@ -66,7 +66,7 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     size_t o_emin = take(sizeof(int32_t) * (size_t)lcap * B);
 
     char* ws = nullptr;
-    if (cudaMallocAsync((void**)&ws, bytes, st) != cudaSuccess) {
+    if (workspace_alloc((void**)&ws, bytes, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(SP_ERR_OOM, "workspace allocation (batched form, " + std::to_string(bytes >> 20) + " MiB)");
     }

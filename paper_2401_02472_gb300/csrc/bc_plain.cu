@@ -67,7 +67,7 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     const PlainLayout lay = plain_layout(n, lcap, hcap, segcap, ngroups, grid, ngroups > 1 && L.mode == PlainMode::BC, rec);
     const size_t bytes = lay.bytes;
     char* ws = nullptr;
-    cudaError_t ce = cudaMallocAsync((void**)&ws, bytes, st);
+    cudaError_t ce = workspace_alloc((void**)&ws, bytes, st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return fail(SP_ERR_OOM, "workspace allocation (plain form, " + std::to_string(bytes >> 20) + " MiB)");

@@ -324,7 +324,7 @@ sp_status run_small(const SmallLaunch& L, LaunchResult* result) {
     const size_t o_part = take(sizeof(double) * (size_t)n * grid);
     const size_t o_qoff = take(sizeof(int32_t) * (size_t)(n + 2) * grid);
     char* ws = nullptr;
-    if (cudaMallocAsync((void**)&ws, bytes, st) != cudaSuccess) {
+    if (workspace_alloc((void**)&ws, bytes, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(SP_ERR_OOM, "workspace allocation (small form)");
     }

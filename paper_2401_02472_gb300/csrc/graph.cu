@@ -5,6 +5,7 @@
 // host-device transfer optimisation of Section 4.1).  Here the copy is checked
 // on the device before any traversal uses it.
 #include <climits>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -128,6 +129,48 @@ __global__ void symmetric_kernel(const int32_t* __restrict__ rp, const int32_t* 
         }
         if (__any_sync(kFull, miss) && lane == 0) out->asymmetric = 1;
     }
+}
+
+// Launch workspaces come from a memory pool of the library's own that keeps
+// freed memory (release threshold: unlimited), so that a call does not map
+// gigabytes of fresh memory because an earlier call's workspace went back to
+// the device between them.  A failed allocation trims the pool and retries.
+cudaError_t workspace_alloc(void** p, size_t bytes, cudaStream_t st) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    static bool failed[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev] && !failed[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if (cudaMemPoolCreate(&pools[dev], &props) == cudaSuccess) {
+                uint64_t keep = ~0ull;
+                cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+            } else {
+                cudaGetLastError();
+                pools[dev] = nullptr;
+                failed[dev] = true;
+            }
+        }
+        pool = pools[dev];
+    }
+    if (!pool) return cudaMallocAsync(p, bytes, st);
+    e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        cudaStreamSynchronize(st);
+        cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+    }
+    return e;
 }
 
 int device_sm_count(int device) {

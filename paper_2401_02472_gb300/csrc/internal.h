@@ -160,6 +160,9 @@ sp_status csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, 
 sp_status validate_graph(Graph* g, uint32_t flags, cudaStream_t stream, std::string* detail);
 
 int device_sm_count(int device);
+// Stream-ordered allocation of a launch workspace from the library's pool
+// (freed with cudaFreeAsync like any stream-ordered allocation).
+cudaError_t workspace_alloc(void** p, size_t bytes, cudaStream_t st);
 int default_batch_width(int32_t nsrc);
 size_t batched_workspace_bytes(const Graph* g, int width, bool theta_f32);
 
