@@ -27,6 +27,12 @@
  * complete, in host or device memory alike: the level loop runs inside
  * persistent kernels whose error word the host reads at the end of the call.
  *
+ * Device memory: a graph owns its CSR copy until sp_graph_destroy.  Each BC
+ * call takes its workspace (per-source state, level stack) from a memory pool
+ * of the library's own, stream-ordered on `stream`, and returns it at the end
+ * of the call; the pool keeps freed memory for later calls (a failed
+ * allocation releases it and retries once).
+ *
  * Errors: every entry point returns an sp_status.  Argument errors, allocation
  * failures, CUDA errors and errors found by the GPU (a path count out of
  * range, a device-side wait that timed out) are returned by the call that met
