@@ -6,10 +6,14 @@ The oracle cannot run every source of the large workloads in test time, so:
                                   call against the invariant sum_v BC(v) =
                                   sum over reached ordered pairs (d - 1) with
                                   distances from the oracle's BFS;
-  RMAT scale 22, 1,024 sources:   4 sources against the oracle in FP32 and
-                                  FP64 at width 256, and the full autotuned
+  RMAT scale 22, 1,024 sources:   the first 32 sources, as a call of their
+                                  own, against the oracle in FP64 and FP32
+                                  (widths 32 and 256), and the full autotuned
                                   call against the sum of two half calls.
 """
+from concurrent.futures import ThreadPoolExecutor
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -72,10 +76,16 @@ def test_rmat22_sampled_sources_and_split_linearity():
     g = gen.workload_graph("rmat22")
     srcs = gen.sources(g, 1024, 14)
     G = sp.Graph(g.row_ptr, g.col_idx)
-    want, _ = oracle.bc(g, srcs[:4])
-    for prec, rtol in [(sp.SP_FP32_DELTA, 1e-4), (sp.SP_FP64, 1e-9)]:
-        got, _ = gpu_bc(G, srcs[:4], prec, sp.SP_FORM_BATCHED, 256)
-        assert_close(got, want, rtol, f"rmat22 4 sources precision {prec}")
+    # the oracle over the first 32 sources, one slice per host thread (BC is a
+    # sum over sources; the slices differ from one pass by rounding only)
+    spot = srcs[:32]
+    parts = np.array_split(spot, min(len(spot), os.cpu_count() or 1))
+    with ThreadPoolExecutor(len(parts)) as ex:
+        want = sum(ex.map(lambda p: oracle.bc(g, p)[0], parts))
+    for prec, rtol in [(sp.SP_FP64, 1e-9), (sp.SP_FP32_DELTA, 1e-4)]:
+        for width in (32, 256):
+            got, _ = gpu_bc(G, spot, prec, sp.SP_FORM_BATCHED, width)
+            assert_close(got, want, rtol, f"rmat22 32 sources precision {prec} width {width}")
     full, st = gpu_bc(G, srcs, sp.SP_FP32_DELTA)
     a, _ = gpu_bc(G, srcs[:512], sp.SP_FP32_DELTA, sp.SP_FORM_BATCHED, st["batch"])
     b, _ = gpu_bc(G, srcs[512:], sp.SP_FP32_DELTA, sp.SP_FORM_BATCHED, st["batch"])
