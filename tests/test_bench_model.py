@@ -30,28 +30,34 @@ def test_pair_model_worked_example():
 def _fake_tree(root):
     csrc = root / "paper_2401_02472_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    for name, text in [("a.cu", "kernel a"), ("b.cuh", "kernel b"), ("c.h", "header"),
+    for name, text in [("bc_batched.cuh", "batched kernel"), ("bc_batched_w4.cu", "width 4"),
+                       ("api.cu", "launch and tuners"), ("common.cuh", "shared device code"),
+                       ("internal.h", "declarations"), ("graph.cu", "validation, workspace"),
+                       ("bc_plain_kernel.cuh", "plain form"), ("bc_small.cu", "small form"),
                        ("server.cu", "serving loop"), ("notes.txt", "not a source")]:
         (csrc / name).write_text(text)
     return csrc
 
 
 def test_source_hash_follows_the_measured_path(tmp_path, monkeypatch):
+    # The recorded traffic is the batched kernel's: its sources and the host
+    # code that shapes its launch enter the hash, the other forms, the
+    # serving loop and non-source files do not.
     csrc = _fake_tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h0 = bench.kernel_source_hash()
-    # the serving loop and non-source files do not enter the hash
-    (csrc / "server.cu").write_text("serving loop, edited")
-    (csrc / "notes.txt").write_text("edited")
+    for name in ("bc_plain_kernel.cuh", "bc_small.cu", "server.cu", "notes.txt"):
+        (csrc / name).write_text("edited")
     assert bench.kernel_source_hash() == h0
-    # any kernel, header or launch source does
-    for name in ("a.cu", "b.cuh", "c.h"):
+    for name in ("bc_batched.cuh", "bc_batched_w4.cu", "api.cu", "common.cuh", "internal.h", "graph.cu"):
         saved = (csrc / name).read_text()
         (csrc / name).write_text(saved + " ")
         assert bench.kernel_source_hash() != h0, name
         (csrc / name).write_text(saved)
         assert bench.kernel_source_hash() == h0
-    # a renamed file changes it too
-    shutil.move(str(csrc / "a.cu"), str(csrc / "a2.cu"))
+    # a new batched-path file changes it too
+    (csrc / "bc_batched_w16.cu").write_text("width 16")
     assert bench.kernel_source_hash() != h0
-    assert os.path.exists(csrc / "a2.cu")
+    os.remove(csrc / "bc_batched_w16.cu")
+    shutil.copy(str(csrc / "notes.txt"), str(csrc / "notes2.txt"))
+    assert bench.kernel_source_hash() == h0
