@@ -207,6 +207,7 @@ extern "C" sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_id
     a.t_hub = kTHub;
     a.seg = kSeg;
     a.bu_den = 0;
+    a.centre_bound = 512;
     a.trace = nullptr;
 
     // Exact 64-bit path counts first; FP64 counts with per-level rescaling

@@ -99,6 +99,7 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     a.t_hub = tiers.t_hub;
     a.seg = tiers.seg;
     a.bu_den = L.bottom_up_den;
+    a.centre_bound = L.sigma_float && L.theta_f32 && L.mode == PlainMode::BC ? 64 : 512;
     cudaMemsetAsync(a.trace, 0, sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32), st);
 
     void* args[] = {&a};

@@ -151,7 +151,7 @@ static __device__ __forceinline__ void step_work(PlainKernel<SigT, ThT, false>& 
         K.hoff_d = ss.hoff_d;
         K.hoff_next = K.hoff_d + K.nrec_d;
         if constexpr (kFloatSig) {
-            K.cshift_prev = d > 0 ? centre_shift(ld_volatile(&K.emax()[d - 1]), ld_volatile(&K.emin()[d - 1])) : 0;
+            K.cshift_prev = d > 0 ? K.shift_of(ld_volatile(&K.emax()[d - 1]), ld_volatile(&K.emin()[d - 1])) : 0;
         }
         K.discover = !ss.bu;
         K.template level_work<true>(0, ss.qb, ss.qe, false, ss.bu ? (n + 8 * kWarp - 1) / (8 * kWarp) : 0);
@@ -167,7 +167,7 @@ static __device__ __forceinline__ void step_work(PlainKernel<SigT, ThT, false>& 
         const int qbd = ld_volatile(&K.qoff()[d]);
         const int qed = ld_volatile(&K.qoff()[d + 1]);
         K.hoff_d = ld_volatile(&K.hoff()[d]);
-        if constexpr (kFloatSig) K.cshift_cur = centre_shift(ld_volatile(&K.emax()[d]), ld_volatile(&K.emin()[d]));
+        if constexpr (kFloatSig) K.cshift_cur = K.shift_of(ld_volatile(&K.emax()[d]), ld_volatile(&K.emin()[d]));
         K.template level_work<false>(0, qbd, qed, d == ss.L - 1);
     }
     // statistics: block sums, one atomic per block and counter
@@ -349,6 +349,7 @@ sp_status run_plain_graph(const PlainLaunch& L, LaunchResult* result) {
     a.t_hub = tiers.t_hub;
     a.seg = tiers.seg;
     a.bu_den = L.bottom_up_den;
+    a.centre_bound = L.sigma_float && L.theta_f32 ? 64 : 512;
     a.trace = nullptr;
     hb.state.stage = kStageInit;
     hb.state.step_limit = (long long)L.nsrc * (2 * n + 2) + 2;

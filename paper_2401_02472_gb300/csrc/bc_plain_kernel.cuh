@@ -96,6 +96,10 @@ struct PlainArgs {
     unsigned long long timeout_ns;
     int t_thread, t_hub, seg;
     int bu_den;  // bottom-up discovery on levels with more than n / bu_den vertices (0 = never)
+    // FP64 path counts: a level is recentred once its exponent range leaves
+    // [-centre_bound, centre_bound] (0 = 512).  With FP32 theta the host passes
+    // 64, so that theta-hat = (1 + delta) / sigma-hat stays in FP32 normals.
+    int centre_bound;
     int* trace;  // SP_TRACE builds: 8 ints per warp
 };
 
@@ -235,6 +239,14 @@ struct PlainKernel {
             if (a.ngroups > 1) return *reinterpret_cast<double*>(a.lvl + (gn + (size_t)v) * kRecInts + 2);
         }
         return a.ngroups == 1 ? a.bc[v] : a.bcpart[gn + (size_t)v];
+    }
+    // Power-of-two shift that centres a level of scaled path counts whose
+    // exponents span [emin, emax] (X6 with the launch's bound).
+    __device__ __forceinline__ int shift_of(int emax, int emin) const {
+        const int b = a.centre_bound > 0 ? a.centre_bound : 512;
+        if (emax < emin) return 0;  // empty level
+        if (emax <= b && emin >= -b) return 0;
+        return (emax + emin) >> 1;
     }
     __device__ __forceinline__ int32_t* q() const { return a.q + gn; }
     __device__ __forceinline__ int2* qrow() const { return a.qrow + gn; }
@@ -636,7 +648,7 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
             K.nseg_d = (int)(hc & 0xFFFFFFFFull);
             K.hoff_next = K.hoff_d + K.nrec_d;
             if constexpr (kFloatSig) {
-                K.cshift_prev = d > 0 ? centre_shift(ld_volatile(&K.emax()[d - 1]), ld_volatile(&K.emin()[d - 1])) : 0;
+                K.cshift_prev = d > 0 ? K.shift_of(ld_volatile(&K.emax()[d - 1]), ld_volatile(&K.emin()[d - 1])) : 0;
             }
             if (tid == 0) K.open_level(qe);
             K.my_emax = INT_MIN;
@@ -676,7 +688,7 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
                 long long f = 0;
                 for (int l = 0; l < L; ++l) {
                     K.fexp()[l] = f;
-                    if constexpr (kFloatSig) f += centre_shift(K.emax()[l], K.emin()[l]);
+                    if constexpr (kFloatSig) f += K.shift_of(K.emax()[l], K.emin()[l]);
                 }
             }
             if (!sync()) goto out;
@@ -706,7 +718,7 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
             K.hoff_d = ld_volatile(&K.hoff()[d]);
             K.nrec_d = (int)(hc >> 32);
             K.nseg_d = (int)(hc & 0xFFFFFFFFull);
-            if constexpr (kFloatSig) K.cshift_cur = centre_shift(ld_volatile(&K.emax()[d]), ld_volatile(&K.emin()[d]));
+            if constexpr (kFloatSig) K.cshift_cur = K.shift_of(ld_volatile(&K.emax()[d]), ld_volatile(&K.emin()[d]));
             K.template level_work<false>(phase, qbd, qed, d == L - 1);
             if (!sync()) goto out;
         }
