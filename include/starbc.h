@@ -21,11 +21,22 @@
  * edge and a self-loop is never on a shortest path.
  *
  * Pointers: every array argument may be host memory or device memory of the
- * current device; the library tells them apart with cudaPointerGetAttributes.
- * Work is issued on `stream` (a cudaStream_t; NULL is the legacy default
- * stream), and every call except sp_bc_submit returns once its result is
- * complete, in host or device memory alike: the level loop runs inside
- * persistent kernels whose error word the host reads at the end of the call.
+ * current device (device memory of another GPU is refused with
+ * SP_ERR_INVALID_ARG); the library tells them apart with
+ * cudaPointerGetAttributes.  Work is issued on `stream` (a cudaStream_t; NULL
+ * is the legacy default stream).
+ *
+ * Completion: sp_bc, and sp_bc_ex without statistics, are asynchronous when
+ * bc_out is device memory: the work is enqueued on `stream` and the call
+ * returns without waiting for the GPU (the level loop runs inside persistent
+ * kernels; no host decision is needed between levels).  Device sources are
+ * read in place and must stay valid until the stream reaches the work; host
+ * sources are checked and copied before return.  Such a call still blocks
+ * once per graph for one-time set-up (the eccentricity and landmark BFS, and
+ * the timing trials that pick a batch width or a plain-form driver for a new
+ * graph shape), and whenever it runs the graph-driven plain form.  All other
+ * calls (host output, statistics requested, sp_bfs, sp_sigma, graph creation)
+ * return once their result is complete.
  *
  * Device memory: a graph owns its CSR copy until sp_graph_destroy.  Each BC
  * call takes its workspace (per-source state, level stack) from a memory pool
@@ -34,10 +45,19 @@
  * allocation releases it and retries once).
  *
  * Errors: every entry point returns an sp_status.  Argument errors, allocation
- * failures, CUDA errors and errors found by the GPU (a path count out of
- * range, a device-side wait that timed out) are returned by the call that met
- * them.  sp_last_error() gives a one-line description of the last failure on
- * the calling thread.  Nothing here ever aborts or traps the GPU.
+ * failures and CUDA errors are returned by the call that met them, and so are
+ * errors the GPU finds during a blocking call.  An asynchronous call's device
+ * errors (a path count or dependency out of range, a device-side wait that
+ * timed out, a source in a device array that is not a vertex, a workspace
+ * limit) are latched in the graph's error word and returned, once, by the
+ * next call on that graph (which then does nothing else) or by
+ * sp_graph_sync.  Conditions that a wider representation fixes are handled
+ * on the GPU without the host: counts past the exact integer range or
+ * dependencies past FP32 open a fallback launch of the plain form with FP64
+ * counts and dependencies that runs in the same stream only when needed, and
+ * later calls on the graph start in the representation that fits.
+ * sp_last_error() gives a one-line description of the last failure on the
+ * calling thread.  Nothing here ever aborts or traps the GPU.
  */
 #ifndef STARBC_H
 #define STARBC_H
@@ -105,7 +125,11 @@ typedef struct {
  */
 SP_API sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
                           uint32_t flags, sp_stream stream, sp_graph* out);
+/* Frees the graph after the work issued on it has finished. */
 SP_API sp_status sp_graph_destroy(sp_graph g);
+/* Wait for `stream`, then return (and clear) the error latched by an earlier
+   asynchronous call on the graph: SP_OK when there is none. */
+SP_API sp_status sp_graph_sync(sp_graph g, sp_stream stream);
 
 /*
  * Build a graph from an undirected edge list on the GPU (the CSR offset array
@@ -199,7 +223,8 @@ typedef struct {
     int32_t bottom_up;      /* plain and batched forms: levels wider than n / bottom_up were discovered
                                bottom-up; 0 = never */
     int32_t shared;         /* serving: requests that shared this request's launch (itself included) */
-    int32_t reserved;
+    int32_t recentred;      /* (level, source) pairs whose FP64 path counts were recentred by a power of
+                               two (X6 of the readings; 0 unless sigma_float) */
 } sp_bc_stats;
 
 SP_API void sp_bc_opts_default(sp_bc_opts* o);
@@ -207,12 +232,16 @@ SP_API void sp_bc_opts_default(sp_bc_opts* o);
 /*
  * BC over sources[0..nsrc) into bc_out[n] (FP64, overwritten, not accumulated:
  * the paper's attachNodeProperty(BC = 0) then the per-source sums).
- * sources: int32, host or device; each in [0, n).  nsrc == 0 gives all zeros.
- * bc_out: host or device.  Returns when bc_out holds the result.
+ * sources: int32, host or device; each in [0, n) (host sources are checked
+ * before return; a bad source in a device array is a latched error).
+ * nsrc == 0 gives all zeros.  bc_out: host or device.  With device bc_out the
+ * call is asynchronous on `stream` (see Completion above); with host bc_out
+ * it returns when bc_out holds the result.
  */
 SP_API sp_status sp_bc(sp_graph g, const int32_t* sources, int32_t nsrc, double* bc_out, sp_stream stream);
 
-/* As sp_bc with options; `stats` (host, may be NULL) receives the call's statistics. */
+/* As sp_bc with options.  `stats` (host, may be NULL) receives the call's
+   statistics; a call that asks for them returns when the result is complete. */
 SP_API sp_status sp_bc_ex(sp_graph g, const int32_t* sources, int32_t nsrc, const sp_bc_opts* opts, double* bc_out,
                    sp_bc_stats* stats, sp_stream stream);
 
@@ -241,7 +270,8 @@ SP_API sp_status sp_sigma(sp_graph g, int32_t src, double* mant_out, int64_t* ex
  *   row_ptr[n+1], col_idx[nnz], sources[nsrc], bc_out[n]: device memory of
  *   the current device; the same CSR rules as sp_graph_create, checked on
  *   the GPU.  n <= 262144 and nnz <= 16777216, else SP_ERR_TOO_LARGE.
- *   bc_out is overwritten.  The call returns when the result is complete.
+ *   bc_out is overwritten.  The call is synchronous: it returns after its
+ *   kernels have finished and the result is complete.
  * The first call on a device looks up the array's device address (once per
  * device); make that first call before any stream capture.  Every call uses
  * the same array, so calls that overlap on the GPU (other streams or host
@@ -258,17 +288,19 @@ SP_API sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_idx, i
  * Graphs added to it stay resident (the paper keeps the graph on the device
  * across kernels, Section 4.1).  A request is admitted, in arrival order, when
  * its device footprint fits in what is left of `hbm_budget_bytes`; a free slot
- * takes the oldest admitted request and runs it as one BC call (regrouped
- * source batches of the width tuned for the graph, in one persistent launch).
- * With several slots, each launch is capped to its share of the SMs, so a
- * request that arrives while others run starts at once and overlaps with
- * them on the device.  A request's result does not depend on what else runs:
- * its batches and the order in which their BC is added are fixed by the
+ * takes the oldest admitted request and runs it in one persistent launch;
+ * when the batched form serves it, every other admitted request on the same
+ * graph with the same options joins that launch (continuous batching, up to
+ * 1,024 sources), each in 32-source words of its own.  With several slots,
+ * launches of different slots are sized for the whole GPU and overlap on the
+ * device as SMs free up.  A request's result does not depend on what else
+ * runs: its words and the order in which their BC is added are fixed by the
  * request alone.
  */
 SP_API sp_status sp_server_create(size_t hbm_budget_bytes, int32_t max_slots, sp_server* out);
 SP_API sp_status sp_server_add_graph(sp_server s, sp_graph g, int32_t* graph_id);
-/* bc_out: device double[n] (n of the graph); sources copied before return. */
+/* bc_out: device double[n] (n of the graph) on the graph's GPU, else SP_ERR_INVALID_ARG;
+   sources (host or device) copied before return. */
 SP_API sp_status sp_bc_submit(sp_server s, int32_t graph_id, const int32_t* sources, int32_t nsrc,
                        const sp_bc_opts* opts, double* bc_out, sp_request* req);
 SP_API sp_status sp_bc_poll(sp_server s, sp_request req);                     /* SP_OK, SP_NOT_READY or the error */

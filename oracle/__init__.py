@@ -11,6 +11,9 @@ Functions
 bfs(g, src)          -> int32 dist[n] (-1 unreachable), FIFO BFS.
 sigma(g, src, mode)  -> (mant, exp2, dist, stats): path counts mant * 2**exp2.
 bc(g, sources, mode) -> (bc[n], per-source stats).
+distance_sums(g, sources) -> (sum of d(s, t) over reached t, |R_s|) per source,
+                     from a 64-source bit-parallel BFS (for the invariant
+                     sum_v BC(v) = sum over reached ordered pairs of d - 1).
 
 Modes: PLAIN (doubles; overflow reported as inf), XFLOAT (sigma with a 64-bit
 exponent), AUTO (PLAIN per source, rerun in XFLOAT when sigma overflows).
@@ -82,6 +85,8 @@ def _declare(lib):
     lib.oracle_bc.restype = ctypes.c_int
     lib.oracle_sigma.argtypes = [i32, p, p, i32, ctypes.c_int, p, p, p, p]
     lib.oracle_sigma.restype = ctypes.c_int
+    lib.oracle_distance_sums.argtypes = [i32, p, p, p, i32, p, p]
+    lib.oracle_distance_sums.restype = ctypes.c_int
     return lib
 
 
@@ -130,3 +135,36 @@ def bc(g, sources, mode: int = AUTO, lib=None):
     if rc != 0:
         raise ValueError(f"oracle_bc rc={rc}")
     return out[: g.n], st[:nsrc]
+
+
+def distance_sums(g, sources, lib=None):
+    """Per source: (sum of hop distances to reached vertices, reached count incl. the source)."""
+    lib = lib or load()
+    rp, ci = _csr(g)
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1))
+    nsrc = int(src.size)
+    dsum = np.zeros(max(nsrc, 1), np.int64)
+    reached = np.zeros(max(nsrc, 1), np.int64)
+    buf = src if nsrc else np.zeros(1, np.int32)
+    rc = lib.oracle_distance_sums(g.n, rp.ctypes.data, ci.ctypes.data, buf.ctypes.data, nsrc, dsum.ctypes.data,
+                                  reached.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_distance_sums rc={rc}")
+    return dsum[:nsrc], reached[:nsrc]
+
+
+def pair_distance_excess(g, sources, threads: int = 1) -> int:
+    """sum over sources s and reached t != s of (d(s, t) - 1), the total of all BC values.
+
+    With threads > 1 the sources are cut into slices of 64 searched in parallel
+    (the C code keeps no shared state and ctypes releases the GIL)."""
+    src = np.asarray(sources, dtype=np.int32).reshape(-1)
+    slices = [src[i:i + 64] for i in range(0, src.size, 64)]
+    if threads > 1 and len(slices) > 1:
+        from concurrent.futures import ThreadPoolExecutor
+
+        with ThreadPoolExecutor(min(threads, len(slices))) as ex:
+            parts = list(ex.map(lambda s: distance_sums(g, s), slices))
+    else:
+        parts = [distance_sums(g, s) for s in slices]
+    return int(sum(int(d.sum()) - int((r - 1).sum()) for d, r in parts))

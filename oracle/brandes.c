@@ -16,8 +16,8 @@
  *           for w in neighbours(v): v.delta += (v.sigma / w.sigma) * (1 + w.delta)
  *           v.BC += v.delta
  *
- * Readings taken where the listing is silent (each also stated in the design
- * notes): the forward sum runs over BFS parents only (dist[w] == dist[v] - 1)
+ * Readings taken where the listing is silent: the forward sum runs over BFS
+ * parents only (dist[w] == dist[v] - 1)
  * and the backward sum over BFS children only (dist[w] == dist[v] + 1), as in
  * Brandes' algorithm; graphs are undirected and ordered (s, t) pairs are
  * counted, with no halving; vertices not reached from src have no sigma, no
@@ -263,4 +263,63 @@ int oracle_sigma(int32_t n, const int32_t* rp, const int32_t* ci, int32_t src, i
     }
     free(dist); free(order); free(sigma); free(xsigma); free(delta); free(bc);
     return rc;
+}
+
+/*
+ * Per-source sums of hop distances, for the invariant
+ *     sum_v BC(v) = sum over sources s, reached t != s of (d(s, t) - 1):
+ * dsum[i] = sum of d(sources[i], t) over reached t, reached[i] = |R_s| with s.
+ * Up to 64 sources share one breadth-first search as bits of a 64-bit word
+ * per vertex (multi-source BFS: bit i of frontier[v] means d(s_i, v) = the
+ * current level), a different method from the FIFO search above, used only
+ * for the benchmark-size invariant where one search per source is too slow.
+ * Returns 0, -1 on bad arguments, -2 when out of memory.
+ */
+int oracle_distance_sums(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* sources, int32_t nsrc,
+                         int64_t* dsum, int64_t* reached) {
+    if (n < 0 || nsrc < 0 || (nsrc > 0 && n == 0)) return -1;
+    for (int32_t i = 0; i < nsrc; ++i)
+        if (sources[i] < 0 || sources[i] >= n) return -1;
+    if (nsrc == 0) return 0;
+    uint64_t* seen = (uint64_t*)calloc((size_t)n, sizeof(uint64_t));
+    uint64_t* front = (uint64_t*)calloc((size_t)n, sizeof(uint64_t));
+    uint64_t* next = (uint64_t*)calloc((size_t)n, sizeof(uint64_t));
+    if (!seen || !front || !next) { free(seen); free(front); free(next); return -2; }
+    for (int32_t g0 = 0; g0 < nsrc; g0 += 64) {
+        int32_t cnt = nsrc - g0 < 64 ? nsrc - g0 : 64;
+        memset(seen, 0, (size_t)n * sizeof(uint64_t));
+        memset(front, 0, (size_t)n * sizeof(uint64_t));
+        for (int32_t i = 0; i < cnt; ++i) {
+            uint64_t bit = (uint64_t)1 << i;
+            seen[sources[g0 + i]] |= bit;
+            front[sources[g0 + i]] |= bit;
+            dsum[g0 + i] = 0;
+            reached[g0 + i] = 1;
+        }
+        for (int64_t d = 1;; ++d) {
+            memset(next, 0, (size_t)n * sizeof(uint64_t));
+            for (int32_t v = 0; v < n; ++v) {
+                uint64_t f = front[v];
+                if (!f) continue;
+                for (int32_t e = rp[v]; e < rp[v + 1]; ++e) next[ci[e]] |= f;
+            }
+            int any = 0;
+            for (int32_t u = 0; u < n; ++u) {
+                uint64_t nb = next[u] & ~seen[u];
+                front[u] = nb;
+                if (!nb) continue;
+                any = 1;
+                seen[u] |= nb;
+                while (nb) {
+                    int i = __builtin_ctzll(nb);
+                    nb &= nb - 1;
+                    dsum[g0 + i] += d;
+                    reached[g0 + i] += 1;
+                }
+            }
+            if (!any) break;
+        }
+    }
+    free(seen); free(front); free(next);
+    return 0;
 }

@@ -45,10 +45,10 @@ class sp_bc_stats(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("batches", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("promoted", ctypes.c_int32), ("sigma_float", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("tuned", ctypes.c_int32), ("driver", ctypes.c_int32),
-                ("bottom_up", ctypes.c_int32), ("shared", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("bottom_up", ctypes.c_int32), ("shared", ctypes.c_int32), ("recentred", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class sp_graph_info(ctypes.Structure):
@@ -71,6 +71,7 @@ _P, _I32, _I64, _U32, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, cty
 SIGNATURES = {
     "sp_graph_create": ([_P, _P, _I32, _I64, _U32, _P, _P], ctypes.c_int),
     "sp_graph_destroy": ([_P], ctypes.c_int),
+    "sp_graph_sync": ([_P, _P], ctypes.c_int),
     "sp_graph_get_info": ([_P, _P], ctypes.c_int),
     "sp_graph_from_edges": ([_P, _P, _I64, _I32, _U32, _P, _P], ctypes.c_int),
     "sp_graph_get_csr": ([_P, _P, _P, _P], ctypes.c_int),
@@ -175,6 +176,11 @@ def sp_graph_create(row_ptr, col_idx, n: int | None = None, nnz: int | None = No
 
 def sp_graph_destroy(g: int):
     _check(lib.sp_graph_destroy(g), "sp_graph_destroy")
+
+
+def sp_graph_sync(g: int, stream=None):
+    """Wait for the stream; raise the error an earlier asynchronous call on g latched."""
+    _check(lib.sp_graph_sync(g, _stream(stream)), "sp_graph_sync")
 
 
 def sp_graph_from_edges(src, dst, n: int, flags: int = 0, stream=None) -> int:

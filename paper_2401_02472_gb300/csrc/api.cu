@@ -10,6 +10,7 @@
 #include <string>
 #include <map>
 #include <tuple>
+#include <initializer_list>
 #include <vector>
 
 #include "common.cuh"
@@ -41,6 +42,32 @@ static bool is_device_ptr(const void* p) {
         return false;
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device memory of a GPU other than the current one.  Such buffers are
+// refused: the kernels read and write device buffers directly, and without
+// peer access that would be an illegal access on a shared GPU.
+static bool on_other_device(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.device != dev;
+}
+
+static sp_status refuse_other_device(std::initializer_list<const void*> ptrs, const char* call) {
+    for (const void* p : ptrs)
+        if (on_other_device(p))
+            return fail(SP_ERR_INVALID_ARG, std::string(call) + ": a buffer is device memory of another GPU");
+    return SP_OK;
 }
 
 static sp_status check_device() {
@@ -135,6 +162,8 @@ static sp_status map_device_error(int err, const char* form, const std::string& 
         case kErrSigmaOverflow: return fail(SP_ERR_RANGE, f + ": path counts overflowed");
         case kErrThetaRange32: return fail(SP_ERR_RANGE, f + ": FP32 dependency out of range");
         case kErrCorrupt: return fail(SP_ERR_CUDA, f + ": device state out of range (internal error)");
+        case SP_ERR_INVALID_ARG:
+            return fail(SP_ERR_INVALID_ARG, f + ": a source in the device array is not a vertex id in [0, n)");
         default: return fail(SP_ERR_CUDA, f + ": device error " + std::to_string(err));
     }
 }
@@ -191,6 +220,7 @@ static void add_range_hint(const Graph* g, int bit) {
 
 static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
                            sp_bc_stats* stats, cudaStream_t st);
+static void absorb_hints(Graph* g);
 
 // Time the batched form on the call's first min(nsrc, 256) sources at each
 // width 32 / 64 / 128 / 256 — the same sources for every width — with
@@ -293,16 +323,20 @@ static sp_status autotune_plain(Graph* g, const int32_t* d_src, const sp_bc_opts
 // BFS level for most vertices, so batching them in adjacent bit positions
 // fills mask words and shares the 32-byte sectors of the per-(vertex, source)
 // rows the kernels gather.
-__global__ void source_keys_kernel(const int32_t* __restrict__ src, int32_t nsrc, const int32_t* __restrict__ rp,
-                                   const int32_t* __restrict__ ci, const int32_t* __restrict__ dist,
-                                   const int32_t* __restrict__ dist2, const int32_t* __restrict__ dist3,
-                                   unsigned long long* __restrict__ keys) {
+__global__ void source_keys_kernel(const int32_t* __restrict__ src, int32_t nsrc, int32_t n,
+                                   const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                   const int32_t* __restrict__ dist, const int32_t* __restrict__ dist2,
+                                   const int32_t* __restrict__ dist3, unsigned long long* __restrict__ keys) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
     auto clamp8 = [](int d) -> unsigned long long { return d < 0 || d > 255 ? 255ull : (unsigned long long)d; };
     for (int i = warp; i < nsrc; i += nwarp) {
         const int s = src[i];
+        if (s < 0 || s >= n) {  // not a vertex: an asynchronous call's check reports it; read nothing
+            if (lane == 0) keys[i] = ~0ull;
+            continue;
+        }
         const int ds = dist[s];
         int best = INT_MAX;
         if (ds > 0)
@@ -443,7 +477,74 @@ static int plain_bottom_up(const Graph* g, int32_t opt) {
     return g->n >= (1 << 20) ? 100 : 0;
 }
 
-static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cudaStream_t st, int32_t** out) {
+// Stable sort of the sources by key on the device: a bitonic network over
+// (key, position) pairs, ties resolved by position so that equal keys keep
+// the caller's order; in one block's shared memory for up to kSortBlockMax
+// sources, else in global memory with one launch per merge step.
+constexpr int kSortBlockMax = 4096;
+
+__device__ __forceinline__ bool pair_less(unsigned long long ka, unsigned ia, unsigned long long kb, unsigned ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+__global__ void sort_sources_block_kernel(const unsigned long long* __restrict__ keys,
+                                          const int32_t* __restrict__ src, int32_t m, int32_t p2,
+                                          int32_t* __restrict__ out) {
+    __shared__ unsigned long long sk[kSortBlockMax];
+    __shared__ unsigned si[kSortBlockMax];
+    for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+        sk[i] = i < m ? keys[i] : ~0ull;
+        si[i] = (unsigned)i;
+    }
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const bool gt = pair_less(sk[l], si[l], sk[i], si[i]);
+                    if (gt == up) {
+                        const unsigned long long tk = sk[i]; sk[i] = sk[l]; sk[l] = tk;
+                        const unsigned ti = si[i]; si[i] = si[l]; si[l] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) out[i] = src[si[i]];
+}
+
+__global__ void sort_init_kernel(const unsigned long long* __restrict__ keys, int32_t m, int32_t p2,
+                                 unsigned long long* __restrict__ K, unsigned* __restrict__ I) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p2; i += gridDim.x * blockDim.x) {
+        K[i] = i < m ? keys[i] : ~0ull;
+        I[i] = (unsigned)i;
+    }
+}
+
+__global__ void sort_step_kernel(unsigned long long* __restrict__ K, unsigned* __restrict__ I, int32_t p2, int j,
+                                 int k) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p2; i += gridDim.x * blockDim.x) {
+        const int l = i ^ j;
+        if (l <= i) continue;
+        const bool up = (i & k) == 0;
+        if (pair_less(K[l], I[l], K[i], I[i]) == up) {
+            const unsigned long long tk = K[i]; K[i] = K[l]; K[l] = tk;
+            const unsigned ti = I[i]; I[i] = I[l]; I[l] = ti;
+        }
+    }
+}
+
+__global__ void sort_gather_kernel(const int32_t* __restrict__ src, const unsigned* __restrict__ I, int32_t m,
+                                   int32_t* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) out[i] = src[I[i]];
+}
+
+// A copy of the call's sources in key order (stable), built on the device
+// without waiting for it; nullptr for fewer than two sources.
+static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cudaStream_t st, int32_t** out,
+                               int* launches) {
     *out = nullptr;
     if (nsrc < 2 || g->n == 0) return SP_OK;
     {
@@ -456,32 +557,49 @@ static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cud
     }
     const int32_t* d2 = g->d_land_dist;
     const int32_t* d3 = d2 ? d2 + g->n : nullptr;
-    unsigned long long* d_keys = nullptr;
-    SP_CUDA(cudaMallocAsync((void**)&d_keys, sizeof(unsigned long long) * (size_t)nsrc, st));
-    source_keys_kernel<<<std::min(1024, (nsrc + 7) / 8), 256, 0, st>>>(d_src, nsrc, g->d_rp, g->d_ci, g->d_top_dist,
-                                                                          d2, d3, d_keys);
-    std::vector<unsigned long long> keys(nsrc);
-    std::vector<int32_t> srcs(nsrc);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned long long) * nsrc, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(srcs.data(), d_src, sizeof(int32_t) * nsrc, cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(d_keys, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "source ordering");
-    std::vector<int32_t> idx(nsrc);
-    for (int32_t i = 0; i < nsrc; ++i) idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return keys[x] < keys[y]; });
-    std::vector<int32_t> sorted(nsrc);
-    for (int32_t i = 0; i < nsrc; ++i) sorted[i] = srcs[idx[i]];
-    SP_CUDA(cudaMallocAsync((void**)out, sizeof(int32_t) * (size_t)nsrc, st));
-    e = cudaMemcpyAsync(*out, sorted.data(), sizeof(int32_t) * nsrc, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int32_t p2 = 1;
+    while (p2 < nsrc) p2 <<= 1;
+    const bool one_block = p2 <= kSortBlockMax;
+    // keys [nsrc] (+ K [p2], I [p2] for the multi-launch sort) and the output
+    const size_t kbytes = sizeof(unsigned long long) * (size_t)nsrc;
+    const size_t sbytes = one_block ? 0 : (sizeof(unsigned long long) + sizeof(unsigned)) * (size_t)p2;
+    char* buf = nullptr;
+    SP_CUDA(cudaMallocAsync((void**)&buf, kbytes + sbytes, st));
+    int32_t* sorted = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&sorted, sizeof(int32_t) * (size_t)nsrc, st);
     if (e != cudaSuccess) {
-        cudaFreeAsync(*out, st);
-        *out = nullptr;
+        cudaFreeAsync(buf, st);
         return cuda_fail(e, "source ordering");
     }
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(buf);
+    source_keys_kernel<<<std::min(1024, (nsrc + 7) / 8), 256, 0, st>>>(d_src, nsrc, g->n, g->d_rp, g->d_ci,
+                                                                          g->d_top_dist, d2, d3, keys);
+    int nl = 1;
+    if (one_block) {
+        sort_sources_block_kernel<<<1, 1024, 0, st>>>(keys, d_src, nsrc, p2, sorted);
+        nl += 1;
+    } else {
+        unsigned long long* K = reinterpret_cast<unsigned long long*>(buf + kbytes);
+        unsigned* I = reinterpret_cast<unsigned*>(buf + kbytes + sizeof(unsigned long long) * (size_t)p2);
+        const int grid = (int)std::min<int64_t>((p2 + 255) / 256, (int64_t)device_sm_count(g->device) * 8);
+        sort_init_kernel<<<grid, 256, 0, st>>>(keys, nsrc, p2, K, I);
+        nl += 1;
+        for (int k = 2; k <= p2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                sort_step_kernel<<<grid, 256, 0, st>>>(K, I, p2, j, k);
+                nl += 1;
+            }
+        sort_gather_kernel<<<grid, 256, 0, st>>>(d_src, I, nsrc, sorted);
+        nl += 1;
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(buf, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(sorted, st);
+        return cuda_fail(e, "source ordering");
+    }
+    *out = sorted;
+    if (launches) *launches += nl;
     return SP_OK;
 }
 
@@ -489,6 +607,7 @@ static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cud
 // workspace when the device reports that it ran out of one.
 static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
                            sp_bc_stats* stats, cudaStream_t st) {
+    absorb_hints(g);
     bool sigma_float;
     {
         std::lock_guard<std::mutex> lk(g->mu);
@@ -582,12 +701,9 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
     }
     int32_t* d_sorted = nullptr;
     if (form == SP_FORM_BATCHED && !(o.flags & SP_BC_KEEP_ORDER)) {
-        sp_status orc = order_sources(g, d_src, nsrc, st, &d_sorted);
+        sp_status orc = order_sources(g, d_src, nsrc, st, &d_sorted, &launches);
         if (orc != SP_OK) return orc;
-        if (d_sorted) {
-            d_src = d_sorted;
-            launches += 1;
-        }
+        if (d_sorted) d_src = d_sorted;
     }
     struct FreeSorted {
         int32_t* p;
@@ -706,6 +822,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         stats->promoted = promoted || (o.precision == SP_FP32_DELTA && !theta_f32);
         stats->sigma_float = sigma_float ? 1 : sigma_batches;
         stats->dag_arcs = (int64_t)r.dag_arcs;
+        stats->recentred = (int32_t)std::min<unsigned long long>(r.recentred, INT32_MAX);
         stats->kernel_ms = kernel_ms;
         stats->launches = launches;
         stats->tuned = tuned;
@@ -752,6 +869,7 @@ sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts
         SP_CUDA(cudaStreamSynchronize(st));
         return SP_OK;
     }
+    absorb_hints(g);
     bool sigma_float, theta_f32 = o.precision == SP_FP32_DELTA;
     {
         const int hints = range_hints(g);
@@ -802,7 +920,7 @@ sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts
     }
     const int32_t* d2 = g->d_land_dist;
     source_keys_kernel<<<std::min<int64_t>(1024, (total + 7) / 8), 256, 0, st>>>(
-        d_all, (int32_t)total, g->d_rp, g->d_ci, g->d_top_dist, d2, d2 ? d2 + g->n : nullptr, d_keys);
+        d_all, (int32_t)total, g->n, g->d_rp, g->d_ci, g->d_top_dist, d2, d2 ? d2 + g->n : nullptr, d_keys);
     std::vector<unsigned long long> keys((size_t)total);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
@@ -933,14 +1051,262 @@ sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts
         st_p.form = SP_FORM_BATCHED;
         st_p.promoted = promoted || (o.precision == SP_FP32_DELTA && !theta_f32);
         st_p.sigma_float = sigma_float ? 1 : 0;
+        st_p.recentred = (int32_t)std::min<unsigned long long>(r.recentred, INT32_MAX);
         st_p.launches = launches + nparts;
     }
     return SP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous calls: enqueue on the caller's stream and return.  The host
+// never waits: sources in a device array are checked by a kernel whose
+// verdict the BC kernels read before touching them; a launch ends with a
+// finish step that latches a device error in the graph's mapped flags (the
+// next call on the graph, or sp_graph_sync, returns it) or, for a condition
+// that a wider representation fixes, opens the gate of a fallback launch of
+// the plain form with FP64 counts and dependencies, and records a hint so
+// that later calls start in the representation that fits.
+
+__global__ void check_sources_async_kernel(const int32_t* __restrict__ s, int32_t nsrc, int32_t n, int* pre_err) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsrc; i += gridDim.x * blockDim.x)
+        if (s[i] < 0 || s[i] >= n) atomicCAS(pre_err, 0, (int)SP_ERR_INVALID_ARG);
+}
+
+__global__ void finish_async_kernel(const Ctl* __restrict__ ctl, DevFlags* flags, int* fallback) {
+    if (threadIdx.x != 0) return;
+    const int e = ld_volatile(&ctl->err);
+    if (e == 0) return;
+    int hint = 0;
+    if (e == kErrSigmaOverflow) hint = kHintSigmaFloat;
+    else if (e == kErrThetaRange32) hint = kHintThetaF64;
+    else if (e == kErrCapEntries) hint = kHintEntries;
+    else if (e == kErrCapHubs) hint = kHintHubs;
+    if (hint != 0) atomicOr_system(&flags->hints, hint);
+    const bool fixable = hint != 0 || e == kErrCapLevels || e == kErrCapacity;
+    if (fixable && fallback != nullptr) {
+        *fallback = 1;
+        return;
+    }
+    atomicCAS_system(&flags->err, 0, e);
+}
+
+sp_status enqueue_finish(const Ctl* d_ctl, const AsyncHooks& h, cudaStream_t st) {
+    finish_async_kernel<<<1, 32, 0, st>>>(d_ctl, h.flags, h.fallback);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
+// Hints that earlier asynchronous calls' launches recorded (read without a
+// CUDA call; a launch still running may add more later).
+static void absorb_hints(Graph* g) {
+    if (!g->flags_host) return;
+    const int h = __atomic_exchange_n(&g->flags_host->hints, 0, __ATOMIC_ACQ_REL);
+    if (h == 0) return;
+    if (h & kHintSigmaFloat) add_range_hint(g, 1);
+    if (h & kHintThetaF64) add_range_hint(g, 2);
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (h & kHintSigmaFloat) g->sigma_float = true;
+    if (h & kHintThetaF64) g->theta_f64 = true;
+    if (h & kHintEntries) g->ecap_mult = std::min(2 * g->ecap_mult, 1 << 12);
+    if (h & kHintHubs) g->hcap_mult = std::min(2 * g->hcap_mult, 1 << 12);
+}
+
+// The error an earlier asynchronous call on g latched, taken (cleared).
+static sp_status take_latched(Graph* g) {
+    if (!g->flags_host) return SP_OK;
+    const int e = __atomic_exchange_n(&g->flags_host->err, 0, __ATOMIC_ACQ_REL);
+    if (e == 0) return SP_OK;
+    return map_device_error(e, "an earlier asynchronous call on this graph");
+}
+
+// Enqueue BC over device buffers without waiting.  src_checked: the sources
+// were already validated on the host.  Returns SP_NOT_READY (nothing
+// enqueued) when the call needs the host first: an autotuning trial that has
+// not run for this graph shape, or the graph-driven plain form; the caller
+// then runs it synchronously.
+static sp_status bc_enqueue(Graph* g, const int32_t* d_src, bool src_checked, int32_t nsrc, const sp_bc_opts& o,
+                            double* d_bc, cudaStream_t st) {
+    absorb_hints(g);
+    bool sigma_float, theta_f32 = o.precision == SP_FP32_DELTA;
+    int ecap_mult, hcap_mult;
+    {
+        const int hints = range_hints(g);
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (hints & 1) g->sigma_float = true;
+        if (hints & 2) g->theta_f64 = true;
+        if (g->theta_f64) theta_f32 = false;
+        sigma_float = g->sigma_float;
+        ecap_mult = g->ecap_mult;
+        hcap_mult = g->hcap_mult;
+    }
+    int form = o.form;
+    const bool small_fits = (int64_t)g->n <= small_form_max_n(g->device);
+    if (form == SP_FORM_AUTO && !sigma_float && small_fits) form = SP_FORM_SMALL;
+    if (form == SP_FORM_SMALL && !small_fits)
+        return fail(SP_ERR_TOO_LARGE, "graph too large for the small form (" + std::to_string(g->n) + " vertices)");
+    {
+        sp_status rc = ensure_top_bfs(g, st);  // once per graph; sizes the fallback's block groups
+        if (rc != SP_OK) return rc;
+    }
+    if (form == SP_FORM_AUTO) form = (nsrc >= 2 && g->top_levels <= 64) ? SP_FORM_BATCHED : SP_FORM_PLAIN;
+    int width = 1, batch_bu = batched_bottom_up(g, o.bottom_up), bottom_up = o.bottom_up;
+    if (form == SP_FORM_BATCHED) {
+        if (o.batch > 0) {
+            width = o.batch;
+        } else {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tuned.find(tune_key(g, o.precision));
+            if (it != g_tuned.end()) {
+                width = it->second.width;
+                if (o.bottom_up == 0) batch_bu = batched_bottom_up(g, it->second.bottom_up);
+            } else if (nsrc >= 128) {
+                return SP_NOT_READY;  // the width tuner runs first, synchronously
+            } else {
+                width = default_batch_width(nsrc);
+            }
+        }
+    }
+    if (form == SP_FORM_PLAIN) {
+        int driver = (o.debug_flags & SP_DEBUG_SKIP_BARRIER) ? SP_DRIVER_PERSISTENT : o.driver;
+        if (driver == SP_DRIVER_AUTO) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_plain_tune.find(tune_key(g, o.precision));
+            if (it != g_plain_tune.end() && (o.bottom_up == 0 || it->second.bottom_up == o.bottom_up)) {
+                driver = it->second.driver;
+                bottom_up = it->second.bottom_up;
+            } else if (nsrc >= 16) {
+                return SP_NOT_READY;  // the driver tuner runs first, synchronously
+            } else {
+                driver = SP_DRIVER_PERSISTENT;
+            }
+        }
+        if (driver == SP_DRIVER_GRAPH) return SP_NOT_READY;
+    }
+
+    // per-call words: [0] the sources' check, [1] the fallback's gate
+    int* words = nullptr;
+    SP_CUDA(cudaMallocAsync((void**)&words, 2 * sizeof(int), st));
+    struct FreeWords {
+        int* p;
+        int32_t* q;
+        cudaStream_t s;
+        ~FreeWords() {
+            if (q) cudaFreeAsync(q, s);
+            cudaFreeAsync(p, s);
+        }
+    } fw{words, nullptr, st};
+    SP_CUDA(cudaMemsetAsync(words, 0, 2 * sizeof(int), st));
+    if (!src_checked) {
+        check_sources_async_kernel<<<std::min(1024, (nsrc + 255) / 256), 256, 0, st>>>(d_src, nsrc, g->n, words);
+        SP_CUDA(cudaGetLastError());
+    }
+    // FP64 counts and FP64 dependencies in the plain form admit no wider
+    // representation: their errors are latched directly.
+    const bool widest = form == SP_FORM_PLAIN && sigma_float && !theta_f32;
+    AsyncHooks h;
+    h.pre_err = src_checked ? nullptr : words;
+    h.flags = g->flags_dev;
+    h.fallback = widest ? nullptr : words + 1;
+
+    const int32_t* d_run = d_src;
+    if (form == SP_FORM_BATCHED && !(o.flags & SP_BC_KEEP_ORDER)) {
+        sp_status rc = order_sources(g, d_src, nsrc, st, &fw.q, nullptr);
+        if (rc != SP_OK) return rc;
+        if (fw.q) d_run = fw.q;
+    }
+    LaunchResult r;
+    sp_status rc;
+    if (form == SP_FORM_SMALL) {
+        SmallLaunch L{};
+        L.g = g;
+        L.d_sources = d_run;
+        L.nsrc = nsrc;
+        L.d_bc = d_bc;
+        L.theta_f32 = theta_f32;
+        L.max_ctas = o.max_ctas;
+        L.stream = st;
+        L.async = h;
+        rc = run_small(L, &r);
+    } else if (form == SP_FORM_PLAIN) {
+        PlainLaunch L{};
+        L.g = g;
+        L.d_sources = d_run;
+        L.nsrc = nsrc;
+        L.d_bc = d_bc;
+        L.mode = PlainMode::BC;
+        L.sigma_float = sigma_float;
+        L.theta_f32 = theta_f32;
+        L.max_ctas = o.max_ctas;
+        L.timeout_ns = timeout_of(o);
+        L.debug_flags = o.debug_flags;
+        L.stream = st;
+        L.group_blocks = plain_group_blocks(g);
+        L.bottom_up_den = plain_bottom_up(g, bottom_up);
+        L.async = h;
+        rc = run_plain(L, &r);
+    } else {
+        BatchedLaunch L{};
+        L.g = g;
+        L.d_sources = d_run;
+        L.nsrc = nsrc;
+        L.d_bc = d_bc;
+        L.width = width;
+        L.sigma_float = sigma_float;
+        L.theta_f32 = theta_f32;
+        L.max_ctas = o.max_ctas;
+        L.timeout_ns = timeout_of(o);
+        L.debug_flags = o.debug_flags;
+        L.stream = st;
+        if (ecap_mult > 1) L.entry_cap = std::max<int64_t>(8 * (int64_t)g->n, 1 << 16) * ecap_mult;
+        if (hcap_mult > 1) L.hub_cap = ((g->nnz / 64) * 4 + 1024) * hcap_mult;
+        L.bottom_up_den = batch_bu;
+        L.async = h;
+        rc = run_batched(L, &r);
+    }
+    if (rc != SP_OK) return rc;
+    if (widest) return SP_OK;
+    // The fallback: the plain form with FP64 counts and dependencies, in the
+    // caller's source order; its kernels return at once unless the finish
+    // step of the launch above opened the gate.
+    PlainLaunch F{};
+    F.g = g;
+    F.d_sources = d_src;
+    F.nsrc = nsrc;
+    F.d_bc = d_bc;
+    F.mode = PlainMode::BC;
+    F.sigma_float = true;
+    F.theta_f32 = false;
+    F.max_ctas = o.max_ctas;
+    F.timeout_ns = timeout_of(o);
+    F.stream = st;
+    F.group_blocks = plain_group_blocks(g);
+    F.bottom_up_den = plain_bottom_up(g, 0);
+    F.async.gate = words + 1;
+    F.async.flags = g->flags_dev;
+    LaunchResult r2;
+    return run_plain(F, &r2);
+}
+
 sp_status bc_device_entry(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
                           sp_bc_stats* stats, cudaStream_t st) {
     return bc_device(g, d_src, nsrc, o, d_bc, stats, st);
+}
+
+// The graph's mapped flags (error and hint words of asynchronous calls).
+static sp_status alloc_flags(Graph* g) {
+    void* hp = nullptr;
+    cudaError_t e = cudaHostAlloc(&hp, sizeof(DevFlags), cudaHostAllocMapped);
+    if (e != cudaSuccess) return cuda_fail(e, "graph flags");
+    std::memset(hp, 0, sizeof(DevFlags));
+    void* dp = nullptr;
+    e = cudaHostGetDevicePointer(&dp, hp, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(hp);
+        return cuda_fail(e, "graph flags");
+    }
+    g->flags_host = static_cast<DevFlags*>(hp);
+    g->flags_dev = static_cast<DevFlags*>(dp);
+    return SP_OK;
 }
 
 }  // namespace sp
@@ -986,6 +1352,7 @@ sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_
     if (nnz > 0 && !col_idx) return fail(SP_ERR_INVALID_ARG, "col_idx is NULL");
     if (flags & ~(uint32_t)(SP_GRAPH_CHECK_SYMMETRIC | SP_GRAPH_SORT_ROWS)) return fail(SP_ERR_INVALID_ARG, "unknown flag");
     sp_status rc = check_device();
+    if (rc == SP_OK) rc = refuse_other_device({row_ptr, col_idx}, "sp_graph_create");
     if (rc != SP_OK) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Graph* g = new Graph();
@@ -1020,6 +1387,7 @@ sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_
     }
     rc = validate_graph(g, flags & SP_GRAPH_CHECK_SYMMETRIC, st, &detail);
     if (rc == SP_ERR_BAD_GRAPH) return cleanup(fail(rc, detail));
+    if (rc == SP_OK) rc = alloc_flags(g);
     if (rc != SP_OK) return cleanup(rc);
     *out = reinterpret_cast<sp_graph>(g);
     return SP_OK;
@@ -1035,6 +1403,7 @@ sp_status sp_graph_from_edges(const int32_t* src, const int32_t* dst, int64_t m,
     if (2 * m >= (int64_t)INT32_MAX) return fail(SP_ERR_TOO_LARGE, "2 m must be below 2^31 (int32 row_ptr)");
     if (flags & ~(uint32_t)SP_GRAPH_CHECK_SYMMETRIC) return fail(SP_ERR_INVALID_ARG, "unknown flag");
     sp_status rc = check_device();
+    if (rc == SP_OK) rc = refuse_other_device({src, dst}, "sp_graph_from_edges");
     if (rc != SP_OK) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int32_t* d_src = nullptr;
@@ -1065,6 +1434,7 @@ sp_status sp_graph_from_edges(const int32_t* src, const int32_t* dst, int64_t m,
     std::string detail;
     rc = csr_from_edges(d_src, d_dst, m, n, st, &g->d_rp, &g->d_ci, &g->nnz, &detail);
     if (rc == SP_OK) rc = validate_graph(g, flags, st, &detail);
+    if (rc == SP_OK) rc = alloc_flags(g);
     if (rc != SP_OK) {
         if (g->d_rp) cudaFree(g->d_rp);
         if (g->d_ci) cudaFree(g->d_ci);
@@ -1079,6 +1449,10 @@ sp_status sp_graph_get_csr(sp_graph gh, int32_t* row_ptr_out, int32_t* col_idx_o
     set_last_error("");
     if (!gh || !row_ptr_out || !col_idx_out) return fail(SP_ERR_INVALID_ARG, "NULL argument");
     Graph* g = reinterpret_cast<Graph*>(gh);
+    {
+        sp_status rc = refuse_other_device({row_ptr_out, col_idx_out}, "sp_graph_get_csr");
+        if (rc != SP_OK) return rc;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     auto kind = [](const void* p) { return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; };
     cudaError_t e = cudaMemcpyAsync(row_ptr_out, g->d_rp, sizeof(int32_t) * ((size_t)g->n + 1), kind(row_ptr_out), st);
@@ -1095,10 +1469,21 @@ sp_status sp_graph_destroy(sp_graph gh) {
     if (g->d_top_dist) cudaFree(g->d_top_dist);
     if (g->d_land_dist) cudaFree(g->d_land_dist);
     destroy_step_cache(g);
-    cudaFree(g->d_rp);
+    cudaFree(g->d_rp);  // waits for work still running on the graph
     cudaFree(g->d_ci);
+    if (g->flags_host) cudaFreeHost(g->flags_host);
     delete g;
     return SP_OK;
+}
+
+sp_status sp_graph_sync(sp_graph gh, sp_stream stream) {
+    set_last_error("");
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "sp_graph_sync");
+    absorb_hints(g);
+    return take_latched(g);
 }
 
 sp_status sp_graph_get_info(sp_graph gh, sp_graph_info* out) {
@@ -1125,10 +1510,42 @@ sp_status sp_bc_ex(sp_graph gh, const int32_t* sources, int32_t nsrc, const sp_b
     if (o.max_ctas < 0 || o.barrier_timeout_ns < 0 || o.bottom_up < -1) return fail(SP_ERR_INVALID_ARG, "negative option");
     if (o.driver < SP_DRIVER_AUTO || o.driver > SP_DRIVER_GRAPH) return fail(SP_ERR_INVALID_ARG, "driver");
     if (o.flags & ~(int32_t)SP_BC_KEEP_ORDER) return fail(SP_ERR_INVALID_ARG, "unknown flag");
+    {
+        sp_status rc = refuse_other_device({sources, bc_out}, "sp_bc");
+        if (rc != SP_OK) return rc;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (stats) std::memset(stats, 0, sizeof(*stats));
+    {
+        sp_status rc = take_latched(g);
+        if (rc != SP_OK) return rc;
+    }
     if (g->n == 0) return SP_OK;
     const bool host_out = !is_device_ptr(bc_out);
+    if (!host_out && !stats) {
+        // Asynchronous: enqueue on `stream` and return.  Host sources are
+        // checked here and staged (the copy reads them before return);
+        // device sources are read in place by the kernels.
+        const bool dev_src = nsrc > 0 && is_device_ptr(sources);
+        int32_t* staged = nullptr;
+        if (nsrc > 0 && !dev_src) {
+            for (int32_t i = 0; i < nsrc; ++i)
+                if (sources[i] < 0 || sources[i] >= g->n)
+                    return fail(SP_ERR_INVALID_ARG, "source " + std::to_string(i) + " is not a vertex id in [0, n)");
+            sp_status rc = stage_in(sources, nsrc, st, &staged);
+            if (rc != SP_OK) return rc;
+        }
+        sp_status rc;
+        if (nsrc == 0) {
+            cudaError_t e = cudaMemsetAsync(bc_out, 0, sizeof(double) * (size_t)g->n, st);
+            rc = e == cudaSuccess ? SP_OK : cuda_fail(e, "zeroing bc_out");
+        } else {
+            rc = bc_enqueue(g, dev_src ? sources : staged, !dev_src, nsrc, o, bc_out, st);
+        }
+        if (staged) cudaFreeAsync(staged, st);
+        if (rc != SP_NOT_READY) return rc;
+        set_last_error("");  // needs a host decision first: run synchronously below
+    }
     double* d_bc = bc_out;
     if (host_out) SP_CUDA(cudaMallocAsync((void**)&d_bc, sizeof(double) * (size_t)g->n, st));
     int32_t* d_src = nullptr;
@@ -1163,8 +1580,16 @@ sp_status sp_bfs(sp_graph gh, const int32_t* sources, int32_t nsrc, int32_t* dis
     if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
     Graph* g = reinterpret_cast<Graph*>(gh);
     if (nsrc < 0) return fail(SP_ERR_INVALID_ARG, "nsrc < 0");
+    {
+        sp_status rc = take_latched(g);
+        if (rc != SP_OK) return rc;
+    }
     if (nsrc == 0 || g->n == 0) return SP_OK;
     if (!sources || !dist_out) return fail(SP_ERR_INVALID_ARG, "NULL pointer");
+    {
+        sp_status rc = refuse_other_device({sources, dist_out}, "sp_bfs");
+        if (rc != SP_OK) return rc;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t count = (size_t)nsrc * (size_t)g->n;
     const bool host_out = !is_device_ptr(dist_out);
@@ -1213,8 +1638,16 @@ sp_status sp_sigma(sp_graph gh, int32_t src, double* mant_out, int64_t* exp2_out
     set_last_error("");
     if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
     Graph* g = reinterpret_cast<Graph*>(gh);
+    {
+        sp_status rc = take_latched(g);
+        if (rc != SP_OK) return rc;
+    }
     if (src < 0 || src >= g->n) return fail(SP_ERR_INVALID_ARG, "source out of range");
     if (!mant_out || !exp2_out) return fail(SP_ERR_INVALID_ARG, "NULL pointer");
+    {
+        sp_status rc = refuse_other_device({mant_out, exp2_out}, "sp_sigma");
+        if (rc != SP_OK) return rc;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t n = (size_t)g->n;
     const bool host_m = !is_device_ptr(mant_out), host_e = !is_device_ptr(exp2_out);

@@ -70,7 +70,7 @@ struct BatchArgs {
     int32_t* emin;            // [lcap][B]
     int32_t lcap;
     Ctl* ctl;
-    int* err_latch;
+    const int* pre_err;       // asynchronous calls: nonzero = the sources failed their check, do nothing
     int debug_flags;
     unsigned long long timeout_ns;
     int t_hub, seg;
@@ -83,6 +83,7 @@ struct BatchArgs {
     double* word_bc;                 // [nsrc / 32][n], zeroed by the host; null outside request mode
     unsigned long long* word_stats;  // [nsrc / 32][2]
     int bu_den;  // bottom-up discovery on levels with more than n / bu_den entries (0 = never)
+    int centre_bound;  // FP64 path counts: recentre a level whose exponents leave [-bound, bound]
 };
 
 template <int W>
@@ -309,8 +310,11 @@ struct BatchKernel {
     }
 
     // Backward: from the per-lane sums of theta over children, delta, theta(v), BC.
+    // The entry's dependencies are added into BC in FP64 whatever their
+    // storage precision: each lane's W values, then a fixed-order butterfly
+    // over the warp.
     __device__ __forceinline__ void delta_flush(int v, const uint32_t (&F)[W], const AccT (&acc)[W]) {
-        AccT bcsum = 0;
+        double bcsum = 0.0;
         AccT dk[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -330,7 +334,7 @@ struct BatchKernel {
                     float t = (1.0f + delta) / sf;
                     if (!normal_finite_f(t) || !normal_finite_f(sf)) set_error(ctl, kErrThetaRange32);
                     th()[idx] = t;
-                    bcsum += delta;
+                    bcsum += (double)delta;
                     dk[k] = delta;
                 } else {
                     double s = (double)sv;
@@ -349,18 +353,17 @@ struct BatchKernel {
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 if (F[k] == 0u) continue;  // the entry's mask: the same in every lane
-                AccT x = dk[k];
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+                const double x = warp_sum_f64((double)dk[k]);
                 if (lane == 0) {
                     double* p = a.word_bc + (size_t)(word0 + k) * (size_t)a.n + v;
-                    *p = __ldcg(p) + (double)x;
+                    *p = __ldcg(p) + x;
                 }
             }
             return;
         }
         // fixed-order reduction over the sources of this entry
-        for (int o = 16; o > 0; o >>= 1) bcsum += __shfl_xor_sync(kFull, bcsum, o);
-        if (lane == 0) a.bc[v] = __ldcg(&a.bc[v]) + (double)bcsum;
+        bcsum = warp_sum_f64(bcsum);
+        if (lane == 0) a.bc[v] = __ldcg(&a.bc[v]) + bcsum;
     }
 
     // Request mode: per-word counts of traversed (arc, source) pairs and
@@ -816,6 +819,13 @@ struct BatchKernel {
 
 template <int W, typename SigT, typename ThT>
 __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(BatchArgs a) {
+    if (a.pre_err != nullptr) {  // the same word for every block: all return, nothing is touched
+        const int pe = ld_volatile(a.pre_err);
+        if (pe != 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->err = pe;
+            return;
+        }
+    }
     using K_t = BatchKernel<W, SigT, ThT>;
     constexpr int B = K_t::B;
     constexpr bool kFloatSig = K_t::kFloatSig;
@@ -946,8 +956,15 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
 #pragma unroll
                 for (int k = 0; k < W; ++k)
                     K.cshift[k] = d > 0 ? centre_shift(ld_volatile(&a.emax[(size_t)(d - 1) * B + k * 32 + lane]),
-                                                       ld_volatile(&a.emin[(size_t)(d - 1) * B + k * 32 + lane]))
+                                                       ld_volatile(&a.emin[(size_t)(d - 1) * B + k * 32 + lane]),
+                                                       a.centre_bound)
                                         : 0;
+                if (blockIdx.x == 0 && threadIdx.x < 32) {  // one warp counts the recentred (level, source) pairs
+                    int nrec = 0;
+#pragma unroll
+                    for (int k = 0; k < W; ++k) nrec += __popc(__ballot_sync(kFull, K.cshift[k] != 0) & K.active[k]);
+                    if (lane == 0 && nrec) atomicAdd(&ctl->recentred, (unsigned long long)nrec);
+                }
                 if (d + 1 < a.lcap)
                     for (int i = tid; i < B; i += nthr) {
                         a.emax[(size_t)(d + 1) * B + i] = INT_MIN;
@@ -1003,7 +1020,7 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
 #pragma unroll
                 for (int k = 0; k < W; ++k)
                     K.cshift[k] = centre_shift(ld_volatile(&a.emax[(size_t)dd * B + k * 32 + lane]),
-                                               ld_volatile(&a.emin[(size_t)dd * B + k * 32 + lane]));
+                                               ld_volatile(&a.emin[(size_t)dd * B + k * 32 + lane]), a.centre_bound);
             }
             // scatter F_dd into its dense ring slot (read by level dd-1), clear F_{dd+2},
             // and clear seen of this level's vertices
@@ -1073,8 +1090,6 @@ out:
             atomicAdd(&ctl->scanned_arcs, s_st[3]);
             atomicAdd(&ctl->dag_arcs, s_st[4]);
             atomicMax(&ctl->max_levels, levels_max);
-            int e = ld_volatile(&ctl->err);
-            if (e != 0 && a.err_latch) *(volatile int*)a.err_latch = e;
         }
 #ifdef SP_PROFILE
         if ((threadIdx.x & 31) == 0)

@@ -104,7 +104,7 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.emin = reinterpret_cast<int32_t*>(ws + o_emin);
     a.lcap = (int32_t)lcap;
     a.ctl = reinterpret_cast<Ctl*>(ws + o_ctl);
-    a.err_latch = nullptr;
+    a.pre_err = L.async.pre_err;
     a.debug_flags = L.debug_flags;
     a.timeout_ns = L.timeout_ns;
     a.t_hub = t_hub;
@@ -112,8 +112,24 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.word_bc = L.d_word_bc;
     a.bu_den = L.bottom_up_den;
     a.word_stats = L.d_word_stats;
+    a.centre_bound = sigma_centre_bound(L.sigma_float, L.theta_f32, PlainMode::BC);
 
     void* args[] = {&a};
+    if (L.async.flags != nullptr) {  // enqueue only: the finish step moves the error word on
+        ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBatchThreads), args, 0, st);
+        if (ce != cudaSuccess) {
+            cudaFreeAsync(ws, st);
+            return cuda_fail(ce, "cudaLaunchCooperativeKernel (batched form)");
+        }
+        sp_status frc = enqueue_finish(a.ctl, L.async, st);
+        cudaFreeAsync(ws, st);
+        result->launches = 2;
+        result->grid = grid;
+        result->ecap = ecap;
+        result->hcap = hcap;
+        result->lcap = lcap;
+        return frc;
+    }
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
@@ -137,6 +153,7 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     result->entries = h.entries;
     result->scanned_arcs = h.scanned_arcs;
     result->dag_arcs = h.dag_arcs;
+    result->recentred = h.recentred;
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) result->kernel_ms = ms;
     cudaEventDestroy(ev0);

@@ -108,13 +108,17 @@ __global__ void noalloc_check_kernel(const int32_t* __restrict__ rp, const int32
     }
 }
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (or managed memory, which every device may
+// access).  Memory of another GPU is refused: the kernels read and write the
+// buffers directly, and without peer access that would be an illegal access.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -133,14 +137,15 @@ extern "C" sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_id
                                           ", nnz = " + std::to_string(nnz) + "); use sp_bc");
     if (!row_ptr || !bc_out || (nnz > 0 && !col_idx) || (nsrc > 0 && !sources))
         return fail(SP_ERR_INVALID_ARG, "sp_bc_noalloc: NULL pointer");
-    if (!on_device(row_ptr) || !on_device(bc_out) || (nnz > 0 && !on_device(col_idx)) ||
-        (nsrc > 0 && !on_device(sources)))
-        return fail(SP_ERR_INVALID_ARG, "sp_bc_noalloc: row_ptr, col_idx, sources and bc_out must be device memory");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return fail(SP_ERR_NO_DEVICE, "no CUDA device");
     }
+    if (!on_device(row_ptr, dev) || !on_device(bc_out, dev) || (nnz > 0 && !on_device(col_idx, dev)) ||
+        (nsrc > 0 && !on_device(sources, dev)))
+        return fail(SP_ERR_INVALID_ARG,
+                    "sp_bc_noalloc: row_ptr, col_idx, sources and bc_out must be device memory of the current device");
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
@@ -200,14 +205,15 @@ extern "C" sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_id
     a.emin = reinterpret_cast<int32_t*>(ws + kOffEmin);
     a.fexp = reinterpret_cast<long long*>(ws + kOffFexp);
     a.ctl = reinterpret_cast<Ctl*>(ws + kOffCtl);
-    a.err_latch = nullptr;
+    a.pre_err = nullptr;
+    a.gate = nullptr;
     a.mode = (int)PlainMode::BC;
     a.timeout_ns = 20000000000ull;
     a.t_thread = kTThread;
     a.t_hub = kTHub;
     a.seg = kSeg;
     a.bu_den = 0;
-    a.centre_bound = 512;
+    a.centre_bound = sigma_centre_bound(true, false, PlainMode::BC);
     a.trace = nullptr;
 
     // Exact 64-bit path counts first; FP64 counts with per-level rescaling

@@ -88,7 +88,8 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     a.hcap = (int32_t)hcap;
     a.segcap = (int32_t)segcap;
     a.lcap = (int32_t)lcap;
-    a.err_latch = nullptr;
+    a.pre_err = L.async.pre_err;
+    a.gate = L.async.gate;
     a.dist_out = L.d_dist;
     a.mant_out = L.d_mant;
     a.exp_out = L.d_exp;
@@ -99,21 +100,40 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     a.t_hub = tiers.t_hub;
     a.seg = tiers.seg;
     a.bu_den = L.bottom_up_den;
-    a.centre_bound = L.sigma_float && L.theta_f32 && L.mode == PlainMode::BC ? 64 : 512;
+    a.centre_bound = sigma_centre_bound(L.sigma_float, L.theta_f32, L.mode);
     cudaMemsetAsync(a.trace, 0, sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32), st);
 
     void* args[] = {&a};
+    auto launch = [&]() -> cudaError_t {
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPlainThreads), args, 0, st);
+        if (e == cudaSuccess && ngroups > 1 && L.mode == PlainMode::BC) {
+            int rgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count(dev) * 8);
+            const double* part = rec ? reinterpret_cast<const double*>(a.lvl) + 1 : a.bcpart;
+            sum_group_partials_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(part, ngroups, n, rec ? 4 : 1, L.d_bc,
+                                                                          a.gate);
+            e = cudaGetLastError();
+        }
+        return e;
+    };
+    if (L.async.flags != nullptr) {  // enqueue only: the finish step moves the error word on
+        ce = launch();
+        if (ce != cudaSuccess) {
+            cudaFreeAsync(ws, st);
+            return cuda_fail(ce, "plain-form launch");
+        }
+        sp_status frc = enqueue_finish(a.ctl, L.async, st);
+        cudaFreeAsync(ws, st);
+        result->launches = ngroups > 1 && L.mode == PlainMode::BC ? 3 : 2;
+        result->lcap = lcap;
+        result->grid = grid;
+        result->groups = ngroups;
+        return frc;
+    }
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
     cudaEventRecord(ev0, st);
-    ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPlainThreads), args, 0, st);
-    if (ce == cudaSuccess && ngroups > 1 && L.mode == PlainMode::BC) {
-        int rgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count(dev) * 8);
-        const double* part = rec ? reinterpret_cast<const double*>(a.lvl) + 1 : a.bcpart;
-        sum_group_partials_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(part, ngroups, n, rec ? 4 : 1, L.d_bc);
-        ce = cudaGetLastError();
-    }
+    ce = launch();
     cudaEventRecord(ev1, st);
     if (ce != cudaSuccess) {
         cudaFreeAsync(ws, st);
@@ -136,6 +156,7 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     result->entries = h.reached;
     result->scanned_arcs = h.scanned_arcs;
     result->dag_arcs = h.dag_arcs;
+    result->recentred = h.recentred;
     result->lcap = lcap;
     result->grid = grid;
     result->groups = ngroups;

@@ -152,6 +152,7 @@ static __device__ __forceinline__ void step_work(PlainKernel<SigT, ThT, false>& 
         K.hoff_next = K.hoff_d + K.nrec_d;
         if constexpr (kFloatSig) {
             K.cshift_prev = d > 0 ? K.shift_of(ld_volatile(&K.emax()[d - 1]), ld_volatile(&K.emin()[d - 1])) : 0;
+            if (blockIdx.x == 0 && threadIdx.x == 0 && K.cshift_prev != 0) atomicAdd(&sa.ctl->recentred, 1ull);
         }
         K.discover = !ss.bu;
         K.template level_work<true>(0, ss.qb, ss.qe, false, ss.bu ? (n + 8 * kWarp - 1) / (8 * kWarp) : 0);
@@ -341,7 +342,8 @@ sp_status run_plain_graph(const PlainLaunch& L, LaunchResult* result) {
     a.hcap = (int32_t)hcap;
     a.segcap = (int32_t)segcap;
     a.lcap = (int32_t)lcap;
-    a.err_latch = nullptr;
+    a.pre_err = nullptr;
+    a.gate = nullptr;
     a.mode = (int)PlainMode::BC;
     a.debug_flags = 0;
     a.timeout_ns = L.timeout_ns;
@@ -349,7 +351,7 @@ sp_status run_plain_graph(const PlainLaunch& L, LaunchResult* result) {
     a.t_hub = tiers.t_hub;
     a.seg = tiers.seg;
     a.bu_den = L.bottom_up_den;
-    a.centre_bound = L.sigma_float && L.theta_f32 ? 64 : 512;
+    a.centre_bound = sigma_centre_bound(L.sigma_float, L.theta_f32, L.mode);
     a.trace = nullptr;
     hb.state.stage = kStageInit;
     hb.state.step_limit = (long long)L.nsrc * (2 * n + 2) + 2;
@@ -404,6 +406,7 @@ sp_status run_plain_graph(const PlainLaunch& L, LaunchResult* result) {
     result->entries = h.reached;
     result->scanned_arcs = h.scanned_arcs;
     result->dag_arcs = h.dag_arcs;
+    result->recentred = h.recentred;
     result->lcap = lcap;
     result->grid = grid;
     result->groups = 1;

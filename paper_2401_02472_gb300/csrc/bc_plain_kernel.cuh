@@ -87,7 +87,8 @@ struct PlainArgs {
     int32_t lcap;
     Ctl* ctl;               // launch-wide: error, statistics
     GroupCtl* gctl;         // [ngroups]
-    int* err_latch;
+    const int* pre_err;     // asynchronous calls: nonzero = the sources failed their check, do nothing
+    const int* gate;        // asynchronous fallback launch: run only when *gate != 0 (null = always)
     int32_t* dist_out;
     double* mant_out;
     long long* exp_out;
@@ -243,10 +244,7 @@ struct PlainKernel {
     // Power-of-two shift that centres a level of scaled path counts whose
     // exponents span [emin, emax] (X6 with the launch's bound).
     __device__ __forceinline__ int shift_of(int emax, int emin) const {
-        const int b = a.centre_bound > 0 ? a.centre_bound : 512;
-        if (emax < emin) return 0;  // empty level
-        if (emax <= b && emin >= -b) return 0;
-        return (emax + emin) >> 1;
+        return centre_shift(emax, emin, a.centre_bound > 0 ? a.centre_bound : 512);
     }
     __device__ __forceinline__ int32_t* q() const { return a.q + gn; }
     __device__ __forceinline__ int2* qrow() const { return a.qrow + gn; }
@@ -596,8 +594,24 @@ struct PlainKernel {
     }
 };
 
+// Whether an asynchronous launch skips its work: a fallback launch whose gate
+// is closed, or a call whose sources failed their check on the device (the
+// same words for every block, written before the launch).
+static __device__ __forceinline__ bool plain_skip(const PlainArgs& a) {
+    if (a.gate != nullptr && ld_volatile(a.gate) == 0) return true;
+    if (a.pre_err != nullptr) {
+        const int pe = ld_volatile(a.pre_err);
+        if (pe != 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->err = pe;
+            return true;
+        }
+    }
+    return false;
+}
+
 template <typename SigT, typename ThT, bool kRec>
 __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
+    if (plain_skip(a)) return;
     constexpr bool kFloatSig = !std::is_integral<SigT>::value;
     const int g = blockIdx.x / a.gblocks;
     if (g >= a.ngroups) return;  // the host sizes the grid to ngroups * gblocks
@@ -649,6 +663,7 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
             K.hoff_next = K.hoff_d + K.nrec_d;
             if constexpr (kFloatSig) {
                 K.cshift_prev = d > 0 ? K.shift_of(ld_volatile(&K.emax()[d - 1]), ld_volatile(&K.emin()[d - 1])) : 0;
+                if (tid == 0 && K.cshift_prev != 0) atomicAdd(&ctl->recentred, 1ull);
             }
             if (tid == 0) K.open_level(qe);
             K.my_emax = INT_MIN;
@@ -741,8 +756,6 @@ out:
             atomicAdd(&ctl->scanned_arcs, s_st[2]);
             atomicAdd(&ctl->dag_arcs, s_st[3]);
             atomicMax(&ctl->max_levels, levels_max);
-            int e = ld_volatile(&ctl->err);
-            if (e != 0 && a.err_latch) *(volatile int*)a.err_latch = e;
         }
     }
 }
@@ -810,7 +823,8 @@ inline void plain_bind(PlainArgs& a, char* ws, const PlainLayout& o) {
 // gi at vertex v: part[gi * n * vstride + v * vstride] (vstride 1 for the
 // partial-BC arrays, 4 for the BC field of 32-byte vertex records).
 static __global__ void sum_group_partials_kernel(const double* __restrict__ part, int ngroups, int64_t n,
-                                                 int vstride, double* __restrict__ out) {
+                                                 int vstride, double* __restrict__ out, const int* gate) {
+    if (gate != nullptr && ld_volatile(gate) == 0) return;  // a fallback launch that did not run
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int gi = 0; gi < ngroups; ++gi) s += part[((int64_t)gi * n + v) * vstride];

@@ -48,6 +48,7 @@ struct SmallArgs {
     double* bcpart;   // [gridDim.x][n] partial BC per block
     int32_t* qoff;    // [gridDim.x][n + 2] level offsets per block
     Ctl* ctl;
+    const int* pre_err;  // asynchronous calls: nonzero = the sources failed their check, do nothing
 };
 
 // Shared-memory bytes of one block for n vertices.
@@ -55,6 +56,13 @@ inline size_t small_smem_bytes(int64_t n) { return (size_t)n * 16 + 64; }
 
 template <typename ThT>
 __global__ void __launch_bounds__(kSmallThreads, 2) small_kernel(SmallArgs a) {
+    if (a.pre_err != nullptr) {
+        const int pe = ld_volatile(a.pre_err);
+        if (pe != 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->err = pe;
+            return;
+        }
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n;
     unsigned long long* slot = reinterpret_cast<unsigned long long*>(smem);  // sigma, then theta bits
@@ -344,6 +352,22 @@ sp_status run_small(const SmallLaunch& L, LaunchResult* result) {
     a.bcpart = reinterpret_cast<double*>(ws + o_part);
     a.qoff = reinterpret_cast<int32_t*>(ws + o_qoff);
     a.ctl = reinterpret_cast<Ctl*>(ws + o_ctl);
+    a.pre_err = L.async.pre_err;
+
+    if (L.async.flags != nullptr) {  // enqueue only: the finish step moves the error word on
+        void* args[] = {&a};
+        cudaError_t ce = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st);
+        if (ce == cudaSuccess) {
+            const int rgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count(g->device) * 8);
+            small_sum_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(a.bcpart, grid, n, L.d_bc);
+            ce = cudaGetLastError();
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "small form");
+        result->launches = 3;
+        result->grid = grid;
+        result->groups = grid;
+        return enqueue_finish(a.ctl, L.async, st);  // the workspace is freed after it (FreeWs)
+    }
 
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);

@@ -42,6 +42,7 @@ struct Ctl {
     unsigned long long entries;
     unsigned long long scanned_arcs;
     unsigned long long dag_arcs;     // (arc, source) pairs on shortest-path DAGs
+    unsigned long long recentred;    // (level, source) pairs whose FP64 path counts were recentred
     int max_levels;
     unsigned int timeout_count;      // arrivals seen by the first wait that timed out
     int snap[2];                     // qtail as the last block found it, per barrier parity
@@ -160,11 +161,11 @@ __device__ __forceinline__ bool normal_finite_f(float x) {
 }
 // Per-level recentring of scaled path counts: with the level's largest and
 // smallest unbiased exponents, shift only when the level strays from 2^0 by
-// more than 2^512, and then centre it.  0 shift keeps values bit-identical to
-// unscaled FP64 arithmetic.
-__device__ __forceinline__ int centre_shift(int emax, int emin) {
+// more than 2^bound, and then centre it.  0 shift keeps values bit-identical
+// to unscaled FP64 arithmetic.
+__device__ __forceinline__ int centre_shift(int emax, int emin, int bound) {
     if (emax < emin) return 0;  // empty level
-    if (emax <= 512 && emin >= -512) return 0;
+    if (emax <= bound && emin >= -bound) return 0;
     return (emax + emin) >> 1;
 }
 

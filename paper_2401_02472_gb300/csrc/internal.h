@@ -16,6 +16,35 @@ namespace sp {
 struct Ctl;
 struct HubRec;
 
+// Per-graph words that the device writes and the host reads without a CUDA
+// call (mapped pinned host memory): the first error of an asynchronous call,
+// returned by the next call on the graph or by sp_graph_sync, and the
+// representation hints its launches found (kHint* bits).
+struct DevFlags {
+    int err;
+    int hints;
+};
+constexpr int kHintSigmaFloat = 1;  // path counts needed FP64 with per-level exponents
+constexpr int kHintThetaF64 = 2;    // FP32 dependencies left the FP32 range
+constexpr int kHintEntries = 4;     // the batched level stack was too small
+constexpr int kHintHubs = 8;        // the batched hub records were too few
+
+// Hooks of an asynchronous call; all null for a synchronous one.  The launch
+// is only enqueued and nothing is read back: its kernels skip all work when
+// *pre_err holds an error (bad sources found on the device) or when `gate` is
+// set and *gate == 0; after the launch a finish kernel moves the launch's
+// error word on: a condition that the FP64 fallback launch fixes opens
+// *fallback and records a hint, any other error is latched in flags->err.
+struct AsyncHooks {
+    const int* pre_err = nullptr;
+    const int* gate = nullptr;
+    DevFlags* flags = nullptr;  // device view of the graph's flags; non-null = asynchronous launch
+    int* fallback = nullptr;    // null: no fallback follows, every error is latched
+};
+
+// Enqueue the finish step of an asynchronous launch whose control block is d_ctl.
+sp_status enqueue_finish(const Ctl* d_ctl, const AsyncHooks& h, cudaStream_t st);
+
 struct Graph {
     int device = 0;
     int32_t n = 0;
@@ -23,8 +52,9 @@ struct Graph {
     int32_t* d_rp = nullptr;  // [n+1]
     int32_t* d_ci = nullptr;  // [max(nnz,1)]
     sp_graph_info info{};
-    int* err_latch_host = nullptr;  // mapped pinned int: device-side errors of asynchronous calls
-    int* err_latch_dev = nullptr;
+    DevFlags* flags_host = nullptr;  // mapped pinned: errors and hints of asynchronous calls
+    DevFlags* flags_dev = nullptr;   // the same words, as the device addresses them
+    int ecap_mult = 1, hcap_mult = 1;  // batched capacities learnt from asynchronous calls
     std::mutex mu;
     bool sigma_float = false;  // path counts of this graph overflowed 64-bit integers before
     int32_t top_vertex = 0;     // a vertex of maximum degree
@@ -55,6 +85,16 @@ struct Tiers {
 
 enum class PlainMode : int { BC = 0, BFS = 1, SIGMA = 2 };
 
+// Exponent bound beyond which a level of FP64 path counts is recentred (X6
+// of the readings: the shift is the mean of the level's largest and smallest
+// exponents).  512 leaves the widest within-level spread to FP64; when
+// dependencies are stored in FP32, theta-hat = (1 + delta) / sigma-hat must
+// stay in FP32 normals, so BC calls with FP32 theta recentre at 64.  Every
+// form and driver takes the bound from here.
+inline int sigma_centre_bound(bool sigma_float, bool theta_f32, PlainMode mode) {
+    return sigma_float && theta_f32 && mode == PlainMode::BC ? 64 : 512;
+}
+
 struct PlainLaunch {
     const Graph* g;
     const int32_t* d_sources;
@@ -73,6 +113,7 @@ struct PlainLaunch {
     int group_blocks;       // blocks per group (0 = one group of every block)
     int64_t level_cap;      // BFS levels per group; 0 = default
     int bottom_up_den;      // bottom-up discovery on levels wider than n / this (0 = top-down only)
+    AsyncHooks async;
 };
 
 struct LaunchResult {
@@ -83,6 +124,7 @@ struct LaunchResult {
     unsigned long long dag_arcs = 0;
     double kernel_ms = 0.0;                // CUDA-event time of the launch
     int launches = 0;
+    unsigned long long recentred = 0;      // (level, source) pairs recentred
     int grid = 0;
     int groups = 1;
     std::string diag;                      // barrier state when a wait timed out
@@ -107,6 +149,7 @@ struct SmallLaunch {
     bool theta_f32;
     int max_ctas;
     cudaStream_t stream;
+    AsyncHooks async;
 };
 
 // Small-graph form: one block per source, per-source state in shared memory.
@@ -131,6 +174,7 @@ struct BatchedLaunch {
     int bottom_up_den;                 // bottom-up discovery on levels with more than n / this entries (0 = never)
     double* d_word_bc;                 // request mode: [nsrc/32][n] per-word partial BC (else null)
     unsigned long long* d_word_stats;  // request mode: [nsrc/32][2]
+    AsyncHooks async;
 };
 
 // Serving: several requests on one graph in one batched launch, each

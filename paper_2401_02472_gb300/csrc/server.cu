@@ -247,6 +247,14 @@ sp_status sp_bc_submit(sp_server sh, int32_t graph_id, const int32_t* sources, i
     }
     if (nsrc < 0 || (nsrc > 0 && !sources)) return fail(SP_ERR_INVALID_ARG, "sources");
     if (g->n > 0 && !bc_out) return fail(SP_ERR_INVALID_ARG, "bc_out is NULL");
+    if (g->n > 0) {
+        // the kernels write bc_out directly: it must be memory this GPU can write
+        cudaPointerAttributes at{};
+        const bool ok = cudaPointerGetAttributes(&at, bc_out) == cudaSuccess &&
+                        (at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == g->device));
+        cudaGetLastError();
+        if (!ok) return fail(SP_ERR_INVALID_ARG, "bc_out must be device memory of the graph's GPU");
+    }
     auto r = std::make_shared<Request>();
     r->g = g;
     r->bc_out = bc_out;

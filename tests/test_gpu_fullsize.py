@@ -8,8 +8,10 @@ The oracle cannot run every source of the large workloads in test time, so:
                                   distances from the oracle's BFS;
   RMAT scale 22, 1,024 sources:   the first 32 sources, as a call of their
                                   own, against the oracle in FP64 and FP32
-                                  (widths 32 and 256), and the full autotuned
-                                  call against the sum of two half calls.
+                                  (widths 32, 128 and 256), the full autotuned
+                                  call against the same invariant (distance
+                                  sums from the oracle's 64-source BFS) and
+                                  against the sum of two half calls.
 """
 from concurrent.futures import ThreadPoolExecutor
 import os
@@ -70,6 +72,7 @@ def test_knn_1m_256_sources():
     assert abs(got.sum() - excess) <= 1e-4 * excess
     assert st["max_levels"] > 1000
     assert st["sigma_float"] == 1  # path counts pass 2^64: the FP64 per-level-exponent path ran
+    assert st["promoted"] == 0  # recentred at +-2^64, theta-hat stays in FP32
 
 
 def test_rmat22_sampled_sources_and_split_linearity():
@@ -83,10 +86,13 @@ def test_rmat22_sampled_sources_and_split_linearity():
     with ThreadPoolExecutor(len(parts)) as ex:
         want = sum(ex.map(lambda p: oracle.bc(g, p)[0], parts))
     for prec, rtol in [(sp.SP_FP64, 1e-9), (sp.SP_FP32_DELTA, 1e-4)]:
-        for width in (32, 256):
+        for width in (32, 128, 256):
             got, _ = gpu_bc(G, spot, prec, sp.SP_FORM_BATCHED, width)
             assert_close(got, want, rtol, f"rmat22 32 sources precision {prec} width {width}")
     full, st = gpu_bc(G, srcs, sp.SP_FP32_DELTA)
+    # the whole call: sum of BC = sum over reached ordered pairs of (d - 1)
+    excess = oracle.pair_distance_excess(g, srcs, threads=os.cpu_count() or 1)
+    assert abs(full.sum() - excess) <= 1e-4 * excess, (full.sum(), excess)
     a, _ = gpu_bc(G, srcs[:512], sp.SP_FP32_DELTA, sp.SP_FORM_BATCHED, st["batch"])
     b, _ = gpu_bc(G, srcs[512:], sp.SP_FP32_DELTA, sp.SP_FORM_BATCHED, st["batch"])
     assert_close(full, a + b, 1e-4, "rmat22 split")

@@ -461,3 +461,109 @@ def test_barrier_timeout_returns_status(form):
     got, _ = gpu_bc(G, list(range(40)), sp.SP_FP64, form, 32)  # the context is still usable
     want, _ = oracle.bc(g, list(range(40)))
     assert_bc_close(got, want, 1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Range handling of path counts (X6 / X9 of the readings)
+
+def diamond_chain(k):
+    """k diamonds in a row: a_i - b_i, a_i - c_i, b_i - a_(i+1), c_i - a_(i+1).
+    From a_0 the path counts double at every a_i (sigma(a_k) = 2^k) while each
+    level holds equal counts, so FP64 counts are needed past 2^64 but a level
+    never spreads."""
+    edges = []
+    for i in range(k):
+        a, b, c, a2 = 3 * i, 3 * i + 1, 3 * i + 2, 3 * i + 3
+        edges += [(a, b), (a, c), (b, a2), (c, a2)]
+    return gen.from_edges(3 * k + 1, edges, f"diamonds{k}")
+
+
+@pytest.mark.parametrize("precision", [sp.SP_FP64, sp.SP_FP32_DELTA])
+@pytest.mark.parametrize("batch", [32, 128])
+def test_batched_recentres_rescaled_counts(batch, precision):
+    # Path counts up to C(1198, 599) ~ 2^1193 on a 600 x 600 grid from three
+    # corners: the batched form reruns with FP64 counts and recentres levels
+    # whose exponents leave the bound.  FP32 dependencies cannot hold theta
+    # here (a level spans ~2^595), so that call is promoted to FP64.
+    g = gen.grid(600, 600)
+    G = device_graph(g)
+    srcs = np.array([0, 599, 600 * 600 - 1], np.int32)
+    got, st = gpu_bc(G, srcs, precision, sp.SP_FORM_BATCHED, batch)
+    want, ost = oracle.bc(g, srcs)
+    assert ost["used_xfloat"].all()
+    assert_bc_close(got, want, RTOL[precision], f"grid600 batched B={batch}")
+    assert st["form"] == sp.SP_FORM_BATCHED and st["sigma_float"] == 1
+    assert st["recentred"] > 0
+    assert st["max_levels"] == 1199
+    if precision == sp.SP_FP32_DELTA:
+        assert st["promoted"] == 1
+    G.close()
+
+
+def test_plain_fp32_promotion_on_wide_levels():
+    # The plain form's FP32 dependencies leave FP32 on the 600 x 600 grid too:
+    # the call reruns with FP64 theta and still matches the oracle.
+    g = gen.grid(600, 600)
+    G = device_graph(g)
+    srcs = np.array([0, 600 * 600 - 1], np.int32)
+    for driver in (sp.SP_DRIVER_PERSISTENT, sp.SP_DRIVER_GRAPH):
+        got, st = gpu_bc(G, srcs, sp.SP_FP32_DELTA, sp.SP_FORM_PLAIN, driver=driver)
+        want, _ = oracle.bc(g, srcs)
+        assert_bc_close(got, want, 1e-4, f"grid600 plain FP32 driver {driver}")
+        assert st["promoted"] == 1 and st["sigma_float"] == 1 and st["recentred"] > 0
+    G.close()
+
+
+@pytest.mark.parametrize("form,kw", [
+    (sp.SP_FORM_PLAIN, dict(driver=sp.SP_DRIVER_PERSISTENT, debug_flags=sp.SP_DEBUG_PLAIN_ARRAYS)),
+    (sp.SP_FORM_PLAIN, dict(driver=sp.SP_DRIVER_PERSISTENT, debug_flags=sp.SP_DEBUG_PLAIN_RECORDS)),
+    (sp.SP_FORM_PLAIN, dict(driver=sp.SP_DRIVER_GRAPH)),
+    (sp.SP_FORM_BATCHED, dict(batch=32)),
+    (sp.SP_FORM_BATCHED, dict(batch=128)),
+    (sp.SP_FORM_SMALL, dict()),
+])
+def test_fp32_dependencies_stay_fp32_past_2_64(form, kw):
+    # Counts reach 2^300 but every level holds equal counts: FP64 counts
+    # recentred at +-2^64 keep theta-hat = (1 + delta) / sigma-hat inside FP32,
+    # so no form reruns with FP64 dependencies (promoted == 0).  With FP64
+    # dependencies the bound is 2^512, which these counts never reach: no
+    # level is recentred.  The small form holds exact counts only and hands
+    # the call to the plain form.
+    g = diamond_chain(300)
+    G = device_graph(g)
+    srcs = np.array([0, 1, 450, 900], np.int32)
+    want, ost = oracle.bc(g, srcs)
+    assert not ost["used_xfloat"].any()
+    for prec in (sp.SP_FP32_DELTA, sp.SP_FP64):
+        got, st = gpu_bc(G, srcs, prec, form, **kw)
+        assert_bc_close(got, want, RTOL[prec], f"diamond chain form {form} {kw} precision {prec}")
+        assert st["sigma_float"] == 1, st
+        assert (st["recentred"] > 0) if prec == sp.SP_FP32_DELTA else (st["recentred"] == 0), st
+        assert st["promoted"] == 0, st
+        assert st["max_levels"] == int(ost["levels"].max())
+    G.close()
+
+
+@pytest.mark.parametrize("form,batch", [(sp.SP_FORM_PLAIN, 0), (sp.SP_FORM_BATCHED, 32)])
+def test_spread_limit_gives_range_error_or_exact_values(form, batch):
+    # On a 2,100 x 2,100 grid from a corner the anti-diagonal level holds path
+    # counts from 1 to C(2099, 1049) ~ 2^2095: wider than the FP64 exponent
+    # range even after centring.  The call must either return values that
+    # match the oracle (extended exponents) or SP_ERR_RANGE; never NaN.
+    g = gen.grid(2100, 2100)
+    G = device_graph(g)
+    try:
+        got, _ = gpu_bc(G, [0], sp.SP_FP64, form, batch)
+    except sp.StarbcError as e:
+        assert e.status == sp.SP_ERR_RANGE, e
+        got = None
+    if got is not None:
+        assert np.all(np.isfinite(got))
+        want, _ = oracle.bc(g, [0])
+        assert_bc_close(got, want, 1e-9, "grid2100")
+    G.close()
+    # the context is still usable
+    g2, G2 = graph("er2000")
+    got, _ = gpu_bc(G2, [1, 2, 3], sp.SP_FP64, form, batch)
+    want, _ = oracle.bc(g2, [1, 2, 3])
+    assert_bc_close(got, want, 1e-9)

@@ -263,3 +263,27 @@ def test_bad_arguments():
         oracle.bc(g, [-1])
     with pytest.raises(ValueError):
         oracle.bfs(g, 9)
+
+
+def test_distance_sums_against_deque_bfs():
+    # The 64-source bit-parallel search behind the benchmark-size invariant:
+    # per-source distance sums and reached counts against one deque BFS per
+    # source, across word boundaries (130 sources), with repeated and
+    # isolated sources and several components.
+    cases = [
+        (gen.er(400, 1200, 5), None),
+        (gen.rmat(11, 8, 6), None),
+        (gen.knn2d(800, 4, 7), None),
+        (gen.disjoint_union(gen.path(9), gen.star(12), gen.cycle(5), gen.from_edges(4, [])),
+         np.array([0, 0, 3, 9, 10, 21, 26, 28, 29, 8, 8], np.int32)),
+    ]
+    for g, srcs in cases:
+        if srcs is None:
+            srcs = gen.sources(g, min(130, g.n), 3)
+        dsum, reached = oracle.distance_sums(g, srcs)
+        for i, s in enumerate(srcs):
+            d = np.asarray(bf.bfs_dist(g, int(s)))
+            assert dsum[i] == int(d[d >= 0].sum()) and reached[i] == int((d >= 0).sum()), (g.name, i)
+        assert oracle.pair_distance_excess(g, srcs, threads=3) == bf.pair_distance_excess(g, srcs)
+    with pytest.raises(ValueError):
+        oracle.distance_sums(gen.path(4), [4])

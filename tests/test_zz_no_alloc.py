@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import gen
+import oracle
 import paper_2401_02472_gb300 as sp
 
 pytestmark = pytest.mark.gpu
@@ -55,3 +56,24 @@ def test_rejects_graphs_beyond_the_scratch_size():
         sp.sp_bc_noalloc(np.zeros(4, np.int32), np.zeros(1, np.int32), np.zeros(1, np.int32),
                          np.zeros(3, np.float64), n=3, nnz=1)
     assert e.value.status == sp.SP_ERR_INVALID_ARG
+
+
+def test_matches_the_oracle_including_counts_past_64_bits():
+    # Against the CPU oracle directly.  The 500 x 500 grid (250,000 vertices,
+    # path counts up to C(998, 499) ~ 2^993) overflows the exact 64-bit
+    # counts, so the call takes its second attempt with FP64 counts and
+    # per-level exponents.
+    for g, srcs in [(gen.er(2000, 10000, 1), np.arange(0, 2000, 13, dtype=np.int32)),
+                    (gen.grid(500, 500), np.array([0, 499, 500 * 500 - 1], np.int32))]:
+        want, _ = oracle.bc(g, srcs)
+        rp = torch.as_tensor(g.row_ptr, device=DEV)
+        ci = torch.as_tensor(g.col_idx, device=DEV)
+        src = torch.as_tensor(srcs, device=DEV)
+        for _ in range(2):
+            out = torch.full((g.n,), -1.0, dtype=torch.float64, device=DEV)
+            sp.sp_bc_noalloc(rp, ci, src, out)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            err = np.abs(got - want)
+            assert np.all(err <= 1e-9 * np.maximum(np.abs(want), 1.0)), (g.name, err.max())
+            assert np.all(got[want == 0.0] == 0.0)
