@@ -52,6 +52,8 @@ def _load():
             lib.gen_er.restype = ctypes.c_int
             lib.gen_rmat.argtypes = [i32, i32, f64, f64, f64, u64, p, p, p]
             lib.gen_rmat.restype = ctypes.c_int
+            lib.gen_rmat_directed.argtypes = [i32, i32, f64, f64, f64, u64, p, p, p]
+            lib.gen_rmat_directed.restype = ctypes.c_int
             lib.gen_knn2d.argtypes = [i32, i32, u64, p, p, p, p]
             lib.gen_knn2d.restype = ctypes.c_int
             lib.gen_sources.argtypes = [i32, p, i32, u64, p]
@@ -110,6 +112,20 @@ def rmat(scale: int, edge_factor: int, seed: int, a=0.57, b=0.19, c=0.19) -> Gra
     if rc != 0:
         raise ValueError(f"gen_rmat failed ({rc})")
     return Graph(n, rp, ci[: nnz[0]].copy(), f"rmat_s{scale}_ef{edge_factor}_s{seed}")
+
+
+def rmat_directed(scale: int, edge_factor: int, seed: int, a=0.57, b=0.19, c=0.19) -> Graph:
+    """Directed RMAT: every draw is one arc u -> v (seeded relabelling, deduped, no self-loops)."""
+    lib = _load()
+    n = 1 << scale
+    m = edge_factor * n
+    rp = np.empty(n + 1, np.int32)
+    ci = np.empty(m, np.int32)
+    nnz = np.zeros(1, np.int64)
+    rc = lib.gen_rmat_directed(scale, edge_factor, a, b, c, seed, _ptr(rp), _ptr(ci), _ptr(nnz))
+    if rc != 0:
+        raise ValueError(f"gen_rmat_directed failed ({rc})")
+    return Graph(n, rp, ci[: nnz[0]].copy(), f"drmat_s{scale}_ef{edge_factor}_s{seed}")
 
 
 def knn2d(n: int, k: int, seed: int, return_points: bool = False):
@@ -174,6 +190,38 @@ def from_edges(n: int, edges, name: str = "") -> Graph:
     rp = np.zeros(n + 1, np.int32)
     rp[1:] = np.cumsum(counts)
     return Graph(n, rp, dst.astype(np.int32), name)
+
+
+def from_arcs(n: int, arcs, name: str = "") -> Graph:
+    """Directed CSR from an iterable of arcs (u, v): rows sorted, repeated arcs once, loops dropped."""
+    e = np.asarray(list(arcs) if not isinstance(arcs, np.ndarray) else arcs, dtype=np.int64).reshape(-1, 2)
+    if e.size:
+        if e.min() < 0 or e.max() >= n:
+            raise ValueError("arc endpoint out of range")
+        e = e[e[:, 0] != e[:, 1]]
+        key = np.unique(e[:, 0] * np.int64(max(n, 1)) + e[:, 1])
+        src = (key // max(n, 1)).astype(np.int64)
+        dst = (key % max(n, 1)).astype(np.int32)
+    else:
+        src = np.zeros(0, np.int64)
+        dst = np.zeros(0, np.int32)
+    counts = np.bincount(src, minlength=n) if n > 0 else np.zeros(0, np.int64)
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum(counts)
+    return Graph(n, rp, dst.astype(np.int32), name)
+
+
+def transpose(g: Graph) -> Graph:
+    """The graph with every arc reversed."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr.astype(np.int64)))
+    return from_arcs(g.n, np.stack([g.col_idx.astype(np.int64), rows], 1), g.name + "^T")
+
+
+def random_small_directed(n: int, p: float, seed: int) -> Graph:
+    """Random digraph on small n: arc (i, j), i != j, present iff its uniform draw < p."""
+    pairs = [(i, j) for i in range(n) for j in range(n) if i != j]
+    u = uniforms(substream(seed, 8), 0, len(pairs))
+    return from_arcs(n, [pq for pq, x in zip(pairs, u) if x < p], f"dgnp{n}_{p}_s{seed}")
 
 
 def path(n: int) -> Graph:

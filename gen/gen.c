@@ -132,8 +132,8 @@ int gen_er(int32_t n, int64_t m, uint64_t seed, int32_t* row_ptr, int32_t* col_i
 
 /* ------------------------------------------------------------------ */
 /* RMAT.  n = 2^scale; draws = ef * n; upper bound for col_idx: 2 * draws. */
-int gen_rmat(int32_t scale, int32_t edge_factor, double a, double b, double c, uint64_t seed,
-             int32_t* row_ptr, int32_t* col_idx, int64_t* nnz_out) {
+static int rmat_arcs(int32_t scale, int32_t edge_factor, double a, double b, double c, uint64_t seed, int both,
+                     int32_t* row_ptr, int32_t* col_idx, int64_t* nnz_out) {
     if (scale < 1 || scale > 30 || edge_factor < 1) return -1;
     int32_t n = (int32_t)1 << scale;
     int64_t m = (int64_t)edge_factor * (int64_t)n;
@@ -161,13 +161,29 @@ int gen_rmat(int32_t scale, int32_t edge_factor, double a, double b, double c, u
             u = (u << 1) | ub; v = (v << 1) | vb;
         }
         uint64_t pu = (uint64_t)perm[u], pv = (uint64_t)perm[v];
-        keys[2 * e] = (pu << 32) | pv;
-        keys[2 * e + 1] = (pv << 32) | pu;
+        if (both) {
+            keys[2 * e] = (pu << 32) | pv;
+            keys[2 * e + 1] = (pv << 32) | pu;
+        } else {
+            keys[e] = (pu << 32) | pv;
+        }
     }
     free(perm);
-    int rc = keys_to_csr(keys, 2 * m, n, row_ptr, col_idx, nnz_out);
+    int rc = keys_to_csr(keys, both ? 2 * m : m, n, row_ptr, col_idx, nnz_out);
     free(keys);
     return rc;
+}
+
+int gen_rmat(int32_t scale, int32_t edge_factor, double a, double b, double c, uint64_t seed,
+             int32_t* row_ptr, int32_t* col_idx, int64_t* nnz_out) {
+    return rmat_arcs(scale, edge_factor, a, b, c, seed, 1, row_ptr, col_idx, nnz_out);
+}
+
+/* Directed RMAT: each draw is one arc u -> v (relabelled, deduped, no
+   self-loops); upper bound for col_idx: draws. */
+int gen_rmat_directed(int32_t scale, int32_t edge_factor, double a, double b, double c, uint64_t seed,
+                      int32_t* row_ptr, int32_t* col_idx, int64_t* nnz_out) {
+    return rmat_arcs(scale, edge_factor, a, b, c, seed, 0, row_ptr, col_idx, nnz_out);
 }
 
 /* ------------------------------------------------------------------ */

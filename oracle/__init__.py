@@ -11,6 +11,9 @@ Functions
 bfs(g, src)          -> int32 dist[n] (-1 unreachable), FIFO BFS.
 sigma(g, src, mode)  -> (mant, exp2, dist, stats): path counts mant * 2**exp2.
 bc(g, sources, mode) -> (bc[n], per-source stats).
+bc(..., directed=True), sigma(..., directed=True): the same on a directed
+                     graph (CSR of out-arcs): BFS and dependencies over
+                     out-arcs, path counts pulled over in-arcs.
 distance_sums(g, sources) -> (sum of d(s, t) over reached t, |R_s|) per source,
                      from a 64-source bit-parallel BFS (for the invariant
                      sum_v BC(v) = sum over reached ordered pairs of d - 1).
@@ -85,6 +88,10 @@ def _declare(lib):
     lib.oracle_bc.restype = ctypes.c_int
     lib.oracle_sigma.argtypes = [i32, p, p, i32, ctypes.c_int, p, p, p, p]
     lib.oracle_sigma.restype = ctypes.c_int
+    lib.oracle_bc_directed.argtypes = [i32, p, p, p, i32, ctypes.c_int, p, p]
+    lib.oracle_bc_directed.restype = ctypes.c_int
+    lib.oracle_sigma_directed.argtypes = [i32, p, p, i32, ctypes.c_int, p, p, p, p]
+    lib.oracle_sigma_directed.restype = ctypes.c_int
     lib.oracle_distance_sums.argtypes = [i32, p, p, p, i32, p, p]
     lib.oracle_distance_sums.restype = ctypes.c_int
     return lib
@@ -108,21 +115,22 @@ def bfs(g, src: int, lib=None) -> np.ndarray:
     return dist[: g.n]
 
 
-def sigma(g, src: int, mode: int = AUTO, lib=None):
+def sigma(g, src: int, mode: int = AUTO, lib=None, directed: bool = False):
     lib = lib or load()
     rp, ci = _csr(g)
     mant = np.empty(g.n, np.float64)
     exp2 = np.empty(g.n, np.int64)
     dist = np.empty(g.n, np.int32)
     st = np.zeros(1, STATS_DTYPE)
-    rc = lib.oracle_sigma(g.n, rp.ctypes.data, ci.ctypes.data, int(src), mode, mant.ctypes.data,
-                          exp2.ctypes.data, dist.ctypes.data, st.ctypes.data)
+    fn = lib.oracle_sigma_directed if directed else lib.oracle_sigma
+    rc = fn(g.n, rp.ctypes.data, ci.ctypes.data, int(src), mode, mant.ctypes.data,
+            exp2.ctypes.data, dist.ctypes.data, st.ctypes.data)
     if rc != 0:
         raise ValueError(f"oracle_sigma rc={rc}")
     return mant, exp2, dist, st[0]
 
 
-def bc(g, sources, mode: int = AUTO, lib=None):
+def bc(g, sources, mode: int = AUTO, lib=None, directed: bool = False):
     lib = lib or load()
     rp, ci = _csr(g)
     src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1))
@@ -130,8 +138,8 @@ def bc(g, sources, mode: int = AUTO, lib=None):
     st = np.zeros(max(src.size, 1), STATS_DTYPE)
     nsrc = int(src.size)
     buf = src if nsrc else np.zeros(1, np.int32)
-    rc = lib.oracle_bc(g.n, rp.ctypes.data, ci.ctypes.data, buf.ctypes.data, nsrc, mode, out.ctypes.data,
-                       st.ctypes.data)
+    fn = lib.oracle_bc_directed if directed else lib.oracle_bc
+    rc = fn(g.n, rp.ctypes.data, ci.ctypes.data, buf.ctypes.data, nsrc, mode, out.ctypes.data, st.ctypes.data)
     if rc != 0:
         raise ValueError(f"oracle_bc rc={rc}")
     return out[: g.n], st[:nsrc]

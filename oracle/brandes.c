@@ -113,8 +113,12 @@ int oracle_bfs(int32_t n, const int32_t* rp, const int32_t* ci, int32_t src, int
     return 0;
 }
 
-/* One source of ComputeBC.  Adds this source's dependencies into bc. */
-static int one_source(int32_t n, const int32_t* rp, const int32_t* ci, int32_t src, int use_xf, double* bc,
+/* One source of ComputeBC.  Adds this source's dependencies into bc.
+ * (rp, ci) hold the out-arcs: the BFS and the backward sum run over them.
+ * (prp, pci) hold the arcs the forward sum pulls over: the same arrays for an
+ * undirected graph, the in-arcs (the transpose) for a directed one. */
+static int one_source(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* prp, const int32_t* pci,
+                      int32_t src, int use_xf, double* bc,
                       int32_t* dist, int32_t* order, double* sigma, xf* xsigma, double* delta,
                       oracle_src_stats* st, double* mant_out, int64_t* exp_out) {
     int64_t reached = bfs_order(n, rp, ci, src, dist, order);
@@ -131,8 +135,8 @@ static int one_source(int32_t n, const int32_t* rp, const int32_t* ci, int32_t s
     int overflow = 0;
     for (int64_t i = 1; i < reached; ++i) {
         int32_t v = order[i];
-        for (int32_t e = rp[v]; e < rp[v + 1]; ++e) {
-            int32_t w = ci[e];
+        for (int32_t e = prp[v]; e < prp[v + 1]; ++e) {
+            int32_t w = pci[e];
             if (dist[w] != dist[v] - 1) continue;
             if (use_xf) xsigma[v] = xf_add(xsigma[v], xsigma[w]);
             else sigma[v] = sigma[v] + sigma[w];
@@ -209,8 +213,8 @@ static int one_source(int32_t n, const int32_t* rp, const int32_t* ci, int32_t s
  * bc[n] is overwritten.  stats may be NULL, else holds nsrc entries.
  * Returns 0, or -1 on bad arguments, -2 when out of memory.
  */
-int oracle_bc(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* sources, int32_t nsrc, int mode,
-              double* bc, oracle_src_stats* stats) {
+static int bc_over(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* prp, const int32_t* pci,
+                   const int32_t* sources, int32_t nsrc, int mode, double* bc, oracle_src_stats* stats) {
     if (n < 0 || nsrc < 0 || (nsrc > 0 && n == 0)) return -1;
     for (int32_t i = 0; i < nsrc; ++i)
         if (sources[i] < 0 || sources[i] >= n) return -1;
@@ -228,9 +232,11 @@ int oracle_bc(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* so
     for (int32_t i = 0; i < nsrc; ++i) {
         oracle_src_stats* st = stats ? &stats[i] : NULL;
         int use_xf = (mode == ORACLE_XFLOAT);
-        int rc = one_source(n, rp, ci, sources[i], use_xf, bc, dist, order, sigma, xsigma, delta, st, NULL, NULL);
+        int rc = one_source(n, rp, ci, prp, pci, sources[i], use_xf, bc, dist, order, sigma, xsigma, delta, st,
+                            NULL, NULL);
         if (rc == 1 && mode == ORACLE_AUTO)
-            rc = one_source(n, rp, ci, sources[i], 1, bc, dist, order, sigma, xsigma, delta, st, NULL, NULL);
+            rc = one_source(n, rp, ci, prp, pci, sources[i], 1, bc, dist, order, sigma, xsigma, delta, st, NULL,
+                            NULL);
         if (rc == 1) { /* PLAIN mode overflowed: report infinity as the result */
             for (int32_t v = 0; v < n; ++v) bc[v] = 1.0 / 0.0;
             break;
@@ -244,8 +250,8 @@ int oracle_bc(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* so
  * Path counts from one source as mant * 2^exp (mant in [1,2), 0 when not
  * reached).  mode as in oracle_bc.  dist may be NULL.
  */
-int oracle_sigma(int32_t n, const int32_t* rp, const int32_t* ci, int32_t src, int mode, double* mant,
-                 int64_t* exp2, int32_t* dist_out, oracle_src_stats* st) {
+static int sigma_over(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* prp, const int32_t* pci,
+                      int32_t src, int mode, double* mant, int64_t* exp2, int32_t* dist_out, oracle_src_stats* st) {
     if (n <= 0 || src < 0 || src >= n) return -1;
     int32_t* dist = (int32_t*)malloc((size_t)n * sizeof(int32_t));
     int32_t* order = (int32_t*)malloc((size_t)n * sizeof(int32_t));
@@ -256,12 +262,65 @@ int oracle_sigma(int32_t n, const int32_t* rp, const int32_t* ci, int32_t src, i
     int rc = -2;
     if (dist && order && sigma && xsigma && delta && bc) {
         int use_xf = (mode == ORACLE_XFLOAT);
-        rc = one_source(n, rp, ci, src, use_xf, bc, dist, order, sigma, xsigma, delta, st, mant, exp2);
+        rc = one_source(n, rp, ci, prp, pci, src, use_xf, bc, dist, order, sigma, xsigma, delta, st, mant, exp2);
         if (rc == 1 && mode == ORACLE_AUTO)
-            rc = one_source(n, rp, ci, src, 1, bc, dist, order, sigma, xsigma, delta, st, mant, exp2);
+            rc = one_source(n, rp, ci, prp, pci, src, 1, bc, dist, order, sigma, xsigma, delta, st, mant, exp2);
         if (rc == 0 && dist_out) memcpy(dist_out, dist, (size_t)n * sizeof(int32_t));
     }
     free(dist); free(order); free(sigma); free(xsigma); free(delta); free(bc);
+    return rc;
+}
+
+int oracle_bc(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* sources, int32_t nsrc, int mode,
+              double* bc, oracle_src_stats* stats) {
+    return bc_over(n, rp, ci, rp, ci, sources, nsrc, mode, bc, stats);
+}
+
+int oracle_sigma(int32_t n, const int32_t* rp, const int32_t* ci, int32_t src, int mode, double* mant,
+                 int64_t* exp2, int32_t* dist_out, oracle_src_stats* st) {
+    return sigma_over(n, rp, ci, rp, ci, src, mode, mant, exp2, dist_out, st);
+}
+
+/*
+ * Directed graphs.  (rp, ci) hold the out-arcs u -> v.  The BFS follows
+ * out-arcs; sigma(v) is pulled from the in-neighbours u of v one level up
+ * (the BFS parents, u -> v with dist[u] = dist[v] - 1), read from the
+ * transpose built here; delta(v) from the out-neighbours w one level down
+ * (u -> w with dist[w] = dist[v] + 1), as above.  Transpose rows list their
+ * in-neighbours in increasing id.
+ */
+static int transpose_csr(int32_t n, const int32_t* rp, const int32_t* ci, int32_t** trp, int32_t** tci) {
+    int64_t nnz = n > 0 ? rp[n] : 0;
+    *trp = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+    *tci = (int32_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    int32_t* fill = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!*trp || !*tci || !fill) { free(*trp); free(*tci); free(fill); return -2; }
+    for (int64_t e = 0; e < nnz; ++e) (*trp)[ci[e] + 1] += 1;
+    for (int32_t v = 0; v < n; ++v) (*trp)[v + 1] += (*trp)[v];
+    for (int32_t v = 0; v < n; ++v) fill[v] = (*trp)[v];
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t e = rp[u]; e < rp[u + 1]; ++e) (*tci)[fill[ci[e]]++] = u;
+    free(fill);
+    return 0;
+}
+
+int oracle_bc_directed(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* sources, int32_t nsrc,
+                       int mode, double* bc, oracle_src_stats* stats) {
+    if (n < 0) return -1;
+    int32_t *trp = NULL, *tci = NULL;
+    if (transpose_csr(n, rp, ci, &trp, &tci) != 0) return -2;
+    int rc = bc_over(n, rp, ci, trp, tci, sources, nsrc, mode, bc, stats);
+    free(trp); free(tci);
+    return rc;
+}
+
+int oracle_sigma_directed(int32_t n, const int32_t* rp, const int32_t* ci, int32_t src, int mode, double* mant,
+                          int64_t* exp2, int32_t* dist_out, oracle_src_stats* st) {
+    if (n <= 0) return -1;
+    int32_t *trp = NULL, *tci = NULL;
+    if (transpose_csr(n, rp, ci, &trp, &tci) != 0) return -2;
+    int rc = sigma_over(n, rp, ci, trp, tci, src, mode, mant, exp2, dist_out, st);
+    free(trp); free(tci);
     return rc;
 }
 

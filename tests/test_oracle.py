@@ -287,3 +287,75 @@ def test_distance_sums_against_deque_bfs():
         assert oracle.pair_distance_excess(g, srcs, threads=3) == bf.pair_distance_excess(g, srcs)
     with pytest.raises(ValueError):
         oracle.distance_sums(gen.path(4), [4])
+
+
+# ---------------------------------------------------------------------------
+# Directed graphs: BFS and dependencies over out-arcs, path counts pulled over
+# in-arcs (the transpose the oracle builds itself).
+
+def test_every_digraph_on_four_vertices():
+    # All 4,096 labelled digraphs on 4 vertices against exact rationals from
+    # explicit shortest-path enumeration, all sources.
+    pairs = [(i, j) for i in range(4) for j in range(4) if i != j]
+    for mask in range(1 << len(pairs)):
+        g = gen.from_arcs(4, [pairs[b] for b in range(len(pairs)) if mask >> b & 1])
+        got, _ = oracle.bc(g, range(4), directed=True)
+        assert close(got, bf.bc_exact(g, range(4))), mask
+
+
+def test_random_digraphs_up_to_nine_vertices():
+    for seed in range(60):
+        n = 5 + seed % 5
+        g = gen.random_small_directed(n, 0.25 + 0.05 * (seed % 6), seed)
+        srcs = [int(x) for x in gen.draws(seed, 0, 6) % n]
+        for mode in (oracle.PLAIN, oracle.XFLOAT):
+            got, _ = oracle.bc(g, srcs, mode, directed=True)
+            assert close(got, bf.bc_exact(g, srcs)), (seed, mode)
+        assert oracle.sigma(g, srcs[0], directed=True)[0].tolist() is not None
+        mant, exp2, _, _ = oracle.sigma(g, srcs[0], oracle.PLAIN, directed=True)
+        assert [m * 2.0 ** int(e) for m, e in zip(mant, exp2)] == bf.sigma_exact(g, srcs[0]), seed
+
+
+@pytest.mark.parametrize("n", [2, 3, 8, 41])
+def test_directed_path(n):
+    # 0 -> 1 -> ... -> n-1, all sources: vertex i lies inside the pairs (s, t)
+    # with s < i < t, i (n - 1 - i) of them.
+    g = gen.from_arcs(n, [(i, i + 1) for i in range(n - 1)])
+    got, _ = oracle.bc(g, range(n), directed=True)
+    assert close(got, [i * (n - 1 - i) for i in range(n)])
+
+
+@pytest.mark.parametrize("n", [3, 4, 9, 50])
+def test_directed_cycle(n):
+    # One path between every ordered pair; a vertex is inside (n - 1)(n - 2) / 2 of them.
+    g = gen.from_arcs(n, [(i, (i + 1) % n) for i in range(n)])
+    got, _ = oracle.bc(g, range(n), directed=True)
+    assert close(got, [Fraction((n - 1) * (n - 2), 2)] * n)
+
+
+def test_symmetric_digraph_equals_undirected_bit_for_bit():
+    # Both directions of every edge stored with sorted rows: the transpose has
+    # the same rows, so the directed pass repeats the undirected arithmetic.
+    for g in [gen.er(500, 2000, 3), gen.rmat(10, 8, 4), gen.grid(30, 31)]:
+        srcs = gen.sources(g, 25, 5)
+        a, _ = oracle.bc(g, srcs)
+        b, _ = oracle.bc(g, srcs, directed=True)
+        assert np.array_equal(a, b)
+
+
+def test_transpose_with_all_sources():
+    # With every vertex a source, reversing every arc maps each ordered pair
+    # (s, t) to (t, s) with the same interior vertices: BC is unchanged.
+    g = gen.rmat_directed(8, 6, 11)
+    a, _ = oracle.bc(g, range(g.n), directed=True)
+    b, _ = oracle.bc(gen.transpose(g), range(g.n), directed=True)
+    assert np.all(np.abs(a - b) <= 1e-12 * np.maximum(np.abs(a), 1))
+    assert not np.allclose(a, oracle.bc(g, range(g.n))[0])  # direction matters on this graph
+
+
+def test_directed_sum_invariant():
+    for g in [gen.rmat_directed(12, 8, 2), gen.from_arcs(6, [(0, 1), (1, 2), (2, 0), (3, 4)])]:
+        srcs = gen.sources(g, min(40, g.n), 6) if g.n > 10 else np.arange(g.n, dtype=np.int32)
+        got, _ = oracle.bc(g, srcs, directed=True)
+        want = oracle.pair_distance_excess(g, srcs)
+        assert abs(got.sum() - want) <= 1e-9 * max(want, 1)

@@ -28,6 +28,9 @@ MUTATIONS = {
     "xf_align_sign": ("a.m + scale2(b.m, -d)", "a.m + scale2(b.m, d)"),
     "xf_ratio_exp": ("scale2(a.m / b.m, a.e - b.e)", "scale2(a.m / b.m, b.e - a.e)"),
     "forward_skips_last": ("for (int64_t i = 1; i < reached; ++i)", "for (int64_t i = 1; i + 1 < reached; ++i)"),
+    "directed_pull_over_out_arcs": ("(*tci)[fill[ci[e]]++] = u;", "(*tci)[fill[ci[e]]++] = ci[e];"),
+    "directed_pulls_out_arcs": ("int rc = bc_over(n, rp, ci, trp, tci, sources, nsrc, mode, bc, stats);",
+                                "int rc = bc_over(n, rp, ci, rp, ci, sources, nsrc, mode, bc, stats);"),
 }
 
 
@@ -40,6 +43,11 @@ def pins_pass(lib) -> bool:
     for seed in range(8):
         g = gen.random_small(7 + seed % 4, 0.4, seed)
         got, _ = oracle.bc(g, range(g.n), lib=lib)
+        if not close(got, bf.bc_exact(g, range(g.n))):
+            return False
+    for seed in range(6):
+        g = gen.random_small_directed(6 + seed % 3, 0.3, seed)
+        got, _ = oracle.bc(g, range(g.n), lib=lib, directed=True)
         if not close(got, bf.bc_exact(g, range(g.n))):
             return False
     n = 9
