@@ -17,8 +17,11 @@
  *
  * Graph input: int32 CSR, row_ptr[n+1] and col_idx[nnz], both directions of
  * every undirected edge stored (the paper's CSR offset array and edge list,
- * Section 3.1).  Rows need not be sorted; a repeated arc counts as a parallel
- * edge and a self-loop is never on a shortest path.
+ * Section 3.1), or the out-arcs of a directed graph (SP_GRAPH_DIRECTED; the
+ * in-arcs are built on the GPU, as the paper's generated code keeps a reverse
+ * CSR for pulls over in-neighbours, Section 3.3, the PageRank listing).  Rows need not be sorted; a
+ * repeated arc counts as a parallel edge and a self-loop is never on a
+ * shortest path.
  *
  * Pointers: every array argument may be host memory or device memory of the
  * current device (device memory of another GPU is refused with
@@ -102,6 +105,7 @@ typedef int64_t sp_request;
 /* Flags for sp_graph_create. */
 #define SP_GRAPH_CHECK_SYMMETRIC 0x1u /* also verify every arc (u,v) has its reverse (v,u) */
 #define SP_GRAPH_SORT_ROWS 0x2u       /* sort every row by neighbour id on the GPU (after the copy) */
+#define SP_GRAPH_DIRECTED 0x4u        /* row v lists the out-arcs v -> w of a directed graph (see below) */
 
 typedef struct {
     int32_t n;
@@ -112,6 +116,8 @@ typedef struct {
     int32_t has_self_loops; /* 1 when some arc (v,v) exists */
     int32_t has_duplicates; /* 1 when some arc appears twice in a row (only detected on sorted rows) */
     int32_t symmetric;      /* 1 yes, 0 no, -1 not checked */
+    int32_t directed;       /* 1 when created with SP_GRAPH_DIRECTED */
+    int32_t reserved;
 } sp_graph_info;
 
 /*
@@ -122,6 +128,14 @@ typedef struct {
  * n >= 0; nnz < 2^31.  Returns SP_ERR_BAD_GRAPH on a CSR that fails, with the
  * first offending index in sp_last_error().  With SP_GRAPH_SORT_ROWS the rows
  * of the copy are sorted (deterministically, on the GPU) before the checks.
+ *
+ * With SP_GRAPH_DIRECTED the CSR holds the arcs of a directed graph (row v:
+ * the heads w of the arcs v -> w) and BC counts directed shortest paths: the
+ * BFS and the dependencies follow out-arcs, path counts are pulled over
+ * in-arcs (BFS parents u -> v).  The library builds each vertex's in-arcs
+ * (the transpose) on the GPU and keeps one combined row per vertex, out-arcs
+ * then in-arcs, so 2 nnz must stay below 2^31 (else SP_ERR_TOO_LARGE);
+ * traversed arcs count out-arcs.  Not with SP_GRAPH_CHECK_SYMMETRIC.
  */
 SP_API sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
                           uint32_t flags, sp_stream stream, sp_graph* out);
@@ -136,9 +150,11 @@ SP_API sp_status sp_graph_sync(sp_graph g, sp_stream stream);
  * and edge list of Section 3.1): for every edge i with src[i] != dst[i] both
  * arcs are stored, rows are sorted by neighbour id and repeated arcs are kept
  * once; self-loops are dropped.  src, dst: int32 [m], host or device, copied
- * before return.  n >= 0 vertices; 2 m < 2^31.  flags: 0 or
- * SP_GRAPH_CHECK_SYMMETRIC.  An endpoint outside [0, n) gives
- * SP_ERR_BAD_GRAPH with the edge index in sp_last_error().  Blocks until done.
+ * before return.  n >= 0 vertices; 2 m < 2^31.  flags: 0,
+ * SP_GRAPH_CHECK_SYMMETRIC, or SP_GRAPH_DIRECTED (each edge i is the single
+ * arc src[i] -> dst[i]; the graph is directed as for sp_graph_create).  An
+ * endpoint outside [0, n) gives SP_ERR_BAD_GRAPH with the edge index in
+ * sp_last_error().  Blocks until done.
  */
 SP_API sp_status sp_graph_from_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, uint32_t flags,
                                      sp_stream stream, sp_graph* out);
@@ -246,7 +262,7 @@ SP_API sp_status sp_bc_ex(sp_graph g, const int32_t* sources, int32_t nsrc, cons
                    sp_bc_stats* stats, sp_stream stream);
 
 /*
- * Hop distances of the forward BFS (Fig. 1, iterateInBFS; Section 3.3 BFS
+ * Hop distances of the forward BFS (Fig. 1, iterateInBFS; Section 3.4 BFS
  * traversal): dist_out[i * n + v] = dist(sources[i], v), -1 when unreachable.
  * dist_out: int32 [nsrc][n], host or device.
  */

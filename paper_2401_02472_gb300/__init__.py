@@ -25,7 +25,7 @@ SP_ERR_RANGE, SP_ERR_TIMEOUT, SP_ERR_CANCELLED, SP_ERR_BAD_GRAPH, SP_ERR_NO_DEVI
 SP_FP64, SP_FP32_DELTA = 0, 1
 SP_FORM_AUTO, SP_FORM_PLAIN, SP_FORM_BATCHED, SP_FORM_SMALL = 0, 1, 2, 3
 SP_DRIVER_AUTO, SP_DRIVER_PERSISTENT, SP_DRIVER_GRAPH = 0, 1, 2
-SP_GRAPH_CHECK_SYMMETRIC, SP_GRAPH_SORT_ROWS = 0x1, 0x2
+SP_GRAPH_CHECK_SYMMETRIC, SP_GRAPH_SORT_ROWS, SP_GRAPH_DIRECTED = 0x1, 0x2, 0x4
 SP_DEBUG_SKIP_BARRIER = 0x1
 SP_DEBUG_PLAIN_RECORDS = 0x2
 SP_DEBUG_PLAIN_ARRAYS = 0x4
@@ -54,10 +54,11 @@ class sp_bc_stats(ctypes.Structure):
 class sp_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("max_degree", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("isolated", ctypes.c_int64), ("sorted_rows", ctypes.c_int32), ("has_self_loops", ctypes.c_int32),
-                ("has_duplicates", ctypes.c_int32), ("symmetric", ctypes.c_int32)]
+                ("has_duplicates", ctypes.c_int32), ("symmetric", ctypes.c_int32), ("directed", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class StarbcError(RuntimeError):

@@ -182,7 +182,8 @@ size_t batched_workspace_bytes(const Graph* g, int width, bool theta_f32) {
     const size_t n = (size_t)g->n, W = (size_t)width / 32, B = (size_t)width;
     const size_t lcap = std::min<size_t>(n + 2, 16384);
     const size_t ecap = std::min<size_t>(std::max<size_t>(8 * n, 1 << 16), n * std::min(B, lcap));
-    const size_t hcap = (size_t)g->nnz / 512 * 8 + 1024, segcap = (size_t)g->nnz / 1024 + (size_t)g->nnz / 512 + 2;
+    const size_t arcs = (size_t)g->knnz();
+    const size_t hcap = arcs / 512 * 8 + 1024, segcap = arcs / 1024 + arcs / 512 + 2;
     return 4 * 4 * n * W + 4 * n * W + 4 * n + 8 * n * B + (theta_f32 ? 4 : 8) * n * B + ecap * (4 + 4 * W) +
            hcap * 24 + segcap * B * 8 + 2 * lcap * B * 4 + 3 * (lcap + 2) * 8 + (1 << 20);
 }
@@ -199,23 +200,23 @@ struct BatchTune {
 static std::map<std::tuple<int32_t, int64_t, int32_t, int32_t>, BatchTune> g_tuned;
 
 static std::tuple<int32_t, int64_t, int32_t, int32_t> tune_key(const Graph* g, int precision) {
-    return std::make_tuple(g->n, g->nnz, g->info.max_degree, (int32_t)precision);
+    return std::make_tuple(g->n, g->nnz, g->info.max_degree, (int32_t)precision | (g->directed ? 0x100 : 0));
 }
 
 // Representation hints learnt by earlier calls on a graph with the same
 // signature: path counts past 64 bits (bit 0), FP32 dependencies out of range
 // (bit 1).  They only skip attempts that would fail and be rerun.
-static std::map<std::tuple<int32_t, int64_t, int32_t>, int> g_hints;
+static std::map<std::tuple<int32_t, int64_t, int32_t, bool>, int> g_hints;
 
 static int range_hints(const Graph* g) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_hints.find(std::make_tuple(g->n, g->nnz, g->info.max_degree));
+    auto it = g_hints.find(std::make_tuple(g->n, g->nnz, g->info.max_degree, g->directed));
     return it == g_hints.end() ? 0 : it->second;
 }
 
 static void add_range_hint(const Graph* g, int bit) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_hints[std::make_tuple(g->n, g->nnz, g->info.max_degree)] |= bit;
+    g_hints[std::make_tuple(g->n, g->nnz, g->info.max_degree, g->directed)] |= bit;
 }
 
 static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
@@ -454,7 +455,7 @@ static sp_status ensure_landmarks(Graph* g, cudaStream_t st) {
 // per block, from the estimated number of levels.
 static int plain_group_blocks(const Graph* g) {
     const int64_t levels = std::max<int64_t>(1, g->top_levels);
-    const int64_t per_level = std::max<int64_t>(1, g->nnz / levels);
+    const int64_t per_level = std::max<int64_t>(1, g->knnz() / levels);
     return (int)std::min<int64_t>((per_level + 8191) / 8192, 1 << 20);
 }
 
@@ -1258,7 +1259,7 @@ static sp_status bc_enqueue(Graph* g, const int32_t* d_src, bool src_checked, in
         L.debug_flags = o.debug_flags;
         L.stream = st;
         if (ecap_mult > 1) L.entry_cap = std::max<int64_t>(8 * (int64_t)g->n, 1 << 16) * ecap_mult;
-        if (hcap_mult > 1) L.hub_cap = ((g->nnz / 64) * 4 + 1024) * hcap_mult;
+        if (hcap_mult > 1) L.hub_cap = ((g->knnz() / 64) * 4 + 1024) * hcap_mult;
         L.bottom_up_den = batch_bu;
         L.async = h;
         rc = run_batched(L, &r);
@@ -1350,7 +1351,12 @@ sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_
     if (nnz >= (int64_t)INT32_MAX) return fail(SP_ERR_TOO_LARGE, "nnz must be below 2^31 (int32 row_ptr)");
     if (!row_ptr) return fail(SP_ERR_INVALID_ARG, "row_ptr is NULL");
     if (nnz > 0 && !col_idx) return fail(SP_ERR_INVALID_ARG, "col_idx is NULL");
-    if (flags & ~(uint32_t)(SP_GRAPH_CHECK_SYMMETRIC | SP_GRAPH_SORT_ROWS)) return fail(SP_ERR_INVALID_ARG, "unknown flag");
+    if (flags & ~(uint32_t)(SP_GRAPH_CHECK_SYMMETRIC | SP_GRAPH_SORT_ROWS | SP_GRAPH_DIRECTED))
+        return fail(SP_ERR_INVALID_ARG, "unknown flag");
+    if ((flags & SP_GRAPH_DIRECTED) && (flags & SP_GRAPH_CHECK_SYMMETRIC))
+        return fail(SP_ERR_INVALID_ARG, "SP_GRAPH_CHECK_SYMMETRIC does not apply to a directed graph");
+    if ((flags & SP_GRAPH_DIRECTED) && 2 * nnz >= (int64_t)INT32_MAX)
+        return fail(SP_ERR_TOO_LARGE, "a directed graph needs 2 nnz below 2^31 (out- and in-arc rows)");
     sp_status rc = check_device();
     if (rc == SP_OK) rc = refuse_other_device({row_ptr, col_idx}, "sp_graph_create");
     if (rc != SP_OK) return rc;
@@ -1362,6 +1368,9 @@ sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_
     auto cleanup = [&](sp_status s) {
         if (g->d_rp) cudaFree(g->d_rp);
         if (g->d_ci) cudaFree(g->d_ci);
+        if (g->d_crp) cudaFree(g->d_crp);
+        if (g->d_cci) cudaFree(g->d_cci);
+        if (g->d_odeg) cudaFree(g->d_odeg);
         delete g;
         return s;
     };
@@ -1387,8 +1396,13 @@ sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_
     }
     rc = validate_graph(g, flags & SP_GRAPH_CHECK_SYMMETRIC, st, &detail);
     if (rc == SP_ERR_BAD_GRAPH) return cleanup(fail(rc, detail));
+    if (rc == SP_OK && (flags & SP_GRAPH_DIRECTED)) {
+        rc = combined_rows(g->d_rp, g->d_ci, n, nnz, st, &g->d_crp, &g->d_cci, &g->d_odeg);
+        g->directed = rc == SP_OK;
+    }
     if (rc == SP_OK) rc = alloc_flags(g);
     if (rc != SP_OK) return cleanup(rc);
+    g->info.directed = g->directed ? 1 : 0;
     *out = reinterpret_cast<sp_graph>(g);
     return SP_OK;
 }
@@ -1401,7 +1415,10 @@ sp_status sp_graph_from_edges(const int32_t* src, const int32_t* dst, int64_t m,
     if (n < 0 || m < 0) return fail(SP_ERR_INVALID_ARG, "negative size");
     if (m > 0 && (!src || !dst)) return fail(SP_ERR_INVALID_ARG, "edge arrays are NULL");
     if (2 * m >= (int64_t)INT32_MAX) return fail(SP_ERR_TOO_LARGE, "2 m must be below 2^31 (int32 row_ptr)");
-    if (flags & ~(uint32_t)SP_GRAPH_CHECK_SYMMETRIC) return fail(SP_ERR_INVALID_ARG, "unknown flag");
+    if (flags & ~(uint32_t)(SP_GRAPH_CHECK_SYMMETRIC | SP_GRAPH_DIRECTED)) return fail(SP_ERR_INVALID_ARG, "unknown flag");
+    if ((flags & SP_GRAPH_DIRECTED) && (flags & SP_GRAPH_CHECK_SYMMETRIC))
+        return fail(SP_ERR_INVALID_ARG, "SP_GRAPH_CHECK_SYMMETRIC does not apply to a directed graph");
+    const bool directed = (flags & SP_GRAPH_DIRECTED) != 0;
     sp_status rc = check_device();
     if (rc == SP_OK) rc = refuse_other_device({src, dst}, "sp_graph_from_edges");
     if (rc != SP_OK) return rc;
@@ -1432,15 +1449,23 @@ sp_status sp_graph_from_edges(const int32_t* src, const int32_t* dst, int64_t m,
     cudaGetDevice(&g->device);
     g->n = n;
     std::string detail;
-    rc = csr_from_edges(d_src, d_dst, m, n, st, &g->d_rp, &g->d_ci, &g->nnz, &detail);
-    if (rc == SP_OK) rc = validate_graph(g, flags, st, &detail);
+    rc = csr_from_edges(d_src, d_dst, m, n, directed, st, &g->d_rp, &g->d_ci, &g->nnz, &detail);
+    if (rc == SP_OK) rc = validate_graph(g, flags & SP_GRAPH_CHECK_SYMMETRIC, st, &detail);
+    if (rc == SP_OK && directed) {
+        rc = combined_rows(g->d_rp, g->d_ci, n, g->nnz, st, &g->d_crp, &g->d_cci, &g->d_odeg);
+        g->directed = rc == SP_OK;
+    }
     if (rc == SP_OK) rc = alloc_flags(g);
     if (rc != SP_OK) {
         if (g->d_rp) cudaFree(g->d_rp);
         if (g->d_ci) cudaFree(g->d_ci);
+        if (g->d_crp) cudaFree(g->d_crp);
+        if (g->d_cci) cudaFree(g->d_cci);
+        if (g->d_odeg) cudaFree(g->d_odeg);
         delete g;
         return rc == SP_ERR_BAD_GRAPH ? fail(rc, detail) : rc;
     }
+    g->info.directed = g->directed ? 1 : 0;
     *out = reinterpret_cast<sp_graph>(g);
     return SP_OK;
 }
@@ -1471,6 +1496,9 @@ sp_status sp_graph_destroy(sp_graph gh) {
     destroy_step_cache(g);
     cudaFree(g->d_rp);  // waits for work still running on the graph
     cudaFree(g->d_ci);
+    if (g->d_crp) cudaFree(g->d_crp);
+    if (g->d_cci) cudaFree(g->d_cci);
+    if (g->d_odeg) cudaFree(g->d_odeg);
     if (g->flags_host) cudaFreeHost(g->flags_host);
     delete g;
     return SP_OK;

@@ -1,7 +1,7 @@
 // Batched form: B = 32*W sources per batch traverse the graph together.
 //
 // Same method as the plain form (paper Section 2, Fig. 1, ComputeBC; level-
-// synchronous BFS of Section 3.3), with many sources sharing each adjacency
+// synchronous BFS of Section 3.4), with many sources sharing each adjacency
 // scan (the sourceSet loop of Fig. 1 run in parallel instead of in sequence):
 //
 //   per vertex v:          seen[v]    B-bit mask of sources that reached v
@@ -84,6 +84,8 @@ struct BatchArgs {
     unsigned long long* word_stats;  // [nsrc / 32][2]
     int bu_den;  // bottom-up discovery on levels with more than n / bu_den entries (0 = never)
     int centre_bound;  // FP64 path counts: recentre a level whose exponents leave [-bound, bound]
+    int directed;      // rp/ci: combined out- and in-arc rows (arc_in / arc_out); odeg: out-degrees
+    const int32_t* odeg;
 };
 
 template <int W>
@@ -419,13 +421,14 @@ struct BatchKernel {
             if (!hubent) {
                 beg = __ldg(&a.rp[v]);
                 deg = __ldg(&a.rp[v + 1]) - beg;
+                const int tdeg = a.odeg != nullptr ? __ldg(&a.odeg[v]) : deg;  // traversed: out-arcs
                 int pc = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) pc += __popc(F[k]);
-                stat(0, (unsigned long long)deg * (unsigned long long)pc);
+                stat(0, (unsigned long long)tdeg * (unsigned long long)pc);
                 stat(1, (unsigned long long)pc);
                 stat(3, (unsigned long long)deg);
-                if (wst != nullptr) count_words((unsigned long long)deg, F);
+                if (wst != nullptr) count_words((unsigned long long)tdeg, F);
             }
         }
         const int incl = warp_incl_scan(deg);
@@ -454,15 +457,16 @@ struct BatchKernel {
             for (int k = 0; k < W; ++k) { Fj[k] = __shfl_sync(kFull, F[k], j); m[k] = 0u; }
             int u = 0;
             if (has) {
-                u = __ldg(&a.ci[bj + (ai - exj)]);
-                if (d > 0) {
+                const int raw = __ldg(&a.ci[bj + (ai - exj)]);
+                u = arc_vertex(raw);
+                if (d > 0 && arc_in(raw, a.directed)) {
                     uint32_t p[W];
                     load_mask<W>(prev + (size_t)u * W, p);
 #pragma unroll
                     for (int k = 0; k < W; ++k) { m[k] = Fj[k] & p[k]; dag += __popc(m[k]); }
                 }
                 mark(0);
-                if (discover_on) discover(u, Fj);
+                if (discover_on && arc_out(raw)) discover(u, Fj);
                 mark(6);
             }
             if (d > 0) {
@@ -518,15 +522,16 @@ struct BatchKernel {
             for (int k = 0; k < W; ++k) m[k] = 0u;
             int u = 0;
             if (has) {
-                u = __ldg(&a.ci[ai]);
-                if (d > 0) {
+                const int raw = __ldg(&a.ci[ai]);
+                u = arc_vertex(raw);
+                if (d > 0 && arc_in(raw, a.directed)) {
                     uint32_t p[W];
                     load_mask<W>(prev + (size_t)u * W, p);
 #pragma unroll
                     for (int k = 0; k < W; ++k) { m[k] = F[k] & p[k]; dag += __popc(m[k]); }
                 }
                 mark(1);
-                if (discover_on) discover(u, F);
+                if (discover_on && arc_out(raw)) discover(u, F);
                 mark(6);
             }
             if (d > 0) {
@@ -543,12 +548,13 @@ struct BatchKernel {
         stat(4, dag);
         auto count_entry = [&]() {
             if (lane == 0) {
+                const int tdeg = a.odeg != nullptr ? __ldg(&a.odeg[hv]) : re - rb;  // traversed: out-arcs
                 int pc = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) pc += __popc(F[k]);
-                stat(0, (unsigned long long)(re - rb) * (unsigned long long)pc);
+                stat(0, (unsigned long long)tdeg * (unsigned long long)pc);
                 stat(1, (unsigned long long)pc);
-                if (wst != nullptr) count_words((unsigned long long)(re - rb), F);
+                if (wst != nullptr) count_words((unsigned long long)tdeg, F);
             }
         };
         if (nseg == 1) {  // the whole row in one segment: no partial sums
@@ -608,8 +614,10 @@ struct BatchKernel {
         }
         if (any && deg <= 32) {
             for (int e = 0; e < deg; ++e) {
+                const int raw = __ldg(&a.ci[rb + e]);
+                if (!arc_in(raw, a.directed)) continue;  // only an arc into u can reach it
                 uint32_t f[W];
-                load_mask<W>(cur + (size_t)__ldg(&a.ci[rb + e]) * W, f);
+                load_mask<W>(cur + (size_t)arc_vertex(raw) * W, f);
                 bool done = true;
 #pragma unroll
                 for (int k = 0; k < W; ++k) { got[k] |= f[k] & unseen[k]; done &= got[k] == unseen[k]; }
@@ -625,8 +633,10 @@ struct BatchKernel {
 #pragma unroll
             for (int k = 0; k < W; ++k) { uns[k] = __shfl_sync(kFull, unseen[k], j); g2[k] = 0u; }
             for (int e = lane; e < dj; e += kWarp) {
+                const int raw = __ldg(&a.ci[bj + e]);
+                if (!arc_in(raw, a.directed)) continue;
                 uint32_t f[W];
-                load_mask<W>(cur + (size_t)__ldg(&a.ci[bj + e]) * W, f);
+                load_mask<W>(cur + (size_t)arc_vertex(raw) * W, f);
 #pragma unroll
                 for (int k = 0; k < W; ++k) g2[k] |= f[k] & uns[k];
             }
@@ -699,8 +709,9 @@ struct BatchKernel {
             for (int k = 0; k < W; ++k) m[k] = 0u;
             int w = 0;
             if (has) {
-                w = __ldg(&a.ci[bj + (ai - exj)]);
-                load_mask<W>(next + (size_t)w * W, m);
+                const int raw = __ldg(&a.ci[bj + (ai - exj)]);
+                w = arc_vertex(raw);
+                if (arc_out(raw)) load_mask<W>(next + (size_t)w * W, m);  // children: out-arcs
             }
             uint32_t anym = 0;
 #pragma unroll
@@ -751,11 +762,14 @@ struct BatchKernel {
 #pragma unroll
             for (int k = 0; k < W; ++k) m[k] = 0u;
             if (has) {
-                w = __ldg(&a.ci[ai]);
-                uint32_t c[W];
-                load_mask<W>(next + (size_t)w * W, c);
+                const int raw = __ldg(&a.ci[ai]);
+                w = arc_vertex(raw);
+                if (arc_out(raw)) {  // children: out-arcs
+                    uint32_t c[W];
+                    load_mask<W>(next + (size_t)w * W, c);
 #pragma unroll
-                for (int k = 0; k < W; ++k) { m[k] = c[k] & F[k]; anym |= m[k]; }
+                    for (int k = 0; k < W; ++k) { m[k] = c[k] & F[k]; anym |= m[k]; }
+                }
             }
             const unsigned pend = __ballot_sync(kFull, anym != 0u);
             mark(3);

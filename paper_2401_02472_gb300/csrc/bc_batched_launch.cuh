@@ -36,9 +36,10 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     int64_t ecap_max = n * std::min<int64_t>(B, lcap);
     int64_t ecap = L.entry_cap > 0 ? L.entry_cap : std::max<int64_t>(8 * n, 1 << 16);
     ecap = std::max<int64_t>(1, std::min(ecap, ecap_max));
-    int64_t hcap = L.hub_cap > 0 ? L.hub_cap : (g->nnz / t_hub) * 4 + 1024;
-    int64_t segcap = g->nnz / seg + g->nnz / t_hub + 2;              // segments of one level
-    int64_t scap = L.hub_cap > 0 ? 2 * L.hub_cap + 4 * (g->nnz / seg) : 4 * (g->nnz / seg) + hcap;  // all levels
+    const int64_t arcs = g->knnz();
+    int64_t hcap = L.hub_cap > 0 ? L.hub_cap : (arcs / t_hub) * 4 + 1024;
+    int64_t segcap = arcs / seg + arcs / t_hub + 2;              // segments of one level
+    int64_t scap = L.hub_cap > 0 ? 2 * L.hub_cap + 4 * (arcs / seg) : 4 * (arcs / seg) + hcap;  // all levels
     if (hcap > INT32_MAX || segcap > INT32_MAX || ecap > INT32_MAX || scap > INT32_MAX)
         return fail(SP_ERR_TOO_LARGE, "batched workspace");
     const size_t th_size = L.theta_f32 ? 4 : 8;
@@ -75,8 +76,10 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     if (ce != cudaSuccess) { cudaFreeAsync(ws, st); return cuda_fail(ce, "cudaMemsetAsync"); }
 
     BatchArgs a{};
-    a.rp = g->d_rp;
-    a.ci = g->d_ci;
+    a.rp = g->krp();
+    a.ci = g->kci();
+    a.directed = g->directed;
+    a.odeg = g->d_odeg;
     a.n = (int32_t)n;
     a.sources = L.d_sources;
     a.nsrc = L.nsrc;

@@ -62,8 +62,8 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     // Workspace: one copy of the per-source arrays per group.
     const int64_t lcap = L.level_cap > 0 ? std::min<int64_t>(L.level_cap, n + 2)
                                          : (ngroups == 1 ? n + 2 : std::min<int64_t>(n + 2, 65536));
-    const int64_t hcap = g->nnz / tiers.t_hub + 2;
-    const int64_t segcap = g->nnz / tiers.seg + hcap + 2;
+    const int64_t hcap = g->knnz() / tiers.t_hub + 2;
+    const int64_t segcap = g->knnz() / tiers.seg + hcap + 2;
     const PlainLayout lay = plain_layout(n, lcap, hcap, segcap, ngroups, grid, ngroups > 1 && L.mode == PlainMode::BC, rec);
     const size_t bytes = lay.bytes;
     char* ws = nullptr;
@@ -76,8 +76,10 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     if (ce != cudaSuccess) { cudaFreeAsync(ws, st); return cuda_fail(ce, "cudaMemsetAsync"); }
 
     PlainArgs a{};
-    a.rp = g->d_rp;
-    a.ci = g->d_ci;
+    a.rp = g->krp();
+    a.ci = g->kci();
+    a.directed = g->directed;
+    a.odeg = g->d_odeg;
     a.n = (int32_t)n;
     a.sources = L.d_sources;
     a.nsrc = L.nsrc;

@@ -3,7 +3,7 @@
 //
 // The paper's generated CUDA code runs the BFS and the reverse sweep as a host
 // loop that launches one kernel per level and copies a `finished` flag back
-// after each (Section 3.3, Fig. 10; Section 4.1 blames this loop and the grid
+// after each (Section 3.4, the iterateInBFS listing; Section 4.1 blames this loop and the grid
 // synchronisation for the BC times).  Here the loop stays on the device but
 // keeps the one-kernel-per-level shape: a graph holds one conditional WHILE
 // node whose body is a chain of kUnroll launches of one step kernel.  In each
@@ -312,8 +312,8 @@ sp_status run_plain_graph(const PlainLaunch& L, LaunchResult* result) {
     if (L.max_ctas > 0 && L.max_ctas < grid) grid = L.max_ctas;
 
     const int64_t lcap = L.level_cap > 0 ? std::min<int64_t>(L.level_cap, n + 2) : n + 2;
-    const int64_t hcap = g->nnz / tiers.t_hub + 2;
-    const int64_t segcap = g->nnz / tiers.seg + hcap + 2;
+    const int64_t hcap = g->knnz() / tiers.t_hub + 2;
+    const int64_t segcap = g->knnz() / tiers.seg + hcap + 2;
     const PlainLayout lay = plain_layout(n, lcap, hcap, segcap, 1, grid, false);
     char* ws = nullptr;
     cudaError_t ce = cudaMallocAsync((void**)&ws, lay.bytes, st);
@@ -330,8 +330,10 @@ sp_status run_plain_graph(const PlainLaunch& L, LaunchResult* result) {
 
     StepBlock hb{};
     PlainArgs& a = hb.args;
-    a.rp = g->d_rp;
-    a.ci = g->d_ci;
+    a.rp = g->krp();
+    a.ci = g->kci();
+    a.directed = g->directed;
+    a.odeg = g->d_odeg;
     a.n = (int32_t)n;
     a.sources = L.d_sources;
     a.nsrc = L.nsrc;

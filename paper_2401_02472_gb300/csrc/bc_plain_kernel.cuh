@@ -1,7 +1,7 @@
 // Plain form: one source at a time per group of blocks.
 //
 // Per source (paper Section 2, Fig. 1, ComputeBC; the level-synchronous BFS of
-// Section 3.3) a group of blocks runs
+// Section 3.4) a group of blocks runs
 //   init      level[] = -1, level[src] = 0, sigma[src] = 1
 //   forward   for d = 0, 1, ...: every vertex v at level d pulls sigma from its
 //             neighbours at level d-1 (the iterateInBFS sum over BFS parents)
@@ -12,7 +12,7 @@
 //             BC(v) += delta(v) (the iterateInReverse sum over BFS children,
 //             written so that no floating-point atomics are needed)
 // with a timed barrier over the group's blocks between levels instead of the
-// paper's host loop that copies a `finished` flag every level (Section 3.3;
+// paper's host loop that copies a `finished` flag every level (Section 3.4;
 // Section 4.1).
 //
 // Groups: the persistent launch is cut into `ngroups` groups of `gblocks`
@@ -101,6 +101,8 @@ struct PlainArgs {
     // [-centre_bound, centre_bound] (0 = 512).  With FP32 theta the host passes
     // 64, so that theta-hat = (1 + delta) / sigma-hat stays in FP32 normals.
     int centre_bound;
+    int directed;           // rp/ci: combined out- and in-arc rows (arc_in / arc_out); odeg: out-degrees
+    const int32_t* odeg;
     int* trace;  // SP_TRACE builds: 8 ints per warp
 };
 
@@ -326,19 +328,25 @@ struct PlainKernel {
         }
     }
 
-    // Forward visit of arc (v, u) by a vertex v at level d, u's level already
-    // loaded as lu: claim u for level d+1, or return sigma[u] if u is a parent.
-    __device__ __forceinline__ SigT fwd_visit(int u, int lu) {
+    // Forward visit of the arc `raw` of a vertex v at level d (its other end
+    // u, u's level already loaded as lu): claim u for level d+1 over an arc
+    // out of v, or return sigma[u] if u is a parent over an arc into v.
+    __device__ __forceinline__ SigT fwd_visit(int raw, int lu) {
+        const int u = arc_vertex(raw);
         SigT c = 0;
         if (lu < 0) {
-            if (discover && atomicCAS(&lv(u), -1, d + 1) == -1) push(u, d + 1);
-        } else if (lu == d - 1) {
+            if (discover && arc_out(raw) && atomicCAS(&lv(u), -1, d + 1) == -1) push(u, d + 1);
+        } else if (lu == d - 1 && arc_in(raw, a.directed)) {
             c = __ldcg(&sg(u));
             st_dag += 1;
         }
         return c;
     }
-    __device__ __forceinline__ SigT fwd_arc(int u) { return fwd_visit(u, __ldcg(&lv(u))); }
+    __device__ __forceinline__ SigT fwd_arc(int raw) { return fwd_visit(raw, __ldcg(&lv(arc_vertex(raw)))); }
+    // Out-degree of v (traversed arcs); an undirected graph's row length.
+    __device__ __forceinline__ int out_degree(int v, int row_len) const {
+        return a.odeg != nullptr ? __ldg(&a.odeg[v]) : row_len;
+    }
 
     __device__ void fwd_finalize(int v, SigT acc, int deg) {
         st_arcs += (unsigned long long)deg;
@@ -356,7 +364,9 @@ struct PlainKernel {
         }
     }
 
-    __device__ __forceinline__ double bwd_arc(int w) {
+    __device__ __forceinline__ double bwd_arc(int raw) {
+        if (!arc_out(raw)) return 0.0;  // children: out-arcs only
+        const int w = arc_vertex(raw);
         int lw = __ldcg(&lv(w));
         return lw == d + 1 ? (double)__ldcg(&tt(w)) : 0.0;
     }
@@ -412,8 +422,14 @@ struct PlainKernel {
             constexpr int G = 4;
             for (int k0 = 0; k0 < walk; k0 += G) {
                 int u[G], lu[G];
+                bool out[G], in[G];  // the arc leads out of v (claims, children) / into v (parents)
 #pragma unroll
-                for (int i = 0; i < G; ++i) u[i] = k0 + i < walk ? __ldg(&a.ci[beg + k0 + i]) : -1;
+                for (int i = 0; i < G; ++i) {
+                    const int raw = k0 + i < walk ? __ldg(&a.ci[beg + k0 + i]) : 0;
+                    u[i] = k0 + i < walk ? arc_vertex(raw) : -1;
+                    out[i] = u[i] >= 0 && arc_out(raw);
+                    in[i] = u[i] >= 0 && arc_in(raw, a.directed);
+                }
 #pragma unroll
                 for (int i = 0; i < G; ++i) lu[i] = u[i] >= 0 ? __ldcg(&lv(u[i])) : INT_MIN;
                 if constexpr (FWD) {
@@ -425,8 +441,8 @@ struct PlainKernel {
 #pragma unroll
                     for (int i = 0; i < G; ++i) {
                         c[i] = (SigT)0;
-                        claim[i] = discover && u[i] >= 0 && lu[i] < 0;
-                        if (u[i] >= 0 && lu[i] >= 0 && lu[i] == d - 1) {  // a parent (none on level 0)
+                        claim[i] = discover && out[i] && lu[i] < 0;
+                        if (in[i] && lu[i] >= 0 && lu[i] == d - 1) {  // a parent (none on level 0)
                             c[i] = __ldcg(&sg(u[i]));
                             st_dag += 1;
                         }
@@ -448,7 +464,7 @@ struct PlainKernel {
                 } else {
                     double t[G];
 #pragma unroll
-                    for (int i = 0; i < G; ++i) t[i] = lu[i] == d + 1 ? (double)__ldcg(&tt(u[i])) : 0.0;
+                    for (int i = 0; i < G; ++i) t[i] = out[i] && lu[i] == d + 1 ? (double)__ldcg(&tt(u[i])) : 0.0;
 #pragma unroll
                     for (int i = 0; i < G; ++i) tacc += t[i];
                 }
@@ -462,9 +478,9 @@ struct PlainKernel {
             SigT sp_ = 0;
             double tp = 0.0;
             for (int k = lane; k < dj; k += kWarp) {
-                int u = __ldg(&a.ci[bj + k]);
-                if constexpr (FWD) sp_ = SigOps<SigT>::add(sp_, fwd_arc(u), ovf);
-                else tp += bwd_arc(u);
+                const int raw = __ldg(&a.ci[bj + k]);
+                if constexpr (FWD) sp_ = SigOps<SigT>::add(sp_, fwd_arc(raw), ovf);
+                else tp += bwd_arc(raw);
             }
             if constexpr (FWD) {
                 sp_ = SigOps<SigT>::warp_sum(sp_, ovf);
@@ -476,7 +492,7 @@ struct PlainKernel {
         }
         if (valid && !hubent) {
             st_scanned += (unsigned long long)walk;
-            if constexpr (FWD) fwd_finalize(v, sacc, deg);
+            if constexpr (FWD) fwd_finalize(v, sacc, out_degree(v, deg));
             else bwd_finalize(v, tacc);
         }
     }
@@ -501,9 +517,9 @@ struct PlainKernel {
         SigT sp_ = 0;
         double tp = 0.0;
         for (int k = beg + lane; k < end; k += kWarp) {
-            int u = __ldg(&a.ci[k]);
-            if constexpr (FWD) sp_ = SigOps<SigT>::add(sp_, fwd_arc(u), ovf);
-            else tp += bwd_arc(u);
+            const int raw = __ldg(&a.ci[k]);
+            if constexpr (FWD) sp_ = SigOps<SigT>::add(sp_, fwd_arc(raw), ovf);
+            else tp += bwd_arc(raw);
         }
         if (lane == 0) st_scanned += (unsigned long long)(end - beg);
         int* done = FWD ? &hdone()[r] : &hdone()[a.hcap + r];
@@ -531,7 +547,7 @@ struct PlainKernel {
         }
         if constexpr (FWD) {
             st = SigOps<SigT>::warp_sum(st, ovf);
-            if (lane == 0) fwd_finalize(h.v, st, re - rb);
+            if (lane == 0) fwd_finalize(h.v, st, out_degree(h.v, re - rb));
         } else {
             tt = warp_sum_f64(tt);
             if (lane == 0) bwd_finalize(h.v, tt);
@@ -551,7 +567,9 @@ struct PlainKernel {
                 const int b = __ldg(&a.rp[u]), e = __ldg(&a.rp[u + 1]);
                 for (int k = b; k < e; ++k) {
                     st_scanned += 1;
-                    if (__ldcg(&lv(__ldg(&a.ci[k]))) == d) {
+                    const int raw = __ldg(&a.ci[k]);
+                    if (!arc_in(raw, a.directed)) continue;  // only an arc into u can reach it
+                    if (__ldcg(&lv(arc_vertex(raw))) == d) {
                         lv(u) = d + 1;
                         push(u, d + 1);
                         break;

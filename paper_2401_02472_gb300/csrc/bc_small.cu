@@ -4,7 +4,7 @@
 // For graphs whose per-vertex state fits in one block's shared memory (16 B
 // per vertex: level, a slot holding sigma and then theta, and the level
 // stack), each block runs whole sources on its own (paper Section 2, Fig. 1,
-// ComputeBC; level-synchronous BFS of Section 3.3) with __syncthreads as the
+// ComputeBC; level-synchronous BFS of Section 3.4) with __syncthreads as the
 // level barrier, so a level costs shared-memory latency instead of a grid
 // barrier and global round trips.  The CSR is read through the caches.
 //
@@ -49,6 +49,8 @@ struct SmallArgs {
     int32_t* qoff;    // [gridDim.x][n + 2] level offsets per block
     Ctl* ctl;
     const int* pre_err;  // asynchronous calls: nonzero = the sources failed their check, do nothing
+    int directed;        // rp/ci: combined out- and in-arc rows (arc_in / arc_out); odeg: out-degrees
+    const int32_t* odeg;
 };
 
 // Shared-memory bytes of one block for n vertices.
@@ -119,16 +121,19 @@ __global__ void __launch_bounds__(kSmallThreads, 2) small_kernel(SmallArgs a) {
                 if (valid) {
                     beg = __ldg(&a.rp[v]);
                     deg = __ldg(&a.rp[v + 1]) - beg;
-                    st_arcs += (unsigned long long)deg;
+                    st_arcs += (unsigned long long)(a.odeg != nullptr ? __ldg(&a.odeg[v]) : deg);
                     st_reached += 1;
                     st_scanned += (unsigned long long)deg;
                 }
                 unsigned long long acc = 0;
-                auto visit = [&](int u) -> unsigned long long {
+                // arc `raw` of v: claim its other end over an arc out of v, or
+                // take its path count over an arc into v from level d-1
+                auto visit = [&](int raw) -> unsigned long long {
+                    const int u = arc_vertex(raw);
                     const int lu = lvl[u];
                     if (lu < 0) {
-                        if (atomicCAS(&lvl[u], -1, d + 1) == -1) q[atomicAdd(&s_qtail, 1)] = u;
-                    } else if (lu == d - 1) {
+                        if (arc_out(raw) && atomicCAS(&lvl[u], -1, d + 1) == -1) q[atomicAdd(&s_qtail, 1)] = u;
+                    } else if (lu == d - 1 && arc_in(raw, a.directed)) {
                         st_dag += 1;
                         return slot[u];
                     }
@@ -140,10 +145,10 @@ __global__ void __launch_bounds__(kSmallThreads, 2) small_kernel(SmallArgs a) {
                     for (int k0 = 0; k0 < deg; k0 += 8) {
                         int u[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) u[i] = k0 + i < deg ? __ldg(&a.ci[beg + k0 + i]) : -1;
+                        for (int i = 0; i < 8; ++i) u[i] = k0 + i < deg ? __ldg(&a.ci[beg + k0 + i]) : 0;
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            if (u[i] < 0) continue;
+                            if (k0 + i >= deg) continue;
                             const unsigned long long c = visit(u[i]);
                             const unsigned long long s = acc + c;
                             ovf |= s < acc;
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2) small_kernel(SmallArgs a) {
 #pragma unroll
                         for (int i = 0; i < 8; ++i) w[i] = k0 + i < deg ? __ldg(&a.ci[beg + k0 + i]) : -1;
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
+                        for (int i = 0; i < 8; ++i)  // children: out-arcs (an in-arc is negative here)
                             if (w[i] >= 0 && lvl[w[i]] == dd + 1) acc += theta_of(w[i]);
                     }
                 }
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2) small_kernel(SmallArgs a) {
                     double p = 0.0;
                     for (int k = lane; k < dj; k += 32) {
                         const int w = __ldg(&a.ci[bj + k]);
-                        if (lvl[w] == dd + 1) p += theta_of(w);
+                        if (arc_out(w) && lvl[w] == dd + 1) p += theta_of(w);
                     }
                     p = warp_sum_f64(p);
                     if (lane == j) acc = p;
@@ -344,8 +349,10 @@ sp_status run_small(const SmallLaunch& L, LaunchResult* result) {
     SP_CUDA(cudaMemsetAsync(ws, 0, sizeof(Ctl), st));
 
     SmallArgs a{};
-    a.rp = g->d_rp;
-    a.ci = g->d_ci;
+    a.rp = g->krp();
+    a.ci = g->kci();
+    a.directed = g->directed;
+    a.odeg = g->d_odeg;
     a.n = (int32_t)n;
     a.sources = L.d_sources;
     a.nsrc = L.nsrc;

@@ -51,6 +51,17 @@ struct Ctl {
     int block_phase[1024];           // last barrier each block arrived at (diagnostics)
 };
 
+// Directed graphs: the kernels read a combined CSR whose row v lists v's
+// out-arcs and then its in-arcs, an in-arc's column id tagged with the top
+// bit.  arc_vertex strips the tag.  An untagged arc leads out of v (discovery
+// and the backward sum over children); an arc leads into v (the forward sum
+// over parents, bottom-up discovery) when it is tagged or when the graph is
+// undirected, whose untagged arcs serve both ways.
+constexpr int kArcVertex = 0x7FFFFFFF;
+__device__ __forceinline__ int arc_vertex(int raw) { return raw & kArcVertex; }
+__device__ __forceinline__ bool arc_out(int raw) { return raw >= 0; }
+__device__ __forceinline__ bool arc_in(int raw, bool directed) { return !directed || raw < 0; }
+
 struct HubRec {
     int32_t v;        // vertex id
     int32_t qpos;     // its index in the level stack

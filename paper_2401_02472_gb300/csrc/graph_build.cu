@@ -176,25 +176,70 @@ __global__ void scan_add_kernel(int32_t* __restrict__ out, int64_t count, const 
 }
 
 // Edge list: endpoint check and per-row arc counts (both directions, no loops).
+// Edge list: endpoint check and per-row arc counts (both directions, or only
+// src -> dst for a directed graph; no loops).
 __global__ void edge_count_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                                  int32_t n, int32_t* __restrict__ deg, unsigned long long* __restrict__ bad) {
+                                  int32_t n, bool directed, int32_t* __restrict__ deg,
+                                  unsigned long long* __restrict__ bad) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const int u = src[i], v = dst[i];
         if (u < 0 || u >= n || v < 0 || v >= n) { atomicMin(bad, (unsigned long long)i); continue; }
         if (u == v) continue;
         atomicAdd(&deg[u], 1);
-        atomicAdd(&deg[v], 1);
+        if (!directed) atomicAdd(&deg[v], 1);
     }
 }
 
 __global__ void edge_scatter_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                                    const int32_t* __restrict__ rp, int32_t* __restrict__ fill,
+                                    bool directed, const int32_t* __restrict__ rp, int32_t* __restrict__ fill,
                                     int32_t* __restrict__ ci) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const int u = src[i], v = dst[i];
         if (u == v) continue;
         ci[rp[u] + atomicAdd(&fill[u], 1)] = v;
-        ci[rp[v] + atomicAdd(&fill[v], 1)] = u;
+        if (!directed) ci[rp[v] + atomicAdd(&fill[v], 1)] = u;
+    }
+}
+
+// Directed graphs: in-degree of every vertex (arc count per target).
+__global__ void in_count_kernel(const int32_t* __restrict__ ci, int64_t nnz, int32_t* __restrict__ indeg) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&indeg[ci[e]], 1);
+}
+
+// Directed graphs: the in-arc rows (warp per source row), in arrival order;
+// sorted afterwards.
+__global__ void in_scatter_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
+                                  const int32_t* __restrict__ irp, int32_t* __restrict__ fill,
+                                  int32_t* __restrict__ ici) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (int u = warp; u < n; u += nwarp)
+        for (int e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+            const int v = ci[e];
+            ici[irp[v] + atomicAdd(&fill[v], 1)] = u;
+        }
+}
+
+// Directed graphs: combined row v = v's out-arcs, then its in-arcs tagged
+// with the top bit; crp = rp + irp; odeg = out-degrees (warp per row).
+__global__ void combine_rows_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                    const int32_t* __restrict__ irp, const int32_t* __restrict__ ici, int32_t n,
+                                    int32_t* __restrict__ crp, int32_t* __restrict__ cci,
+                                    int32_t* __restrict__ odeg) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (int v = warp; v <= n; v += nwarp) {
+        const int base = rp[v] + irp[v];
+        if (lane == 0) crp[v] = base;
+        if (v == n) continue;
+        const int ob = rp[v], od = rp[v + 1] - ob;
+        const int ib = irp[v], id = irp[v + 1] - ib;
+        if (lane == 0) odeg[v] = od;
+        for (int k = lane; k < od; k += 32) cci[base + k] = ci[ob + k];
+        for (int k = lane; k < id; k += 32) cci[base + od + k] = (int)((unsigned)ici[ib + k] | 0x80000000u);
     }
 }
 
@@ -370,8 +415,9 @@ sp_status sort_rows_device(const int32_t* d_rp, int32_t* d_ci, int32_t n, int64_
 
 // Symmetric, deduplicated CSR from an edge list, on the device.  On success
 // *d_rp_out / *d_ci_out are cudaMalloc allocations the caller owns.
-sp_status csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, cudaStream_t st,
-                         int32_t** d_rp_out, int32_t** d_ci_out, int64_t* nnz_out, std::string* detail) {
+sp_status csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, bool directed,
+                         cudaStream_t st, int32_t** d_rp_out, int32_t** d_ci_out, int64_t* nnz_out,
+                         std::string* detail) {
     *d_rp_out = nullptr;
     *d_ci_out = nullptr;
     *nnz_out = 0;
@@ -391,7 +437,7 @@ sp_status csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, 
     SP_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * ((size_t)n + 1), st));
     SP_CUDA(cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), st));
     if (m > 0) {
-        edge_count_kernel<<<egrid, 256, 0, st>>>(d_src, d_dst, m, n, deg, bad);
+        edge_count_kernel<<<egrid, 256, 0, st>>>(d_src, d_dst, m, n, directed, deg, bad);
         SP_CUDA(cudaGetLastError());
     }
     unsigned long long hbad = 0;
@@ -414,7 +460,7 @@ sp_status csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, 
     fr.p.push_back(ci0);
     SP_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * ((size_t)n + 1), st));
     if (m > 0) {
-        edge_scatter_kernel<<<egrid, 256, 0, st>>>(d_src, d_dst, m, rp0, fill, ci0);
+        edge_scatter_kernel<<<egrid, 256, 0, st>>>(d_src, d_dst, m, directed, rp0, fill, ci0);
         SP_CUDA(cudaGetLastError());
     }
     rc = sort_rows_device(rp0, ci0, n, arcs, st);
@@ -448,6 +494,66 @@ sp_status csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, 
     *d_rp_out = rp;
     *d_ci_out = ci;
     *nnz_out = nnz;
+    return SP_OK;
+}
+
+// Directed graphs: the combined rows the kernels read (out-arcs, then in-arcs
+// tagged with the top bit, in increasing source id) and the out-degrees, built
+// on the device from the out-arc CSR.  The three outputs are cudaMalloc
+// allocations the caller owns.  2 nnz must be below 2^31.
+sp_status combined_rows(const int32_t* d_rp, const int32_t* d_ci, int32_t n, int64_t nnz, cudaStream_t st,
+                        int32_t** d_crp, int32_t** d_cci, int32_t** d_odeg) {
+    *d_crp = *d_cci = *d_odeg = nullptr;
+    if (2 * nnz >= (int64_t)INT32_MAX) return fail(SP_ERR_TOO_LARGE, "directed graphs need 2 nnz below 2^31");
+    const int sms = current_sms();
+    int32_t *indeg = nullptr, *irp = nullptr, *fill = nullptr, *ici = nullptr;
+    struct Free {
+        std::vector<void*> p;
+        cudaStream_t s;
+        ~Free() { for (void* x : p) if (x) cudaFreeAsync(x, s); }
+    } fr{{}, st};
+    SP_CUDA(cudaMallocAsync((void**)&indeg, sizeof(int32_t) * ((size_t)n + 1), st));
+    fr.p.push_back(indeg);
+    SP_CUDA(cudaMallocAsync((void**)&irp, sizeof(int32_t) * ((size_t)n + 1), st));
+    fr.p.push_back(irp);
+    SP_CUDA(cudaMallocAsync((void**)&fill, sizeof(int32_t) * ((size_t)n + 1), st));
+    fr.p.push_back(fill);
+    SP_CUDA(cudaMallocAsync((void**)&ici, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1), st));
+    fr.p.push_back(ici);
+    SP_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * ((size_t)n + 1), st));
+    SP_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * ((size_t)n + 1), st));
+    const int egrid = (int)std::max<int64_t>(1, std::min<int64_t>((nnz + 255) / 256, (int64_t)sms * 8));
+    const int wgrid = std::max(1, std::min((n + 8) / 8, sms * 16));
+    if (nnz > 0) in_count_kernel<<<egrid, 256, 0, st>>>(d_ci, nnz, indeg);
+    SP_CUDA(cudaGetLastError());
+    sp_status rc = exclusive_scan(indeg, n, irp, st);
+    if (rc != SP_OK) return rc;
+    if (n > 0) in_scatter_kernel<<<wgrid, 256, 0, st>>>(d_rp, d_ci, n, irp, fill, ici);
+    SP_CUDA(cudaGetLastError());
+    rc = sort_rows_device(irp, ici, n, nnz, st);
+    if (rc != SP_OK) return rc;
+    int32_t *crp = nullptr, *cci = nullptr, *odeg = nullptr;
+    if (cudaMalloc((void**)&crp, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&cci, sizeof(int32_t) * (size_t)std::max<int64_t>(2 * nnz, 1)) != cudaSuccess ||
+        cudaMalloc((void**)&odeg, sizeof(int32_t) * (size_t)std::max<int32_t>(n, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(crp);
+        cudaFree(cci);
+        cudaFree(odeg);
+        return fail(SP_ERR_OOM, "directed graph rows");
+    }
+    combine_rows_kernel<<<wgrid, 256, 0, st>>>(d_rp, d_ci, irp, ici, n, crp, cci, odeg);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(crp);
+        cudaFree(cci);
+        cudaFree(odeg);
+        return cuda_fail(e, "directed graph rows");
+    }
+    *d_crp = crp;
+    *d_cci = cci;
+    *d_odeg = odeg;
     return SP_OK;
 }
 

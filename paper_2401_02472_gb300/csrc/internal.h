@@ -52,6 +52,16 @@ struct Graph {
     int32_t* d_rp = nullptr;  // [n+1]
     int32_t* d_ci = nullptr;  // [max(nnz,1)]
     sp_graph_info info{};
+    // Directed graphs: the kernels read combined rows (out-arcs, then in-arcs
+    // tagged with the top bit) and count traversed arcs by out-degree.  For an
+    // undirected graph the kernels read d_rp / d_ci themselves.
+    bool directed = false;
+    int32_t* d_crp = nullptr;   // [n+1]
+    int32_t* d_cci = nullptr;   // [2 nnz]
+    int32_t* d_odeg = nullptr;  // [n]
+    const int32_t* krp() const { return directed ? d_crp : d_rp; }
+    const int32_t* kci() const { return directed ? d_cci : d_ci; }
+    int64_t knnz() const { return directed ? 2 * nnz : nnz; }
     DevFlags* flags_host = nullptr;  // mapped pinned: errors and hints of asynchronous calls
     DevFlags* flags_dev = nullptr;   // the same words, as the device addresses them
     int ecap_mult = 1, hcap_mult = 1;  // batched capacities learnt from asynchronous calls
@@ -197,8 +207,11 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result);
 // CSR construction (graph_build.cu): sort every row in place; build a
 // symmetric, deduplicated CSR from an edge list (device arrays).
 sp_status sort_rows_device(const int32_t* d_rp, int32_t* d_ci, int32_t n, int64_t nnz, cudaStream_t st);
-sp_status csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, cudaStream_t st,
-                         int32_t** d_rp_out, int32_t** d_ci_out, int64_t* nnz_out, std::string* detail);
+sp_status csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, bool directed,
+                         cudaStream_t st, int32_t** d_rp_out, int32_t** d_ci_out, int64_t* nnz_out,
+                         std::string* detail);
+sp_status combined_rows(const int32_t* d_rp, const int32_t* d_ci, int32_t n, int64_t nnz, cudaStream_t st,
+                        int32_t** d_crp, int32_t** d_cci, int32_t** d_odeg);
 
 // Graph validation kernels.
 sp_status validate_graph(Graph* g, uint32_t flags, cudaStream_t stream, std::string* detail);

@@ -32,9 +32,13 @@ def dev(a, dtype=torch.int32):
 
 
 def warm(G, srcs, **kw):
-    """A blocking call first: one-time set-up and tuning of the graph shape."""
+    """A blocking call, then an asynchronous one: one-time set-up and tuning
+    of the graph shape, and the first launch of every kernel the asynchronous
+    path uses (modules load on first use)."""
     out = torch.empty(G.n, dtype=torch.float64, device=DEV)
     sp.sp_bc_ex(G.handle, dev(srcs), out, sp.make_opts(**kw))
+    sp.sp_bc_ex(G.handle, dev(srcs), out, sp.make_opts(**kw), want_stats=False)
+    sp.sp_graph_sync(G.handle)
     torch.cuda.synchronize()
 
 
