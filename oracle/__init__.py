@@ -14,6 +14,9 @@ bc(g, sources, mode) -> (bc[n], per-source stats).
 bc(..., directed=True), sigma(..., directed=True): the same on a directed
                      graph (CSR of out-arcs): BFS and dependencies over
                      out-arcs, path counts pulled over in-arcs.
+pagerank(g, damping, tol, max_iter) -> (pr[n], iterations, last L1 change):
+                     pull-form PageRank of the paper's reduction listing
+                     (``pagerank.c``), over in-arcs, FP64.
 distance_sums(g, sources) -> (sum of d(s, t) over reached t, |R_s|) per source,
                      from a 64-source bit-parallel BFS (for the invariant
                      sum_v BC(v) = sum over reached ordered pairs of d - 1).
@@ -34,6 +37,7 @@ PLAIN, XFLOAT, AUTO = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "brandes.c")
+_PR_SRC = os.path.join(_HERE, "pagerank.c")
 _SO = os.path.join(_HERE, "_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -59,12 +63,13 @@ STATS_DTYPE = np.dtype(
 )
 
 
-def build(force: bool = False, src: str = _SRC, out: str = _SO) -> str:
+def build(force: bool = False, src: str = _SRC, out: str = _SO, pr_src: str = _PR_SRC) -> str:
     """Compile the oracle into a shared library (also used on tampered copies in tests)."""
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+    newest = max(os.path.getmtime(src), os.path.getmtime(pr_src))
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
         return out
     tmp = out + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", *CFLAGS, src, "-o", tmp, "-lm"], check=True, capture_output=True)
+    subprocess.run(["gcc", *CFLAGS, src, pr_src, "-o", tmp, "-lm"], check=True, capture_output=True)
     os.replace(tmp, out)
     return out
 
@@ -92,6 +97,8 @@ def _declare(lib):
     lib.oracle_bc_directed.restype = ctypes.c_int
     lib.oracle_sigma_directed.argtypes = [i32, p, p, i32, ctypes.c_int, p, p, p, p]
     lib.oracle_sigma_directed.restype = ctypes.c_int
+    lib.oracle_pagerank.argtypes = [i32, p, p, ctypes.c_double, ctypes.c_double, i32, p, p, p]
+    lib.oracle_pagerank.restype = ctypes.c_int
     lib.oracle_distance_sums.argtypes = [i32, p, p, p, i32, p, p]
     lib.oracle_distance_sums.restype = ctypes.c_int
     return lib
@@ -176,3 +183,17 @@ def pair_distance_excess(g, sources, threads: int = 1) -> int:
     else:
         parts = [distance_sums(g, s) for s in slices]
     return int(sum(int(d.sum()) - int((r - 1).sum()) for d, r in parts))
+
+
+def pagerank(g, damping: float = 0.85, tol: float = 0.0, max_iter: int = 100, lib=None):
+    """(pr[n], iterations run, last iteration's L1 change)."""
+    lib = lib or load()
+    rp, ci = _csr(g)
+    pr = np.empty(max(g.n, 1), np.float64)
+    it = ctypes.c_int32()
+    ch = ctypes.c_double()
+    rc = lib.oracle_pagerank(g.n, rp.ctypes.data, ci.ctypes.data, float(damping), float(tol), int(max_iter),
+                             pr.ctypes.data, ctypes.byref(it), ctypes.byref(ch))
+    if rc != 0:
+        raise ValueError(f"oracle_pagerank rc={rc}")
+    return pr[: g.n], it.value, ch.value
