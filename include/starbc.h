@@ -276,6 +276,26 @@ SP_API sp_status sp_bfs(sp_graph g, const int32_t* sources, int32_t nsrc, int32_
 SP_API sp_status sp_sigma(sp_graph g, int32_t src, double* mant_out, int64_t* exp2_out, sp_stream stream);
 
 /*
+ * PageRank of a resident graph: the pull form of the paper's generated
+ * reduction code for PageRank (Section 3.3, the listing over the reverse
+ * CSR).  PR starts at 1/N; every iteration sets, for each vertex v,
+ *     PR'(v) = (1 - damping) / N + damping * sum over in-neighbours u of PR(u) / outdeg(u)
+ * (an undirected graph's in-neighbours are its neighbours; a vertex without
+ * out-arcs passes nothing on) and measures the change sum_v |PR'(v) - PR(v)|.
+ * The loop stops after the first iteration whose change is at most `tol`
+ * (never when tol < 0) or after max_iter iterations.  FP64 throughout.
+ *   damping in [0, 1]; max_iter >= 0.
+ *   pr_out: double[n], host or device, overwritten.
+ *   iterations_out, change_out: host, may be NULL; the iterations run and the
+ *   last change.
+ * With device pr_out and both NULL the call is asynchronous on `stream`
+ * (device errors latched as for sp_bc); otherwise it returns when pr_out
+ * holds the result.
+ */
+SP_API sp_status sp_pagerank(sp_graph g, double damping, double tol, int32_t max_iter, double* pr_out,
+                             int32_t* iterations_out, double* change_out, sp_stream stream);
+
+/*
  * BC for callers that cannot allocate device memory (the paper has no
  * counterpart: this entry point exists for callers such as threads of a
  * framework that owns all device memory, real-time or serving loops that

@@ -81,6 +81,7 @@ SIGNATURES = {
     "sp_bc_ex": ([_P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "sp_bfs": ([_P, _P, _I32, _P, _P], ctypes.c_int),
     "sp_sigma": ([_P, _I32, _P, _P, _P], ctypes.c_int),
+    "sp_pagerank": ([_P, ctypes.c_double, ctypes.c_double, _I32, _P, _P, _P, _P], ctypes.c_int),
     "sp_bc_noalloc": ([_P, _P, _I32, _I64, _P, _I32, _P, _P], ctypes.c_int),
     "sp_server_create": ([_SZ, _I32, _P], ctypes.c_int),
     "sp_server_add_graph": ([_P, _P, _P], ctypes.c_int),
@@ -243,6 +244,19 @@ def sp_sigma(g: int, src: int, mant_out, exp2_out, stream=None):
     _check_dtype(mant_out, "float64", "mant_out")
     _check_dtype(exp2_out, "int64", "exp2_out")
     _check(lib.sp_sigma(g, int(src), _ptr(mant_out), _ptr(exp2_out), _stream(stream)), "sp_sigma")
+
+
+def sp_pagerank(g: int, pr_out, damping: float = 0.85, tol: float = 0.0, max_iter: int = 100, stream=None,
+                want_result: bool = True):
+    """PageRank into pr_out; returns (iterations, last L1 change), or None when want_result is False
+    (then a device pr_out makes the call asynchronous)."""
+    _check_dtype(pr_out, "float64", "pr_out")
+    it = ctypes.c_int32()
+    ch = ctypes.c_double()
+    _check(lib.sp_pagerank(g, float(damping), float(tol), int(max_iter), _ptr(pr_out),
+                           ctypes.byref(it) if want_result else None, ctypes.byref(ch) if want_result else None,
+                           _stream(stream)), "sp_pagerank")
+    return (it.value, ch.value) if want_result else None
 
 
 def sp_bc_noalloc(row_ptr, col_idx, sources, bc_out, n: int | None = None, nnz: int | None = None, stream=None):

@@ -1494,6 +1494,7 @@ sp_status sp_graph_destroy(sp_graph gh) {
     if (g->d_top_dist) cudaFree(g->d_top_dist);
     if (g->d_land_dist) cudaFree(g->d_land_dist);
     destroy_step_cache(g);
+    destroy_pr_plan(g);
     cudaFree(g->d_rp);  // waits for work still running on the graph
     cudaFree(g->d_ci);
     if (g->d_crp) cudaFree(g->d_crp);
@@ -1659,6 +1660,56 @@ sp_status sp_bfs(sp_graph gh, const int32_t* sources, int32_t nsrc, int32_t* dis
     if (host_out) cudaFreeAsync(d_dist, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (rc == SP_OK && e != cudaSuccess) rc = cuda_fail(e, "sp_bfs");
+    return rc;
+}
+
+sp_status sp_pagerank(sp_graph gh, double damping, double tol, int32_t max_iter, double* pr_out,
+                      int32_t* iterations_out, double* change_out, sp_stream stream) {
+    set_last_error("");
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    if (!(damping >= 0.0 && damping <= 1.0)) return fail(SP_ERR_INVALID_ARG, "damping must be in [0, 1]");
+    if (max_iter < 0) return fail(SP_ERR_INVALID_ARG, "max_iter < 0");
+    if (g->n > 0 && !pr_out) return fail(SP_ERR_INVALID_ARG, "pr_out is NULL");
+    {
+        sp_status rc = take_latched(g);
+        if (rc == SP_OK) rc = refuse_other_device({pr_out}, "sp_pagerank");
+        if (rc != SP_OK) return rc;
+    }
+    if (iterations_out) *iterations_out = 0;
+    if (change_out) *change_out = 0.0;
+    if (g->n == 0) return SP_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bool host_out = !is_device_ptr(pr_out);
+    PrLaunch L{};
+    L.g = g;
+    L.damping = damping;
+    L.tol = tol;
+    L.max_iter = max_iter;
+    L.timeout_ns = bfs_timeout_ns();
+    L.stream = st;
+    PrResult r;
+    if (!host_out && !iterations_out && !change_out) {  // asynchronous: nothing to read back
+        L.d_pr = pr_out;
+        L.async.flags = g->flags_dev;
+        return run_pagerank(L, &r);
+    }
+    double* d_pr = pr_out;
+    if (host_out) SP_CUDA(cudaMallocAsync((void**)&d_pr, sizeof(double) * (size_t)g->n, st));
+    L.d_pr = d_pr;
+    sp_status rc = run_pagerank(L, &r);
+    if (rc == SP_OK) rc = map_device_error(r.err, "pagerank", r.diag);
+    if (rc == SP_OK && host_out) {
+        cudaError_t e = cudaMemcpyAsync(pr_out, d_pr, sizeof(double) * (size_t)g->n, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copying pr_out");
+    }
+    if (host_out) cudaFreeAsync(d_pr, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == SP_OK && e != cudaSuccess) rc = cuda_fail(e, "sp_pagerank");
+    if (rc == SP_OK) {
+        if (iterations_out) *iterations_out = r.iterations;
+        if (change_out) *change_out = r.change;
+    }
     return rc;
 }
 

@@ -86,6 +86,7 @@ struct BatchArgs {
     int centre_bound;  // FP64 path counts: recentre a level whose exponents leave [-bound, bound]
     int directed;      // rp/ci: combined out- and in-arc rows (arc_in / arc_out); odeg: out-degrees
     const int32_t* odeg;
+    double* sq;        // optional [n]: sum over the call's sources of delta_s(v)^2 (sampling bounds)
 };
 
 template <int W>
@@ -316,7 +317,7 @@ struct BatchKernel {
     // storage precision: each lane's W values, then a fixed-order butterfly
     // over the warp.
     __device__ __forceinline__ void delta_flush(int v, const uint32_t (&F)[W], const AccT (&acc)[W]) {
-        double bcsum = 0.0;
+        double bcsum = 0.0, sqsum = 0.0;
         AccT dk[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -337,6 +338,7 @@ struct BatchKernel {
                     if (!normal_finite_f(t) || !normal_finite_f(sf)) set_error(ctl, kErrThetaRange32);
                     th()[idx] = t;
                     bcsum += (double)delta;
+                    sqsum += (double)delta * (double)delta;
                     dk[k] = delta;
                 } else {
                     double s = (double)sv;
@@ -346,6 +348,7 @@ struct BatchKernel {
                     if (!normal_finite(t)) set_error(ctl, SP_ERR_RANGE);
                     th()[idx] = t;
                     bcsum += delta;
+                    sqsum += delta * delta;
                     dk[k] = delta;
                 }
             }
@@ -366,6 +369,10 @@ struct BatchKernel {
         // fixed-order reduction over the sources of this entry
         bcsum = warp_sum_f64(bcsum);
         if (lane == 0) a.bc[v] = __ldcg(&a.bc[v]) + bcsum;
+        if (a.sq != nullptr) {
+            sqsum = warp_sum_f64(sqsum);
+            if (lane == 0) a.sq[v] = __ldcg(&a.sq[v]) + sqsum;
+        }
     }
 
     // Request mode: per-word counts of traversed (arc, source) pairs and
@@ -908,6 +915,8 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
 
     if (a.word_bc == nullptr)
         for (int i = tid; i < n; i += nthr) a.bc[i] = 0.0;
+    if (a.sq != nullptr)
+        for (int i = tid; i < n; i += nthr) a.sq[i] = 0.0;
     if (!sync()) goto out;
 
     for (int b0 = 0; b0 < a.nsrc; b0 += B) {

@@ -116,6 +116,7 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.bu_den = L.bottom_up_den;
     a.word_stats = L.d_word_stats;
     a.centre_bound = sigma_centre_bound(L.sigma_float, L.theta_f32, PlainMode::BC);
+    a.sq = L.d_sq;
 
     void* args[] = {&a};
     if (L.async.flags != nullptr) {  // enqueue only: the finish step moves the error word on

@@ -52,6 +52,7 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     bool rec = ngroups > 1 && L.mode == PlainMode::BC && (double)ngroups * (double)n * 28.0 > 2.0 * (double)l2;
     if (L.debug_flags & SP_DEBUG_PLAIN_RECORDS) rec = true;
     if (L.debug_flags & SP_DEBUG_PLAIN_ARRAYS) rec = false;
+    if (L.d_sq != nullptr) rec = false;  // the squared dependencies need the partial arrays
     if (rec) {
         int per_sm_rec = 0;
         SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rec, pick(true), kPlainThreads, 0));
@@ -64,7 +65,8 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
                                          : (ngroups == 1 ? n + 2 : std::min<int64_t>(n + 2, 65536));
     const int64_t hcap = g->knnz() / tiers.t_hub + 2;
     const int64_t segcap = g->knnz() / tiers.seg + hcap + 2;
-    const PlainLayout lay = plain_layout(n, lcap, hcap, segcap, ngroups, grid, ngroups > 1 && L.mode == PlainMode::BC, rec);
+    const PlainLayout lay = plain_layout(n, lcap, hcap, segcap, ngroups, grid, ngroups > 1 && L.mode == PlainMode::BC, rec,
+                                         L.d_sq != nullptr);
     const size_t bytes = lay.bytes;
     char* ws = nullptr;
     cudaError_t ce = workspace_alloc((void**)&ws, bytes, st);
@@ -85,6 +87,7 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     a.nsrc = L.nsrc;
     a.bc = L.d_bc;
     plain_bind(a, ws, lay);
+    a.sq = L.mode == PlainMode::BC ? L.d_sq : nullptr;
     a.gblocks = gblocks;
     a.ngroups = ngroups;
     a.hcap = (int32_t)hcap;
@@ -113,6 +116,8 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
             const double* part = rec ? reinterpret_cast<const double*>(a.lvl) + 1 : a.bcpart;
             sum_group_partials_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(part, ngroups, n, rec ? 4 : 1, L.d_bc,
                                                                           a.gate);
+            if (a.sq != nullptr)
+                sum_group_partials_kernel<<<std::max(rgrid, 1), 256, 0, st>>>(a.sqpart, ngroups, n, 1, a.sq, a.gate);
             e = cudaGetLastError();
         }
         return e;

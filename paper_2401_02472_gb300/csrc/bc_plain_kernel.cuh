@@ -65,6 +65,8 @@ struct PlainArgs {
     int32_t nsrc;
     double* bc;             // output; written directly when ngroups == 1
     double* bcpart;         // [ngroups][n] partial BC per group (ngroups > 1)
+    double* sq;             // optional [n]: sum over the sources of delta_s(v)^2 (sampling bounds)
+    double* sqpart;         // [ngroups][n] its partials per group (ngroups > 1)
     int32_t gblocks;        // blocks per group
     int32_t ngroups;
     // Per-group arrays: group g's copy starts at base + g * stride.
@@ -386,6 +388,10 @@ struct PlainKernel {
         }
         double& b = bb(v);
         b = __ldcg(&b) + delta;
+        if (a.sq != nullptr) {
+            double& q = a.ngroups == 1 ? a.sq[v] : a.sqpart[gn + (size_t)v];
+            q = __ldcg(&q) + delta * delta;
+        }
     }
 
     // One chunk of level-stack entries [e0, qe), at most 32.
@@ -654,6 +660,10 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
 
     if (a.mode == (int)PlainMode::BC) {
         for (int i = tid; i < n; i += nthr) K.bb(i) = 0.0;
+        if (a.sq != nullptr) {
+            double* q = a.ngroups == 1 ? a.sq : a.sqpart + K.gn;
+            for (int i = tid; i < n; i += nthr) q[i] = 0.0;
+        }
     }
     if (!sync()) goto out;
 
@@ -782,13 +792,13 @@ out:
 // (per-group copies of every per-source array, 256-byte aligned).
 struct PlainLayout {
     size_t ctl, gctl, zero_end, lvl, sig, th, q, qrow, qoff, hoff, hcnt, emax, emin, fexp, hubs, hdone, part,
-        bcpart, trace, bytes;
+        bcpart, sqpart, trace, bytes;
 };
 
 // rec: one 32-byte record per (group, vertex) at `lvl` instead of the level,
 // path-count, theta and partial-BC arrays.
 inline PlainLayout plain_layout(int64_t n, int64_t lcap, int64_t hcap, int64_t segcap, int ngroups, int grid,
-                                bool bcpart, bool rec = false) {
+                                bool bcpart, bool rec = false, bool sqpart = false) {
     PlainLayout o{};
     const size_t G = (size_t)ngroups;
     size_t bytes = 0;
@@ -811,6 +821,7 @@ inline PlainLayout plain_layout(int64_t n, int64_t lcap, int64_t hcap, int64_t s
     o.hdone = take(sizeof(int32_t) * 2 * (size_t)hcap * G);
     o.part = take(sizeof(double) * (size_t)segcap * G);
     o.bcpart = take(bcpart && !rec ? sizeof(double) * (size_t)n * G : 0);
+    o.sqpart = take(sqpart && bcpart ? sizeof(double) * (size_t)n * G : 0);
     o.trace = take(sizeof(int) * 8 * (size_t)grid * (kPlainThreads / 32));
     o.bytes = bytes;
     return o;
@@ -818,6 +829,7 @@ inline PlainLayout plain_layout(int64_t n, int64_t lcap, int64_t hcap, int64_t s
 
 inline void plain_bind(PlainArgs& a, char* ws, const PlainLayout& o) {
     a.bcpart = reinterpret_cast<double*>(ws + o.bcpart);
+    a.sqpart = reinterpret_cast<double*>(ws + o.sqpart);
     a.lvl = reinterpret_cast<int32_t*>(ws + o.lvl);
     a.sig = ws + o.sig;
     a.th = ws + o.th;

@@ -73,6 +73,7 @@ struct Graph {
     int32_t* d_land_dist = nullptr;  // [2][n] BFS distances from the 2nd and 3rd largest-degree vertices
     bool theta_f64 = false;     // FP32 dependencies of this graph left the FP32 range before
     void* step_cache = nullptr; // graph-driven plain form: device state block and instantiated CUDA graphs
+    void* pr_plan = nullptr;    // PageRank: the hub rows split into segments (found on first use)
 };
 
 // Thread-local error text.
@@ -123,6 +124,7 @@ struct PlainLaunch {
     int group_blocks;       // blocks per group (0 = one group of every block)
     int64_t level_cap;      // BFS levels per group; 0 = default
     int bottom_up_den;      // bottom-up discovery on levels wider than n / this (0 = top-down only)
+    double* d_sq = nullptr; // BC mode, optional: sum over the sources of delta^2 per vertex
     AsyncHooks async;
 };
 
@@ -184,6 +186,7 @@ struct BatchedLaunch {
     int bottom_up_den;                 // bottom-up discovery on levels with more than n / this entries (0 = never)
     double* d_word_bc;                 // request mode: [nsrc/32][n] per-word partial BC (else null)
     unsigned long long* d_word_stats;  // request mode: [nsrc/32][2]
+    double* d_sq = nullptr;            // optional: sum over the sources of delta^2 per vertex
     AsyncHooks async;
 };
 
@@ -203,6 +206,30 @@ bool request_is_batched(Graph* g, int32_t nsrc, const sp_bc_opts& o, cudaStream_
 sp_status run_batched(const BatchedLaunch& L, LaunchResult* result);
 template <int W>
 sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result);
+
+// PageRank (pagerank.cu): the pull form over in-arcs, one persistent launch.
+struct PrLaunch {
+    Graph* g;
+    double damping;
+    double tol;          // stop after the first iteration whose L1 change is at most tol (< 0: never)
+    int32_t max_iter;
+    double* d_pr;        // device [n]: the ranks
+    int max_ctas;
+    uint64_t timeout_ns;
+    cudaStream_t stream;
+    AsyncHooks async;
+};
+struct PrResult {
+    int err = 0;
+    int32_t iterations = 0;
+    double change = 0.0;
+    double kernel_ms = 0.0;
+    int launches = 0;
+    int grid = 0;
+    std::string diag;
+};
+sp_status run_pagerank(const PrLaunch& L, PrResult* result);
+void destroy_pr_plan(Graph* g);
 
 // CSR construction (graph_build.cu): sort every row in place; build a
 // symmetric, deduplicated CSR from an edge list (device arrays).
