@@ -276,6 +276,36 @@ SP_API sp_status sp_bfs(sp_graph g, const int32_t* sources, int32_t nsrc, int32_
 SP_API sp_status sp_sigma(sp_graph g, int32_t src, double* mant_out, int64_t* exp2_out, sp_stream stream);
 
 /*
+ * Approximate BC by source sampling (the paper's BC runs a few sources; the
+ * paper has no estimator or bound: Section 2 and the BC comparison of Section
+ * 5.1).  Sources are drawn uniformly with replacement on the GPU:
+ * s_i = floor(x_i * n / 2^64), x_i = SplitMix64(seed, i) (state
+ * seed + (i + 1) * 0x9E3779B97F4A7C15, then the published finaliser), i = 0,
+ * 1, ...; bc_out[v] = (n / k) * sum_i delta_{s_i}(v) estimates BC over all n
+ * sources (unbiased).  Rounds of sources (k_min first, then at most doubling
+ * k) run until the empirical Bernstein half-width (Maurer and Pontil 2009,
+ * Theorem 4, both sides, union over the n vertices) of every normalised
+ * value BC(v) / ((n - 1)(n - 2)) is at most eps with probability at least
+ * 1 - alpha, or k reaches k_max:
+ *     half = sqrt(2 V L / k) + 7 R L / (3 (k - 1)),  L = ln(4 n / alpha),  R = n / (n - 1),
+ * V the largest sample variance of n delta_s(v) / ((n - 1)(n - 2)).
+ *   eps > 0, 0 < alpha < 1, 2 <= k_min <= k_max < 2^31.
+ *   opts: precision and form as for sp_bc_ex (the small form is not used).
+ *   bc_out: double[n], host or device.  stats (host, may be NULL).
+ * Returns when bc_out holds the estimate.
+ */
+typedef struct {
+    int64_t sources;  /* k, sources drawn */
+    int32_t rounds;
+    int32_t converged; /* 1 when the bound met eps, 0 when k_max stopped the loop */
+    double bound;      /* the half-width reached (normalised units) */
+    double kernel_ms;  /* device time of the BC launches */
+} sp_approx_stats;
+
+SP_API sp_status sp_bc_approx(sp_graph g, uint64_t seed, double eps, double alpha, int64_t k_min, int64_t k_max,
+                              const sp_bc_opts* opts, double* bc_out, sp_approx_stats* stats, sp_stream stream);
+
+/*
  * PageRank of a resident graph: the pull form of the paper's generated
  * reduction code for PageRank (Section 3.3, the listing over the reverse
  * CSR).  PR starts at 1/N; every iteration sets, for each vertex v,

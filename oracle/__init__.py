@@ -197,3 +197,33 @@ def pagerank(g, damping: float = 0.85, tol: float = 0.0, max_iter: int = 100, li
     if rc != 0:
         raise ValueError(f"oracle_pagerank rc={rc}")
     return pr[: g.n], it.value, ch.value
+
+
+# ---------------------------------------------------------------------------
+# Sampled-source BC (estimator and confidence bound), from the definitions:
+# sources drawn uniformly with replacement by multiply-shift of SplitMix64
+# outputs (the seeded generator shared with the GPU tests), estimate
+# (n / k) sum_i delta_{s_i}(v), and the two-sided empirical Bernstein bound
+# (Maurer and Pontil 2009, Theorem 4) with a union over the n vertices.
+
+def sample_sources(n: int, seed: int, count: int, first: int = 0) -> np.ndarray:
+    """s_i = floor(x_i * n / 2^64), x_i the SplitMix64 outputs of the seed, i = first ..."""
+    import gen
+
+    x = gen.draws(seed, first, count)
+    return np.array([(int(v) * n) >> 64 for v in x], dtype=np.int32)
+
+
+def approx_bc(g, seed: int, k: int, alpha: float = 0.1, directed: bool = False, lib=None):
+    """(estimate[n], half-width of the normalised interval, per-source dependencies [k][n])."""
+    n = g.n
+    srcs = sample_sources(n, seed, k)
+    deltas = np.stack([bc(g, [int(s)], lib=lib, directed=directed)[0] for s in srcs])
+    estimate = deltas.sum(axis=0) * (n / k)
+    c = n / ((n - 1.0) * (n - 2.0))
+    y = deltas * c
+    var = y.var(axis=0, ddof=1) if k > 1 else np.full(n, np.inf)
+    L = np.log(4.0 * n / alpha)
+    R = n / (n - 1.0)
+    half = np.sqrt(2.0 * var.max() * L / k) + 7.0 * R * L / (3.0 * (k - 1.0))
+    return estimate, float(half), deltas

@@ -51,6 +51,14 @@ class sp_bc_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class sp_approx_stats(ctypes.Structure):
+    _fields_ = [("sources", ctypes.c_int64), ("rounds", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("bound", ctypes.c_double), ("kernel_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class sp_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("max_degree", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("isolated", ctypes.c_int64), ("sorted_rows", ctypes.c_int32), ("has_self_loops", ctypes.c_int32),
@@ -82,6 +90,8 @@ SIGNATURES = {
     "sp_bfs": ([_P, _P, _I32, _P, _P], ctypes.c_int),
     "sp_sigma": ([_P, _I32, _P, _P, _P], ctypes.c_int),
     "sp_pagerank": ([_P, ctypes.c_double, ctypes.c_double, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "sp_bc_approx": ([_P, ctypes.c_uint64, ctypes.c_double, ctypes.c_double, _I64, _I64, _P, _P, _P, _P],
+                     ctypes.c_int),
     "sp_bc_noalloc": ([_P, _P, _I32, _I64, _P, _I32, _P, _P], ctypes.c_int),
     "sp_server_create": ([_SZ, _I32, _P], ctypes.c_int),
     "sp_server_add_graph": ([_P, _P, _P], ctypes.c_int),
@@ -244,6 +254,17 @@ def sp_sigma(g: int, src: int, mant_out, exp2_out, stream=None):
     _check_dtype(mant_out, "float64", "mant_out")
     _check_dtype(exp2_out, "int64", "exp2_out")
     _check(lib.sp_sigma(g, int(src), _ptr(mant_out), _ptr(exp2_out), _stream(stream)), "sp_sigma")
+
+
+def sp_bc_approx(g: int, bc_out, seed: int, eps: float, alpha: float = 0.1, k_min: int = 256,
+                 k_max: int = 1 << 20, opts: sp_bc_opts | None = None, stream=None) -> dict:
+    """Sampled-source BC estimate into bc_out; returns the sampling statistics."""
+    _check_dtype(bc_out, "float64", "bc_out")
+    st = sp_approx_stats()
+    _check(lib.sp_bc_approx(g, int(seed) & (2**64 - 1), float(eps), float(alpha), int(k_min), int(k_max),
+                            ctypes.byref(opts) if opts is not None else None, _ptr(bc_out), ctypes.byref(st),
+                            _stream(stream)), "sp_bc_approx")
+    return st.as_dict()
 
 
 def sp_pagerank(g: int, pr_out, damping: float = 0.85, tol: float = 0.0, max_iter: int = 100, stream=None,

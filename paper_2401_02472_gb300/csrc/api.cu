@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
+#include <limits>
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
@@ -220,7 +222,7 @@ static void add_range_hint(const Graph* g, int bit) {
 }
 
 static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
-                           sp_bc_stats* stats, cudaStream_t st);
+                           sp_bc_stats* stats, cudaStream_t st, double* d_sq = nullptr);
 static void absorb_hints(Graph* g);
 
 // Time the batched form on the call's first min(nsrc, 256) sources at each
@@ -606,8 +608,11 @@ static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cud
 
 // Run BC on device buffers, rerunning with a wider representation or more
 // workspace when the device reports that it ran out of one.
+// d_sq (optional): per vertex, the sum over the sources of delta_s(v)^2
+// (the plain and batched forms keep it; a call that asks for it does not run
+// the small form).
 static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
-                           sp_bc_stats* stats, cudaStream_t st) {
+                           sp_bc_stats* stats, cudaStream_t st, double* d_sq) {
     absorb_hints(g);
     bool sigma_float;
     {
@@ -630,7 +635,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
     // sources favour batches.  Path counts past 64 bits need the plain or
     // batched form's FP64 representation.  Only the latter two need the
     // eccentricity BFS (diameter estimate, group sizes, source regrouping).
-    const bool small_fits = (int64_t)g->n <= small_form_max_n(g->device);
+    const bool small_fits = (int64_t)g->n <= small_form_max_n(g->device) && d_sq == nullptr;
     if (form == SP_FORM_AUTO && !sigma_float && small_fits) form = SP_FORM_SMALL;
     if (form == SP_FORM_SMALL && !small_fits)
         return fail(SP_ERR_TOO_LARGE, "graph too large for the small form (" + std::to_string(g->n) + " vertices)");
@@ -744,7 +749,8 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             L.group_blocks = plain_group_blocks(g);
             L.level_cap = plain_lcap;
             L.bottom_up_den = plain_bottom_up(g, bottom_up);
-            rc = driver == SP_DRIVER_GRAPH ? run_plain_graph(L, &r) : run_plain(L, &r);
+            L.d_sq = d_sq;
+            rc = driver == SP_DRIVER_GRAPH && d_sq == nullptr ? run_plain_graph(L, &r) : run_plain(L, &r);
         } else {
             BatchedLaunch L{};
             L.g = g;
@@ -762,6 +768,7 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
             L.hub_cap = hcap;
             L.level_cap = lcap;
             L.bottom_up_den = batch_bu;
+            L.d_sq = d_sq;
             rc = run_batched(L, &r);
         }
         if (rc != SP_OK) return rc;
@@ -1288,6 +1295,67 @@ static sp_status bc_enqueue(Graph* g, const int32_t* d_src, bool src_checked, in
     return run_plain(F, &r2);
 }
 
+// ---------------------------------------------------------------------------
+// Approximate BC by source sampling.  The paper's BC runs "a few iterations"
+// of sources (Section 2; Section 5.1, the BC comparison): here the sources are
+// drawn uniformly with replacement, s_i = floor(x_i * n / 2^64) with x_i the
+// i-th SplitMix64 output of the seed (Steele, Lea and Flood 2014: state
+// seed + (i + 1) * 0x9E3779B97F4A7C15, then the published xor-shift-multiply
+// finaliser), and the estimate is BC^(v) = (n / k) sum_i delta_{s_i}(v),
+// unbiased for BC over all n sources.  The confidence half-width of
+// b(v) = BC(v) / ((n - 1)(n - 2)) is the empirical Bernstein bound (Maurer and
+// Pontil 2009, Theorem 4, both sides, a union over the n vertices): with
+// Y_i = n delta_{s_i}(v) / ((n - 1)(n - 2)) in [0, R], R = n / (n - 1), L =
+// ln(4 n / alpha) and V the sample variance of the Y_i,
+//     half(v) = sqrt(2 V L / k) + 7 R L / (3 (k - 1)).
+// Rounds of sources run until max_v half(v) <= eps (after at least k_min
+// sources) or k reaches k_max; each round doubles k at most.
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long i) {
+    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void draw_sources_kernel(unsigned long long seed, long long first, int32_t count, int32_t n,
+                                    int32_t* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        out[i] = (int32_t)__umul64hi(splitmix64(seed, (unsigned long long)(first + i)), (unsigned long long)n);
+}
+
+// acc += round (sums and squared sums); max of the sample variance of delta.
+__global__ void approx_accumulate_kernel(const double* __restrict__ rbc, const double* __restrict__ rsq, int64_t n,
+                                         double* __restrict__ sum, double* __restrict__ sq, double k,
+                                         unsigned long long* __restrict__ max_var_bits) {
+    double best = 0.0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const double s = sum[v] + rbc[v], q = sq[v] + rsq[v];
+        sum[v] = s;
+        sq[v] = q;
+        const double mean = s / k;
+        const double var = k > 1.0 ? fmax(0.0, (q - k * mean * mean) / (k - 1.0)) : 0.0;
+        best = fmax(best, var);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(kFull, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_var_bits, (unsigned long long)__double_as_longlong(best));
+}
+
+__global__ void approx_scale_kernel(const double* __restrict__ sum, int64_t n, double scale, double* __restrict__ out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = sum[v] * scale;
+}
+
+// The half-width of the normalised confidence interval after k sources, from
+// the largest sample variance of delta (all vertices share the second term).
+static double approx_half_width(double max_var_delta, double k, double n, double alpha) {
+    if (k < 2.0 || n < 3.0) return std::numeric_limits<double>::infinity();
+    const double c = n / ((n - 1.0) * (n - 2.0));
+    const double L = std::log(4.0 * n / alpha);
+    const double R = n / (n - 1.0);
+    return std::sqrt(2.0 * c * c * max_var_delta * L / k) + 7.0 * R * L / (3.0 * (k - 1.0));
+}
+
 sp_status bc_device_entry(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
                           sp_bc_stats* stats, cudaStream_t st) {
     return bc_device(g, d_src, nsrc, o, d_bc, stats, st);
@@ -1661,6 +1729,97 @@ sp_status sp_bfs(sp_graph gh, const int32_t* sources, int32_t nsrc, int32_t* dis
     cudaError_t e = cudaStreamSynchronize(st);
     if (rc == SP_OK && e != cudaSuccess) rc = cuda_fail(e, "sp_bfs");
     return rc;
+}
+
+sp_status sp_bc_approx(sp_graph gh, uint64_t seed, double eps, double alpha, int64_t k_min, int64_t k_max,
+                       const sp_bc_opts* opts, double* bc_out, sp_approx_stats* stats, sp_stream stream) {
+    set_last_error("");
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    if (!(eps > 0.0) || !(alpha > 0.0 && alpha < 1.0)) return fail(SP_ERR_INVALID_ARG, "eps > 0 and 0 < alpha < 1");
+    if (k_min < 2 || k_max < k_min || k_max > INT32_MAX) return fail(SP_ERR_INVALID_ARG, "2 <= k_min <= k_max < 2^31");
+    if (g->n > 0 && !bc_out) return fail(SP_ERR_INVALID_ARG, "bc_out is NULL");
+    sp_bc_opts o;
+    sp_bc_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision != SP_FP64 && o.precision != SP_FP32_DELTA) return fail(SP_ERR_INVALID_ARG, "precision");
+    if (o.form == SP_FORM_SMALL) o.form = SP_FORM_AUTO;  // the small form keeps no squared dependencies
+    {
+        sp_status rc = take_latched(g);
+        if (rc == SP_OK) rc = refuse_other_device({bc_out}, "sp_bc_approx");
+        if (rc != SP_OK) return rc;
+    }
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (g->n == 0) return SP_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = g->n;
+    {
+        sp_status rc = ensure_top_bfs(g, st);
+        if (rc != SP_OK) return rc;
+    }
+    if (o.form == SP_FORM_AUTO) o.form = g->top_levels <= 64 ? SP_FORM_BATCHED : SP_FORM_PLAIN;
+    const bool host_out = !is_device_ptr(bc_out);
+    // workspace: sum, sq, round bc, round sq [n] each, sources [k_max chunk], max bits
+    double *sum = nullptr, *sq = nullptr, *rbc = nullptr, *rsq = nullptr;
+    int32_t* src = nullptr;
+    unsigned long long* maxv = nullptr;
+    struct Free {
+        std::vector<void*> p;
+        cudaStream_t s;
+        ~Free() { for (void* x : p) if (x) cudaFreeAsync(x, s); }
+    } fr{{}, st};
+    const int64_t chunk_max = std::min<int64_t>(k_max, 1 << 20);
+    for (double** p : {&sum, &sq, &rbc, &rsq}) {
+        SP_CUDA(cudaMallocAsync((void**)p, sizeof(double) * (size_t)n, st));
+        fr.p.push_back(*p);
+    }
+    SP_CUDA(cudaMallocAsync((void**)&src, sizeof(int32_t) * (size_t)chunk_max, st));
+    fr.p.push_back(src);
+    SP_CUDA(cudaMallocAsync((void**)&maxv, sizeof(unsigned long long), st));
+    fr.p.push_back(maxv);
+    SP_CUDA(cudaMemsetAsync(sum, 0, sizeof(double) * (size_t)n, st));
+    SP_CUDA(cudaMemsetAsync(sq, 0, sizeof(double) * (size_t)n, st));
+    const int egrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count(g->device) * 8);
+    int64_t k = 0;
+    int rounds = 0;
+    double half = std::numeric_limits<double>::infinity(), kernel_ms = 0.0;
+    while (k < k_max) {
+        int64_t want = k == 0 ? k_min : std::max<int64_t>(k, 256);  // at most doubles k
+        want = std::min(want, std::min(k_max - k, chunk_max));
+        draw_sources_kernel<<<(int)std::min<int64_t>((want + 255) / 256, 4096), 256, 0, st>>>(
+            (unsigned long long)seed, (long long)k, (int32_t)want, (int32_t)n, src);
+        SP_CUDA(cudaGetLastError());
+        sp_bc_stats rs{};
+        sp_status rc = bc_device(g, src, (int32_t)want, o, rbc, &rs, st, rsq);
+        if (rc != SP_OK) return rc;
+        kernel_ms += rs.kernel_ms;
+        k += want;
+        ++rounds;
+        SP_CUDA(cudaMemsetAsync(maxv, 0, sizeof(unsigned long long), st));
+        approx_accumulate_kernel<<<std::max(egrid, 1), 256, 0, st>>>(rbc, rsq, n, sum, sq, (double)k, maxv);
+        SP_CUDA(cudaGetLastError());
+        unsigned long long bits = 0;
+        SP_CUDA(cudaMemcpyAsync(&bits, maxv, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        SP_CUDA(cudaStreamSynchronize(st));
+        double max_var;
+        std::memcpy(&max_var, &bits, sizeof(max_var));
+        half = approx_half_width(max_var, (double)k, (double)n, alpha);
+        if (k >= k_min && half <= eps) break;
+    }
+    double* d_out = bc_out;
+    if (host_out) d_out = rbc;  // the round buffer holds the estimate, then it is copied out
+    approx_scale_kernel<<<std::max(egrid, 1), 256, 0, st>>>(sum, n, (double)n / (double)k, d_out);
+    SP_CUDA(cudaGetLastError());
+    if (host_out) SP_CUDA(cudaMemcpyAsync(bc_out, rbc, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    SP_CUDA(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->sources = k;
+        stats->rounds = rounds;
+        stats->converged = half <= eps ? 1 : 0;
+        stats->bound = half;
+        stats->kernel_ms = kernel_ms;
+    }
+    return SP_OK;
 }
 
 sp_status sp_pagerank(sp_graph gh, double damping, double tol, int32_t max_iter, double* pr_out,
