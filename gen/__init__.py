@@ -224,6 +224,29 @@ def random_small_directed(n: int, p: float, seed: int) -> Graph:
     return from_arcs(n, [pq for pq, x in zip(pairs, u) if x < p], f"dgnp{n}_{p}_s{seed}")
 
 
+def _mix64_np(z: np.ndarray) -> np.ndarray:
+    """SplitMix64's finaliser (Steele, Lea, Flood 2014), vectorised over uint64."""
+    z = z.astype(np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def edge_weights(g: Graph, seed: int, lo: int = 1, hi: int = 100, symmetric: bool = True) -> np.ndarray:
+    """Integer weights in [lo, hi], uniform, one per arc (parallel to col_idx), seeded per edge:
+    key = (u, v), or (min, max) when symmetric so both arcs of an undirected edge agree."""
+    rows = np.repeat(np.arange(g.n, dtype=np.uint64), np.diff(g.row_ptr.astype(np.int64)))
+    cols = g.col_idx.astype(np.uint64)
+    if symmetric:
+        rows, cols = np.minimum(rows, cols), np.maximum(rows, cols)
+    key = rows * np.uint64(max(g.n, 1)) + cols
+    with np.errstate(over="ignore"):
+        x = _mix64_np(np.uint64(seed) + (key + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15))
+    span = np.uint64(hi - lo + 1)
+    return (lo + (x % span).astype(np.int64)).astype(np.int32)
+
+
 def path(n: int) -> Graph:
     return from_edges(n, [(i, i + 1) for i in range(n - 1)], f"path{n}")
 

@@ -14,6 +14,9 @@ bc(g, sources, mode) -> (bc[n], per-source stats).
 bc(..., directed=True), sigma(..., directed=True): the same on a directed
                      graph (CSR of out-arcs): BFS and dependencies over
                      out-arcs, path counts pulled over in-arcs.
+bc_weighted(g, weights, sources, directed) -> (bc[n], dist[nsrc][n]): BC under
+                     positive integer arc weights (``weighted.c``: Dijkstra
+                     distances, then the same sums over the shortest-path DAG).
 pagerank(g, damping, tol, max_iter) -> (pr[n], iterations, last L1 change):
                      pull-form PageRank of the paper's reduction listing
                      (``pagerank.c``), over in-arcs, FP64.
@@ -38,6 +41,7 @@ PLAIN, XFLOAT, AUTO = 0, 1, 2
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "brandes.c")
 _PR_SRC = os.path.join(_HERE, "pagerank.c")
+_W_SRC = os.path.join(_HERE, "weighted.c")
 _SO = os.path.join(_HERE, "_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -63,13 +67,13 @@ STATS_DTYPE = np.dtype(
 )
 
 
-def build(force: bool = False, src: str = _SRC, out: str = _SO, pr_src: str = _PR_SRC) -> str:
+def build(force: bool = False, src: str = _SRC, out: str = _SO, pr_src: str = _PR_SRC, w_src: str = _W_SRC) -> str:
     """Compile the oracle into a shared library (also used on tampered copies in tests)."""
-    newest = max(os.path.getmtime(src), os.path.getmtime(pr_src))
+    newest = max(os.path.getmtime(src), os.path.getmtime(pr_src), os.path.getmtime(w_src))
     if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
         return out
     tmp = out + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", *CFLAGS, src, pr_src, "-o", tmp, "-lm"], check=True, capture_output=True)
+    subprocess.run(["gcc", *CFLAGS, src, pr_src, w_src, "-o", tmp, "-lm"], check=True, capture_output=True)
     os.replace(tmp, out)
     return out
 
@@ -97,6 +101,8 @@ def _declare(lib):
     lib.oracle_bc_directed.restype = ctypes.c_int
     lib.oracle_sigma_directed.argtypes = [i32, p, p, i32, ctypes.c_int, p, p, p, p]
     lib.oracle_sigma_directed.restype = ctypes.c_int
+    lib.oracle_bc_weighted.argtypes = [i32, p, p, p, ctypes.c_int, p, i32, p, p]
+    lib.oracle_bc_weighted.restype = ctypes.c_int
     lib.oracle_pagerank.argtypes = [i32, p, p, ctypes.c_double, ctypes.c_double, i32, p, p, p]
     lib.oracle_pagerank.restype = ctypes.c_int
     lib.oracle_distance_sums.argtypes = [i32, p, p, p, i32, p, p]
@@ -227,3 +233,23 @@ def approx_bc(g, seed: int, k: int, alpha: float = 0.1, directed: bool = False, 
     R = n / (n - 1.0)
     half = np.sqrt(2.0 * var.max() * L / k) + 7.0 * R * L / (3.0 * (k - 1.0))
     return estimate, float(half), deltas
+
+
+def bc_weighted(g, weights, sources, directed: bool = False, lib=None):
+    """(bc[n], dist[nsrc][n] with -1 unreachable) under arc weights parallel to col_idx."""
+    lib = lib or load()
+    rp, ci = _csr(g)
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.int32).reshape(-1))
+    if w.size != g.nnz:
+        raise ValueError("one weight per arc")
+    wb = w if w.size else np.ones(1, np.int32)
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1))
+    nsrc = int(src.size)
+    out = np.empty(max(g.n, 1), np.float64)
+    dist = np.empty(max(nsrc * g.n, 1), np.int64)
+    buf = src if nsrc else np.zeros(1, np.int32)
+    rc = lib.oracle_bc_weighted(g.n, rp.ctypes.data, ci.ctypes.data, wb.ctypes.data, int(directed), buf.ctypes.data,
+                                nsrc, out.ctypes.data, dist.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_bc_weighted rc={rc}")
+    return out[: g.n], dist[: nsrc * g.n].reshape(nsrc, g.n)

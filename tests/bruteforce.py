@@ -126,3 +126,49 @@ def pair_distance_excess(g, sources):
         reached = dist[dist > 0]
         total += int((reached - 1).sum())
     return total
+
+
+def bc_exact_weighted(g, weights, sources):
+    """BC from its definition under positive arc weights (parallel to col_idx):
+    weighted Floyd-Warshall distances, every shortest path listed."""
+    n = g.n
+    rp, ci = g.row_ptr, g.col_idx
+    d = [[INF] * n for _ in range(n)]
+    wt = {}
+    for v in range(n):
+        d[v][v] = 0
+        for e in range(rp[v], rp[v + 1]):
+            x, w = int(ci[e]), int(weights[e])
+            d[v][x] = min(d[v][x], w)
+            wt.setdefault((v, x), []).append(w)
+    for k in range(n):
+        for i in range(n):
+            if d[i][k] >= INF:
+                continue
+            for j in range(n):
+                if d[i][k] + d[k][j] < d[i][j]:
+                    d[i][j] = d[i][k] + d[k][j]
+    adj = [[(int(ci[e]), int(weights[e])) for e in range(rp[v], rp[v + 1])] for v in range(n)]
+    bc = [Fraction(0)] * n
+    for s in sources:
+        for t in range(n):
+            if t == s or d[s][t] >= INF:
+                continue
+            paths = []
+
+            def walk(path, dist):
+                x = path[-1]
+                if x == t:
+                    paths.append(tuple(path))
+                    return
+                for y, w in adj[x]:  # parallel arcs are separate paths
+                    if dist + w == d[s][y] and d[s][y] + d[y][t] == d[s][t]:
+                        path.append(y)
+                        walk(path, dist + w)
+                        path.pop()
+
+            walk([s], 0)
+            for p in paths:
+                for v in p[1:-1]:
+                    bc[v] += Fraction(1, len(paths))
+    return bc
