@@ -159,6 +159,30 @@ SP_API sp_status sp_graph_sync(sp_graph g, sp_stream stream);
 SP_API sp_status sp_graph_from_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, uint32_t flags,
                                      sp_stream stream, sp_graph* out);
 
+/*
+ * Arc weights (BC over weighted shortest paths; the paper's SSSP program
+ * relaxes dist[nbr] through dist[v] + weight, Section 3.5, the Min construct).
+ * weights: int32 [nnz] parallel to col_idx (the CSR sp_graph_get_csr
+ * returns), each in [1, 2^20], host or device, copied before return.  The
+ * graph must be undirected with sorted rows and no repeated arc
+ * (SP_GRAPH_SORT_ROWS or sp_graph_from_edges give that), and the two arcs of
+ * an edge must carry the same weight: checked on the GPU (SP_ERR_BAD_GRAPH
+ * with the arc in sp_last_error(); directed graphs: SP_ERR_INVALID_ARG).  From
+ * then on sp_bc / sp_bc_ex compute BC with shortest paths by total weight in
+ * the weighted form (SP_FORM_WEIGHTED, one block per source: distances by
+ * Bellman-Ford frontier rounds with atomicMin, path counts and dependencies
+ * in FP64 over the weighted shortest-path DAG, level by level in distance
+ * order); those calls return when the result is complete, and the precision
+ * option does not apply (FP64).  sp_bfs still gives hop distances.
+ * Calling it again replaces the weights.
+ */
+SP_API sp_status sp_graph_set_weights(sp_graph g, const int32_t* weights, sp_stream stream);
+
+/* Shortest distances under the graph's weights: dist_out[i * n + v] =
+   dist(sources[i], v), -1 when unreachable.  int32 [nsrc][n], host or device.
+   Returns when complete. */
+SP_API sp_status sp_sssp(sp_graph g, const int32_t* sources, int32_t nsrc, int32_t* dist_out, sp_stream stream);
+
 /* Copy the graph's CSR out: row_ptr_out int32 [n+1], col_idx_out int32 [nnz],
    host or device.  Returns when the copy is complete. */
 SP_API sp_status sp_graph_get_csr(sp_graph g, int32_t* row_ptr_out, int32_t* col_idx_out, sp_stream stream);
@@ -168,7 +192,7 @@ SP_API sp_status sp_graph_get_info(sp_graph g, sp_graph_info* out);
 /* Betweenness centrality                                                   */
 
 enum { SP_FP64 = 0, SP_FP32_DELTA = 1 };
-enum { SP_FORM_AUTO = 0, SP_FORM_PLAIN = 1, SP_FORM_BATCHED = 2, SP_FORM_SMALL = 3 };
+enum { SP_FORM_AUTO = 0, SP_FORM_PLAIN = 1, SP_FORM_BATCHED = 2, SP_FORM_SMALL = 3, SP_FORM_WEIGHTED = 4 };
 
 typedef struct {
     int32_t precision;          /* SP_FP64 (delta in FP64) or SP_FP32_DELTA (delta stored in FP32) */
@@ -228,7 +252,7 @@ typedef struct {
     int32_t max_levels;     /* max over sources of L = 1 + eccentricity of s */
     int32_t batches;        /* batches (plain form: one per source) */
     int32_t batch;          /* sources per batch used (1 for the plain form) */
-    int32_t form;           /* SP_FORM_PLAIN, SP_FORM_BATCHED or SP_FORM_SMALL */
+    int32_t form;           /* SP_FORM_PLAIN, SP_FORM_BATCHED, SP_FORM_SMALL or SP_FORM_WEIGHTED */
     int32_t promoted;       /* 1 when FP32 dependencies left the FP32 range and the call reran with FP64 */
     int32_t sigma_float;    /* 1 when path counts needed FP64 with per-level rescaling (a count above
                                2^32 in the batched form, above 2^64 in the plain form, any carry in the

@@ -23,7 +23,7 @@ SP_OK, SP_NOT_READY = 0, 1
 SP_ERR_INVALID_ARG, SP_ERR_OOM, SP_ERR_CUDA, SP_ERR_TOO_LARGE = -1, -2, -3, -4
 SP_ERR_RANGE, SP_ERR_TIMEOUT, SP_ERR_CANCELLED, SP_ERR_BAD_GRAPH, SP_ERR_NO_DEVICE = -5, -6, -7, -8, -9
 SP_FP64, SP_FP32_DELTA = 0, 1
-SP_FORM_AUTO, SP_FORM_PLAIN, SP_FORM_BATCHED, SP_FORM_SMALL = 0, 1, 2, 3
+SP_FORM_AUTO, SP_FORM_PLAIN, SP_FORM_BATCHED, SP_FORM_SMALL, SP_FORM_WEIGHTED = 0, 1, 2, 3, 4
 SP_DRIVER_AUTO, SP_DRIVER_PERSISTENT, SP_DRIVER_GRAPH = 0, 1, 2
 SP_GRAPH_CHECK_SYMMETRIC, SP_GRAPH_SORT_ROWS, SP_GRAPH_DIRECTED = 0x1, 0x2, 0x4
 SP_DEBUG_SKIP_BARRIER = 0x1
@@ -81,6 +81,8 @@ SIGNATURES = {
     "sp_graph_create": ([_P, _P, _I32, _I64, _U32, _P, _P], ctypes.c_int),
     "sp_graph_destroy": ([_P], ctypes.c_int),
     "sp_graph_sync": ([_P, _P], ctypes.c_int),
+    "sp_graph_set_weights": ([_P, _P, _P], ctypes.c_int),
+    "sp_sssp": ([_P, _P, _I32, _P, _P], ctypes.c_int),
     "sp_graph_get_info": ([_P, _P], ctypes.c_int),
     "sp_graph_from_edges": ([_P, _P, _I64, _I32, _U32, _P, _P], ctypes.c_int),
     "sp_graph_get_csr": ([_P, _P, _P, _P], ctypes.c_int),
@@ -193,6 +195,17 @@ def sp_graph_destroy(g: int):
 def sp_graph_sync(g: int, stream=None):
     """Wait for the stream; raise the error an earlier asynchronous call on g latched."""
     _check(lib.sp_graph_sync(g, _stream(stream)), "sp_graph_sync")
+
+
+def sp_graph_set_weights(g: int, weights, stream=None):
+    _check_dtype(weights, "int32", "weights")
+    _check(lib.sp_graph_set_weights(g, _ptr(weights), _stream(stream)), "sp_graph_set_weights")
+
+
+def sp_sssp(g: int, sources, dist_out, stream=None):
+    _check_dtype(sources, "int32", "sources")
+    _check_dtype(dist_out, "int32", "dist_out")
+    _check(lib.sp_sssp(g, _ptr(sources), _count(sources), _ptr(dist_out), _stream(stream)), "sp_sssp")
 
 
 def sp_graph_from_edges(src, dst, n: int, flags: int = 0, stream=None) -> int:

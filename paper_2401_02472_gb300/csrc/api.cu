@@ -611,8 +611,15 @@ static sp_status order_sources(Graph* g, const int32_t* d_src, int32_t nsrc, cud
 // d_sq (optional): per vertex, the sum over the sources of delta_s(v)^2
 // (the plain and batched forms keep it; a call that asks for it does not run
 // the small form).
+static sp_status bc_weighted(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
+                             int32_t* d_dist, sp_bc_stats* stats, cudaStream_t st);
+
 static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
                            sp_bc_stats* stats, cudaStream_t st, double* d_sq) {
+    if (g->d_w != nullptr) {
+        if (d_sq != nullptr) return fail(SP_ERR_INVALID_ARG, "sampling bounds are not kept for weighted graphs");
+        return bc_weighted(g, d_src, nsrc, o, d_bc, nullptr, stats, st);
+    }
     absorb_hints(g);
     bool sigma_float;
     {
@@ -837,6 +844,53 @@ static sp_status bc_device(Graph* g, const int32_t* d_src, int32_t nsrc, const s
         stats->driver = form == SP_FORM_PLAIN ? driver : 0;
         stats->bottom_up = form == SP_FORM_PLAIN ? plain_bottom_up(g, bottom_up)
                                                  : (form == SP_FORM_BATCHED ? batch_bu : 0);
+    }
+    return SP_OK;
+}
+
+// The weighted form: reruns with a larger distance cap when a distance
+// passes it (up to 2^30).
+static sp_status bc_weighted(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
+                             int32_t* d_dist, sp_bc_stats* stats, cudaStream_t st) {
+    LaunchResult r;
+    int64_t cap = 1 << 18;
+    int launches = 0;
+    double kernel_ms = 0.0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        WeightedLaunch L{};
+        L.g = g;
+        L.d_sources = d_src;
+        L.nsrc = nsrc;
+        L.d_bc = d_bc;
+        L.d_dist = d_dist;
+        L.dist_cap = cap;
+        L.max_ctas = o.max_ctas;
+        L.stream = st;
+        r = LaunchResult{};
+        sp_status rc = run_weighted(L, &r);
+        if (rc != SP_OK) return rc;
+        launches += r.launches;
+        kernel_ms += r.kernel_ms;
+        if (r.err == kErrCapLevels && cap < (int64_t)1 << 30) {
+            cap = std::min<int64_t>(cap * 8, (int64_t)1 << 30);
+            continue;
+        }
+        break;
+    }
+    sp_status rc = map_device_error(r.err, "weighted form", r.diag);
+    if (rc != SP_OK) return rc;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->traversed_arcs = (int64_t)r.traversed_arcs;
+        stats->reached = (int64_t)r.reached;
+        stats->entries = (int64_t)r.entries;
+        stats->scanned_arcs = (int64_t)r.scanned_arcs;
+        stats->max_levels = r.levels;
+        stats->batches = nsrc;
+        stats->batch = 1;
+        stats->form = SP_FORM_WEIGHTED;
+        stats->kernel_ms = kernel_ms;
+        stats->launches = launches;
     }
     return SP_OK;
 }
@@ -1134,6 +1188,7 @@ static sp_status take_latched(Graph* g) {
 // then runs it synchronously.
 static sp_status bc_enqueue(Graph* g, const int32_t* d_src, bool src_checked, int32_t nsrc, const sp_bc_opts& o,
                             double* d_bc, cudaStream_t st) {
+    if (g->d_w != nullptr) return SP_NOT_READY;  // the weighted form runs synchronously
     absorb_hints(g);
     bool sigma_float, theta_f32 = o.precision == SP_FP32_DELTA;
     int ecap_mult, hcap_mult;
@@ -1568,9 +1623,57 @@ sp_status sp_graph_destroy(sp_graph gh) {
     if (g->d_crp) cudaFree(g->d_crp);
     if (g->d_cci) cudaFree(g->d_cci);
     if (g->d_odeg) cudaFree(g->d_odeg);
+    if (g->d_w) cudaFree(g->d_w);
     if (g->flags_host) cudaFreeHost(g->flags_host);
     delete g;
     return SP_OK;
+}
+
+sp_status sp_graph_set_weights(sp_graph gh, const int32_t* weights, sp_stream stream) {
+    set_last_error("");
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    if (g->nnz > 0 && !weights) return fail(SP_ERR_INVALID_ARG, "weights is NULL");
+    {
+        sp_status rc = refuse_other_device({weights}, "sp_graph_set_weights");
+        if (rc != SP_OK) return rc;
+    }
+    return set_weights(g, weights, g->nnz > 0 && is_device_ptr(weights), reinterpret_cast<cudaStream_t>(stream));
+}
+
+sp_status sp_sssp(sp_graph gh, const int32_t* sources, int32_t nsrc, int32_t* dist_out, sp_stream stream) {
+    set_last_error("");
+    if (!gh) return fail(SP_ERR_INVALID_ARG, "graph is NULL");
+    Graph* g = reinterpret_cast<Graph*>(gh);
+    if (!g->d_w) return fail(SP_ERR_INVALID_ARG, "the graph has no weights (sp_graph_set_weights)");
+    if (nsrc < 0) return fail(SP_ERR_INVALID_ARG, "nsrc < 0");
+    if (nsrc == 0 || g->n == 0) return SP_OK;
+    if (!sources || !dist_out) return fail(SP_ERR_INVALID_ARG, "NULL pointer");
+    {
+        sp_status rc = take_latched(g);
+        if (rc == SP_OK) rc = refuse_other_device({sources, dist_out}, "sp_sssp");
+        if (rc != SP_OK) return rc;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t count = (size_t)nsrc * (size_t)g->n;
+    const bool host_out = !is_device_ptr(dist_out);
+    int32_t* d_dist = dist_out;
+    if (host_out) SP_CUDA(cudaMallocAsync((void**)&d_dist, sizeof(int32_t) * count, st));
+    int32_t* d_src = nullptr;
+    sp_status rc = stage_in(sources, nsrc, st, &d_src);
+    if (rc == SP_OK) rc = check_sources(d_src, nsrc, g->n, st);
+    sp_bc_opts o;
+    sp_bc_opts_default(&o);
+    if (rc == SP_OK) rc = bc_weighted(g, d_src, nsrc, o, nullptr, d_dist, nullptr, st);
+    if (rc == SP_OK && host_out) {
+        cudaError_t e = cudaMemcpyAsync(dist_out, d_dist, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copying dist_out");
+    }
+    if (d_src) cudaFreeAsync(d_src, st);
+    if (host_out) cudaFreeAsync(d_dist, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == SP_OK && e != cudaSuccess) rc = cuda_fail(e, "sp_sssp");
+    return rc;
 }
 
 sp_status sp_graph_sync(sp_graph gh, sp_stream stream) {
@@ -1601,7 +1704,9 @@ sp_status sp_bc_ex(sp_graph gh, const int32_t* sources, int32_t nsrc, const sp_b
     sp_bc_opts_default(&o);
     if (opts) o = *opts;
     if (o.precision != SP_FP64 && o.precision != SP_FP32_DELTA) return fail(SP_ERR_INVALID_ARG, "precision");
-    if (o.form < SP_FORM_AUTO || o.form > SP_FORM_SMALL) return fail(SP_ERR_INVALID_ARG, "form");
+    if (o.form < SP_FORM_AUTO || o.form > SP_FORM_WEIGHTED) return fail(SP_ERR_INVALID_ARG, "form");
+    if ((o.form == SP_FORM_WEIGHTED) != (g->d_w != nullptr) && o.form != SP_FORM_AUTO)
+        return fail(SP_ERR_INVALID_ARG, "SP_FORM_WEIGHTED is the form of graphs with weights, and theirs only");
     if (o.batch != 0 && o.batch != 32 && o.batch != 64 && o.batch != 128 && o.batch != 256)
         return fail(SP_ERR_INVALID_ARG, "batch must be 0, 32, 64, 128 or 256");
     if (o.max_ctas < 0 || o.barrier_timeout_ns < 0 || o.bottom_up < -1) return fail(SP_ERR_INVALID_ARG, "negative option");

@@ -62,6 +62,7 @@ struct Graph {
     const int32_t* krp() const { return directed ? d_crp : d_rp; }
     const int32_t* kci() const { return directed ? d_cci : d_ci; }
     int64_t knnz() const { return directed ? 2 * nnz : nnz; }
+    int32_t* d_w = nullptr;     // arc weights [nnz] (sp_graph_set_weights): BC under these weights
     DevFlags* flags_host = nullptr;  // mapped pinned: errors and hints of asynchronous calls
     DevFlags* flags_dev = nullptr;   // the same words, as the device addresses them
     int ecap_mult = 1, hcap_mult = 1;  // batched capacities learnt from asynchronous calls
@@ -206,6 +207,22 @@ bool request_is_batched(Graph* g, int32_t nsrc, const sp_bc_opts& o, cudaStream_
 sp_status run_batched(const BatchedLaunch& L, LaunchResult* result);
 template <int W>
 sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result);
+
+// Weighted form (bc_weighted.cu): BC under positive integer arc weights, one
+// block per source; or, with d_dist, the shortest distances only.
+constexpr int32_t kMaxWeight = 1 << 20;
+struct WeightedLaunch {
+    const Graph* g;
+    const int32_t* d_sources;
+    int32_t nsrc;
+    double* d_bc;        // BC mode
+    int32_t* d_dist;     // distance mode: [nsrc][n], -1 when unreachable
+    int64_t dist_cap;    // distances must stay below this (a larger one reruns)
+    int max_ctas;
+    cudaStream_t stream;
+};
+sp_status run_weighted(const WeightedLaunch& L, LaunchResult* result);
+sp_status set_weights(Graph* g, const int32_t* weights, bool device_src, cudaStream_t st);
 
 // PageRank (pagerank.cu): the pull form over in-arcs, one persistent launch.
 struct PrLaunch {
