@@ -123,9 +123,14 @@ __device__ __forceinline__ void zero_mask(uint32_t* p) {
     store_mask<W>(p, z);
 }
 
-template <int W, typename SigT, typename ThT>
+template <int W, typename SigT, typename ThT, bool kDir>
 struct BatchKernel {
     static constexpr int B = 32 * W;
+    // Arcs of the rows this launch reads: for a directed graph the combined
+    // rows (arc_in / arc_out); for an undirected one every arc serves both ways.
+    static __device__ __forceinline__ int avtx(int raw) { return kDir ? arc_vertex(raw) : raw; }
+    static __device__ __forceinline__ bool ain(int raw) { return !kDir || raw < 0; }
+    static __device__ __forceinline__ bool aout(int raw) { return !kDir || raw >= 0; }
     static constexpr bool kFloatSig = !std::is_integral<SigT>::value;
     static constexpr bool kTh32 = sizeof(ThT) == 4;
     // Path counts: stored rows are SigT (u32 exact counts, or FP64 with a
@@ -317,7 +322,7 @@ struct BatchKernel {
     // storage precision: each lane's W values, then a fixed-order butterfly
     // over the warp.
     __device__ __forceinline__ void delta_flush(int v, const uint32_t (&F)[W], const AccT (&acc)[W]) {
-        double bcsum = 0.0, sqsum = 0.0;
+        double bcsum = 0.0;
         AccT dk[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -338,7 +343,6 @@ struct BatchKernel {
                     if (!normal_finite_f(t) || !normal_finite_f(sf)) set_error(ctl, kErrThetaRange32);
                     th()[idx] = t;
                     bcsum += (double)delta;
-                    sqsum += (double)delta * (double)delta;
                     dk[k] = delta;
                 } else {
                     double s = (double)sv;
@@ -348,7 +352,6 @@ struct BatchKernel {
                     if (!normal_finite(t)) set_error(ctl, SP_ERR_RANGE);
                     th()[idx] = t;
                     bcsum += delta;
-                    sqsum += delta * delta;
                     dk[k] = delta;
                 }
             }
@@ -369,7 +372,10 @@ struct BatchKernel {
         // fixed-order reduction over the sources of this entry
         bcsum = warp_sum_f64(bcsum);
         if (lane == 0) a.bc[v] = __ldcg(&a.bc[v]) + bcsum;
-        if (a.sq != nullptr) {
+        if (a.sq != nullptr) {  // squared dependencies (sampling bounds): only when asked for
+            double sqsum = 0.0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) sqsum += (double)dk[k] * (double)dk[k];
             sqsum = warp_sum_f64(sqsum);
             if (lane == 0) a.sq[v] = __ldcg(&a.sq[v]) + sqsum;
         }
@@ -428,7 +434,7 @@ struct BatchKernel {
             if (!hubent) {
                 beg = __ldg(&a.rp[v]);
                 deg = __ldg(&a.rp[v + 1]) - beg;
-                const int tdeg = a.odeg != nullptr ? __ldg(&a.odeg[v]) : deg;  // traversed: out-arcs
+                const int tdeg = kDir ? __ldg(&a.odeg[v]) : deg;  // traversed: out-arcs
                 int pc = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) pc += __popc(F[k]);
@@ -465,15 +471,15 @@ struct BatchKernel {
             int u = 0;
             if (has) {
                 const int raw = __ldg(&a.ci[bj + (ai - exj)]);
-                u = arc_vertex(raw);
-                if (d > 0 && arc_in(raw, a.directed)) {
+                u = avtx(raw);
+                if (d > 0 && ain(raw)) {
                     uint32_t p[W];
                     load_mask<W>(prev + (size_t)u * W, p);
 #pragma unroll
                     for (int k = 0; k < W; ++k) { m[k] = Fj[k] & p[k]; dag += __popc(m[k]); }
                 }
                 mark(0);
-                if (discover_on && arc_out(raw)) discover(u, Fj);
+                if (discover_on && aout(raw)) discover(u, Fj);
                 mark(6);
             }
             if (d > 0) {
@@ -530,15 +536,15 @@ struct BatchKernel {
             int u = 0;
             if (has) {
                 const int raw = __ldg(&a.ci[ai]);
-                u = arc_vertex(raw);
-                if (d > 0 && arc_in(raw, a.directed)) {
+                u = avtx(raw);
+                if (d > 0 && ain(raw)) {
                     uint32_t p[W];
                     load_mask<W>(prev + (size_t)u * W, p);
 #pragma unroll
                     for (int k = 0; k < W; ++k) { m[k] = F[k] & p[k]; dag += __popc(m[k]); }
                 }
                 mark(1);
-                if (discover_on && arc_out(raw)) discover(u, F);
+                if (discover_on && aout(raw)) discover(u, F);
                 mark(6);
             }
             if (d > 0) {
@@ -555,7 +561,7 @@ struct BatchKernel {
         stat(4, dag);
         auto count_entry = [&]() {
             if (lane == 0) {
-                const int tdeg = a.odeg != nullptr ? __ldg(&a.odeg[hv]) : re - rb;  // traversed: out-arcs
+                const int tdeg = kDir ? __ldg(&a.odeg[hv]) : re - rb;  // traversed: out-arcs
                 int pc = 0;
 #pragma unroll
                 for (int k = 0; k < W; ++k) pc += __popc(F[k]);
@@ -622,9 +628,9 @@ struct BatchKernel {
         if (any && deg <= 32) {
             for (int e = 0; e < deg; ++e) {
                 const int raw = __ldg(&a.ci[rb + e]);
-                if (!arc_in(raw, a.directed)) continue;  // only an arc into u can reach it
+                if (!ain(raw)) continue;  // only an arc into u can reach it
                 uint32_t f[W];
-                load_mask<W>(cur + (size_t)arc_vertex(raw) * W, f);
+                load_mask<W>(cur + (size_t)avtx(raw) * W, f);
                 bool done = true;
 #pragma unroll
                 for (int k = 0; k < W; ++k) { got[k] |= f[k] & unseen[k]; done &= got[k] == unseen[k]; }
@@ -641,9 +647,9 @@ struct BatchKernel {
             for (int k = 0; k < W; ++k) { uns[k] = __shfl_sync(kFull, unseen[k], j); g2[k] = 0u; }
             for (int e = lane; e < dj; e += kWarp) {
                 const int raw = __ldg(&a.ci[bj + e]);
-                if (!arc_in(raw, a.directed)) continue;
+                if (!ain(raw)) continue;
                 uint32_t f[W];
-                load_mask<W>(cur + (size_t)arc_vertex(raw) * W, f);
+                load_mask<W>(cur + (size_t)avtx(raw) * W, f);
 #pragma unroll
                 for (int k = 0; k < W; ++k) g2[k] |= f[k] & uns[k];
             }
@@ -717,8 +723,8 @@ struct BatchKernel {
             int w = 0;
             if (has) {
                 const int raw = __ldg(&a.ci[bj + (ai - exj)]);
-                w = arc_vertex(raw);
-                if (arc_out(raw)) load_mask<W>(next + (size_t)w * W, m);  // children: out-arcs
+                w = avtx(raw);
+                if (aout(raw)) load_mask<W>(next + (size_t)w * W, m);  // children: out-arcs
             }
             uint32_t anym = 0;
 #pragma unroll
@@ -770,8 +776,8 @@ struct BatchKernel {
             for (int k = 0; k < W; ++k) m[k] = 0u;
             if (has) {
                 const int raw = __ldg(&a.ci[ai]);
-                w = arc_vertex(raw);
-                if (arc_out(raw)) {  // children: out-arcs
+                w = avtx(raw);
+                if (aout(raw)) {  // children: out-arcs
                     uint32_t c[W];
                     load_mask<W>(next + (size_t)w * W, c);
 #pragma unroll
@@ -838,7 +844,7 @@ struct BatchKernel {
     }
 };
 
-template <int W, typename SigT, typename ThT>
+template <int W, typename SigT, typename ThT, bool kDir>
 __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(BatchArgs a) {
     if (a.pre_err != nullptr) {  // the same word for every block: all return, nothing is touched
         const int pe = ld_volatile(a.pre_err);
@@ -847,7 +853,7 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
             return;
         }
     }
-    using K_t = BatchKernel<W, SigT, ThT>;
+    using K_t = BatchKernel<W, SigT, ThT, kDir>;
     constexpr int B = K_t::B;
     constexpr bool kFloatSig = K_t::kFloatSig;
     K_t K(a);

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "bc_batched.cuh"
 
@@ -20,11 +21,15 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     // path-count rows: exact u32 counts, or FP64 with per-level exponents once
     // a count passes 2^32
     const void* fn;
-    if (L.sigma_float)
-        fn = L.theta_f32 ? (const void*)&batched_kernel<W, double, float> : (const void*)&batched_kernel<W, double, double>;
-    else
-        fn = L.theta_f32 ? (const void*)&batched_kernel<W, unsigned int, float>
-                         : (const void*)&batched_kernel<W, unsigned int, double>;
+    auto pick = [&](auto dir) -> const void* {
+        constexpr bool kDir = decltype(dir)::value;
+        if (L.sigma_float)
+            return L.theta_f32 ? (const void*)&batched_kernel<W, double, float, kDir>
+                               : (const void*)&batched_kernel<W, double, double, kDir>;
+        return L.theta_f32 ? (const void*)&batched_kernel<W, unsigned int, float, kDir>
+                           : (const void*)&batched_kernel<W, unsigned int, double, kDir>;
+    };
+    fn = g->directed ? pick(std::true_type{}) : pick(std::false_type{});
     const size_t sig_size = L.sigma_float ? 8 : 4;
     int per_sm = 0;
     SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, 0));

@@ -219,8 +219,9 @@ extern "C" sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_id
     // Exact 64-bit path counts first; FP64 counts with per-level rescaling
     // when they overflow.
     for (int attempt = 0; attempt < 2; ++attempt) {
-        const void* fn = attempt == 0 ? reinterpret_cast<const void*>(&plain_kernel<unsigned long long, double, false>)
-                                      : reinterpret_cast<const void*>(&plain_kernel<double, double, false>);
+        const void* fn = attempt == 0
+                             ? reinterpret_cast<const void*>(&plain_kernel<unsigned long long, double, false, false>)
+                             : reinterpret_cast<const void*>(&plain_kernel<double, double, false, false>);
         int per_sm = 0;
         SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPlainThreads, 0));
         if (per_sm < 1) return fail(SP_ERR_CUDA, "sp_bc_noalloc: kernel cannot be resident");

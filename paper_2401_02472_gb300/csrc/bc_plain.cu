@@ -11,9 +11,12 @@
 namespace sp {
 
 template <typename SigT, typename ThT>
-static const void* plain_fn(bool rec) {
-    return rec ? reinterpret_cast<const void*>(&plain_kernel<SigT, ThT, true>)
-               : reinterpret_cast<const void*>(&plain_kernel<SigT, ThT, false>);
+static const void* plain_fn(bool rec, bool dir) {
+    if (dir)
+        return rec ? reinterpret_cast<const void*>(&plain_kernel<SigT, ThT, true, true>)
+                   : reinterpret_cast<const void*>(&plain_kernel<SigT, ThT, false, true>);
+    return rec ? reinterpret_cast<const void*>(&plain_kernel<SigT, ThT, true, false>)
+               : reinterpret_cast<const void*>(&plain_kernel<SigT, ThT, false, false>);
 }
 
 sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
@@ -21,9 +24,11 @@ sp_status run_plain(const PlainLaunch& L, LaunchResult* result) {
     const int64_t n = g->n;
     cudaStream_t st = L.stream;
     Tiers tiers{16, 4096, 4096};
+    const bool dir = g->directed;
     auto pick = [&](bool rec) {
-        if (L.sigma_float) return L.theta_f32 ? plain_fn<double, float>(rec) : plain_fn<double, double>(rec);
-        return L.theta_f32 ? plain_fn<unsigned long long, float>(rec) : plain_fn<unsigned long long, double>(rec);
+        if (L.sigma_float) return L.theta_f32 ? plain_fn<double, float>(rec, dir) : plain_fn<double, double>(rec, dir);
+        return L.theta_f32 ? plain_fn<unsigned long long, float>(rec, dir)
+                           : plain_fn<unsigned long long, double>(rec, dir);
     };
     const void* fn = pick(false);
 

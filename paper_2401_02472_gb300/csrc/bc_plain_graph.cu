@@ -64,7 +64,7 @@ constexpr int kUnroll = 4;  // step launches per WHILE iteration
 static __device__ __noinline__ void step_advance(StepBlock* blk, cudaGraphConditionalHandle cond) {
     const PlainArgs& a = blk->args;
     StepState s = blk->state;
-    PlainKernel<unsigned long long, double, false> K(a, 0);
+    PlainKernel<unsigned long long, double, false, false> K(a, 0);
     GroupCtl* gc = a.gctl;
     gc->work[0] = 0u;
     s.steps += 1;
@@ -138,8 +138,8 @@ static __device__ __noinline__ void step_advance(StepBlock* blk, cudaGraphCondit
 
 // One forward or backward level of the current source, then the block's
 // statistics.
-template <typename SigT, typename ThT>
-static __device__ __forceinline__ void step_work(PlainKernel<SigT, ThT, false>& K, const StepState& ss, int n) {
+template <typename SigT, typename ThT, bool kDir>
+static __device__ __forceinline__ void step_work(PlainKernel<SigT, ThT, false, kDir>& K, const StepState& ss, int n) {
     constexpr bool kFloatSig = !std::is_integral<SigT>::value;
     const PlainArgs& sa = K.a;
     const int d = ss.d;
@@ -188,7 +188,7 @@ static __device__ __forceinline__ void step_work(PlainKernel<SigT, ThT, false>& 
     }
 }
 
-template <typename SigT, typename ThT>
+template <typename SigT, typename ThT, bool kDir>
 __global__ void __launch_bounds__(kPlainThreads, 2) plain_step_kernel(StepBlock* blk, cudaGraphConditionalHandle cond) {
     __shared__ PlainArgs sa;
     __shared__ StepState ss;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kPlainThreads, 2) plain_step_kernel(StepBlock*
         }
         return;
     }
-    PlainKernel<SigT, ThT, false> K(sa, 0);
+    PlainKernel<SigT, ThT, false, kDir> K(sa, 0);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
     const int n = sa.n;
@@ -253,8 +253,9 @@ void destroy_step_cache(Graph* g) {
 }
 
 template <typename SigT, typename ThT>
-static const void* step_fn() {
-    return reinterpret_cast<const void*>(&plain_step_kernel<SigT, ThT>);
+static const void* step_fn(bool dir) {
+    return dir ? reinterpret_cast<const void*>(&plain_step_kernel<SigT, ThT, true>)
+               : reinterpret_cast<const void*>(&plain_step_kernel<SigT, ThT, false>);
 }
 
 // Build the graph: one WHILE node (condition 1 at every launch) whose body is
@@ -302,9 +303,10 @@ sp_status run_plain_graph(const PlainLaunch& L, LaunchResult* result) {
     if (L.mode != PlainMode::BC) return fail(SP_ERR_INVALID_ARG, "graph-driven level loop: BC mode only");
     Tiers tiers{16, 4096, 4096};
     const int variant = (L.sigma_float ? 2 : 0) + (L.theta_f32 ? 1 : 0);
-    const void* fn = L.sigma_float ? (L.theta_f32 ? step_fn<double, float>() : step_fn<double, double>())
-                                   : (L.theta_f32 ? step_fn<unsigned long long, float>()
-                                                  : step_fn<unsigned long long, double>());
+    const bool dir = g->directed;
+    const void* fn = L.sigma_float ? (L.theta_f32 ? step_fn<double, float>(dir) : step_fn<double, double>(dir))
+                                   : (L.theta_f32 ? step_fn<unsigned long long, float>(dir)
+                                                  : step_fn<unsigned long long, double>(dir));
     int per_sm = 0;
     SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPlainThreads, 0));
     if (per_sm < 1) return fail(SP_ERR_CUDA, "plain step kernel cannot be resident");

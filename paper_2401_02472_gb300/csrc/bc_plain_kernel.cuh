@@ -197,8 +197,13 @@ struct SigOps<double> {
 // partial @8, path count @16, theta @24) instead of separate arrays, so that a
 // vertex's level test and its path count or theta share one DRAM sector; used
 // when the groups' state is far larger than L2 and every access is a miss.
-template <typename SigT, typename ThT, bool kRec>
+template <typename SigT, typename ThT, bool kRec, bool kDir>
 struct PlainKernel {
+    // Arcs of the rows this launch reads: for a directed graph the combined
+    // rows (arc_in / arc_out); for an undirected one every arc serves both ways.
+    static __device__ __forceinline__ int avtx(int raw) { return kDir ? arc_vertex(raw) : raw; }
+    static __device__ __forceinline__ bool ain(int raw) { return !kDir || raw < 0; }
+    static __device__ __forceinline__ bool aout(int raw) { return !kDir || raw >= 0; }
     const PlainArgs& a;
     Ctl* ctl;
     GroupCtl* gc;
@@ -334,20 +339,20 @@ struct PlainKernel {
     // u, u's level already loaded as lu): claim u for level d+1 over an arc
     // out of v, or return sigma[u] if u is a parent over an arc into v.
     __device__ __forceinline__ SigT fwd_visit(int raw, int lu) {
-        const int u = arc_vertex(raw);
+        const int u = avtx(raw);
         SigT c = 0;
         if (lu < 0) {
-            if (discover && arc_out(raw) && atomicCAS(&lv(u), -1, d + 1) == -1) push(u, d + 1);
-        } else if (lu == d - 1 && arc_in(raw, a.directed)) {
+            if (discover && aout(raw) && atomicCAS(&lv(u), -1, d + 1) == -1) push(u, d + 1);
+        } else if (lu == d - 1 && ain(raw)) {
             c = __ldcg(&sg(u));
             st_dag += 1;
         }
         return c;
     }
-    __device__ __forceinline__ SigT fwd_arc(int raw) { return fwd_visit(raw, __ldcg(&lv(arc_vertex(raw)))); }
+    __device__ __forceinline__ SigT fwd_arc(int raw) { return fwd_visit(raw, __ldcg(&lv(avtx(raw)))); }
     // Out-degree of v (traversed arcs); an undirected graph's row length.
     __device__ __forceinline__ int out_degree(int v, int row_len) const {
-        return a.odeg != nullptr ? __ldg(&a.odeg[v]) : row_len;
+        return kDir ? __ldg(&a.odeg[v]) : row_len;
     }
 
     __device__ void fwd_finalize(int v, SigT acc, int deg) {
@@ -367,8 +372,8 @@ struct PlainKernel {
     }
 
     __device__ __forceinline__ double bwd_arc(int raw) {
-        if (!arc_out(raw)) return 0.0;  // children: out-arcs only
-        const int w = arc_vertex(raw);
+        if (!aout(raw)) return 0.0;  // children: out-arcs only
+        const int w = avtx(raw);
         int lw = __ldcg(&lv(w));
         return lw == d + 1 ? (double)__ldcg(&tt(w)) : 0.0;
     }
@@ -432,9 +437,9 @@ struct PlainKernel {
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
                     const int raw = k0 + i < walk ? __ldg(&a.ci[beg + k0 + i]) : 0;
-                    u[i] = k0 + i < walk ? arc_vertex(raw) : -1;
-                    out[i] = u[i] >= 0 && arc_out(raw);
-                    in[i] = u[i] >= 0 && arc_in(raw, a.directed);
+                    u[i] = k0 + i < walk ? avtx(raw) : -1;
+                    out[i] = u[i] >= 0 && aout(raw);
+                    in[i] = u[i] >= 0 && ain(raw);
                 }
 #pragma unroll
                 for (int i = 0; i < G; ++i) lu[i] = u[i] >= 0 ? __ldcg(&lv(u[i])) : INT_MIN;
@@ -574,8 +579,8 @@ struct PlainKernel {
                 for (int k = b; k < e; ++k) {
                     st_scanned += 1;
                     const int raw = __ldg(&a.ci[k]);
-                    if (!arc_in(raw, a.directed)) continue;  // only an arc into u can reach it
-                    if (__ldcg(&lv(arc_vertex(raw))) == d) {
+                    if (!ain(raw)) continue;  // only an arc into u can reach it
+                    if (__ldcg(&lv(avtx(raw))) == d) {
                         lv(u) = d + 1;
                         push(u, d + 1);
                         break;
@@ -633,13 +638,13 @@ static __device__ __forceinline__ bool plain_skip(const PlainArgs& a) {
     return false;
 }
 
-template <typename SigT, typename ThT, bool kRec>
+template <typename SigT, typename ThT, bool kRec, bool kDir>
 __global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
     if (plain_skip(a)) return;
     constexpr bool kFloatSig = !std::is_integral<SigT>::value;
     const int g = blockIdx.x / a.gblocks;
     if (g >= a.ngroups) return;  // the host sizes the grid to ngroups * gblocks
-    PlainKernel<SigT, ThT, kRec> K(a, g);
+    PlainKernel<SigT, ThT, kRec, kDir> K(a, g);
     __shared__ int s_qtail;
     if (a.gblocks == 1) K.qtail = &s_qtail;  // the whole group is this block
     Ctl* ctl = a.ctl;
