@@ -305,6 +305,8 @@ def workload_graph(name: str) -> Graph:
         return rmat(22, 16, 4)
     if name == "rmat21":
         return rmat(21, 16, 4)
+    if name == "drmat22":
+        return rmat_directed(22, 16, 4)
     raise KeyError(name)
 
 

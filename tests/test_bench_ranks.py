@@ -64,10 +64,14 @@ def test_recorded_traffic_only_for_the_current_kernels(tmp_path, monkeypatch):
     (tmp_path / "profiles" / "t.md").write_text(
         "# capture\n"
         f"traffic-record: workload=w1 width=128 sources={h} dram_bytes=1.5e11\n"
-        "traffic-record: workload=w1 width=256 sources=0000000000000000 dram_bytes=9e9\n")
+        "traffic-record: workload=w1 width=256 sources=0000000000000000 dram_bytes=9e9\n"
+        f"traffic-record: workload=w3 width=128 sources={h} per_alg_byte=1.25 captured=small\n")
     csrc = os.path.join(bench.ROOT, "paper_2401_02472_gb300")
     os.symlink(csrc, tmp_path / "paper_2401_02472_gb300")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.recorded_traffic("w1", 128) == 1.5e11
-    assert bench.recorded_traffic("w1", 256) is None
-    assert bench.recorded_traffic("w2", 128) is None
+    assert bench.recorded_traffic("w1", 128, 1e11)[0] == 1.5e11
+    assert bench.recorded_traffic("w1", 256, 1e11)[0] is None
+    assert bench.recorded_traffic("w2", 128, 1e11)[0] is None
+    # a capture of a smaller launch: bytes per algorithmic byte, scaled by this launch's
+    b, note = bench.recorded_traffic("w3", 128, 4e11)
+    assert b == 5e11 and "small" in note
