@@ -69,6 +69,11 @@ struct PrArgs {
 
 __device__ __forceinline__ bool is_hub(const PrArgs& a, int deg) { return deg > a.seg; }
 
+__device__ __forceinline__ double inv_out(const PrArgs& a, int v, int row_len) {
+    const int od = a.odeg != nullptr ? __ldg(&a.odeg[v]) : row_len;
+    return od > 0 ? 1.0 / (double)od : 0.0;
+}
+
 // New rank of v from its pull sum; writes PR', PR' / outdeg and the change.
 __device__ __forceinline__ void settle(const PrArgs& a, int v, int row_len, double sum, const double* pr_cur,
                                       double* pr_nxt, double* contrib_nxt) {
@@ -92,18 +97,9 @@ __device__ void rows_item(const PrArgs& a, int c, const double* contrib, const d
     double sum = 0.0;
     const bool mine = v < a.n && deg <= kPrLane;
     if (mine) {
-        // four arcs at a time: their column ids, then their gathers, are
-        // issued before the adds, which still run in row order
-        for (int k = 0; k < deg; k += 4) {
-            int raw[4];
-            double c[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) raw[i] = k + i < deg ? __ldg(&a.ci[beg + k + i]) : -1;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                c[i] = k + i < deg && arc_in(raw[i], a.directed) ? __ldcg(&contrib[arc_vertex(raw[i])]) : 0.0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) sum += c[i];
+        for (int k = 0; k < deg; ++k) {
+            const int raw = __ldg(&a.ci[beg + k]);
+            if (arc_in(raw, a.directed)) sum += __ldcg(&contrib[arc_vertex(raw)]);
         }
     }
     unsigned wide = __ballot_sync(kFull, v < a.n && deg > kPrLane && !is_hub(a, deg));
@@ -112,16 +108,9 @@ __device__ void rows_item(const PrArgs& a, int c, const double* contrib, const d
         wide &= wide - 1;
         const int bj = __shfl_sync(kFull, beg, j), dj = __shfl_sync(kFull, deg, j);
         double p = 0.0;
-        for (int k0 = 0; k0 < dj; k0 += 4 * kWarp) {
-            double c[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int k = k0 + i * kWarp + lane;
-                const int raw = k < dj ? __ldg(&a.ci[bj + k]) : -1;
-                c[i] = k < dj && arc_in(raw, a.directed) ? __ldcg(&contrib[arc_vertex(raw)]) : 0.0;
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) p += c[i];
+        for (int k = lane; k < dj; k += kWarp) {
+            const int raw = __ldg(&a.ci[bj + k]);
+            if (arc_in(raw, a.directed)) p += __ldcg(&contrib[arc_vertex(raw)]);
         }
         p = warp_sum_f64(p);
         if (lane == j) sum = p;
@@ -144,16 +133,9 @@ __device__ void hub_item(const PrArgs& a, int g, int iter, const double* contrib
     const int rb = __ldg(&a.rp[v]), re = __ldg(&a.rp[v + 1]);
     const int b = rb + (g - s0) * a.seg, e = min(re, b + a.seg);
     double p = 0.0;
-    for (int k0 = b; k0 < e; k0 += 4 * kWarp) {
-        double c[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = k0 + i * kWarp + lane;
-            const int raw = k < e ? __ldg(&a.ci[k]) : -1;
-            c[i] = k < e && arc_in(raw, a.directed) ? __ldcg(&contrib[arc_vertex(raw)]) : 0.0;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) p += c[i];
+    for (int k = b + lane; k < e; k += kWarp) {
+        const int raw = __ldg(&a.ci[k]);
+        if (arc_in(raw, a.directed)) p += __ldcg(&contrib[arc_vertex(raw)]);
     }
     p = warp_sum_f64(p);
     unsigned old = 0;
