@@ -312,7 +312,10 @@ SP_API sp_status sp_sigma(sp_graph g, int32_t src, double* mant_out, int64_t* ex
  * value BC(v) / ((n - 1)(n - 2)) is at most eps with probability at least
  * 1 - alpha, or k reaches k_max:
  *     half = sqrt(2 V L / k) + 7 R L / (3 (k - 1)),  L = ln(4 n / alpha),  R = n / (n - 1),
- * V the largest sample variance of n delta_s(v) / ((n - 1)(n - 2)).
+ * V the largest sample variance of n delta_s(v) / ((n - 1)(n - 2)).  The
+ * bound is the fixed-sample bound at each round's k: no correction is made
+ * for checking it after several rounds (a union over r rounds would replace
+ * alpha by alpha / r).
  *   eps > 0, 0 < alpha < 1, 2 <= k_min <= k_max < 2^31.
  *   opts: precision and form as for sp_bc_ex (the small form is not used).
  *   bc_out: double[n], host or device.  stats (host, may be NULL).
