@@ -396,6 +396,23 @@ SP_API sp_status sp_server_add_graph(sp_server s, sp_graph g, int32_t* graph_id)
    sources (host or device) copied before return. */
 SP_API sp_status sp_bc_submit(sp_server s, int32_t graph_id, const int32_t* sources, int32_t nsrc,
                        const sp_bc_opts* opts, double* bc_out, sp_request* req);
+/*
+ * PageRank request (NEXT to BC on the same resident graphs: the paper's
+ * PageRank, Section 3.3; the computation of sp_pagerank, run alone in one
+ * launch on a free slot).  damping in [0, 1], max_iter >= 0, tol as for
+ * sp_pagerank; pr_out: device double[n] on the graph's GPU, else
+ * SP_ERR_INVALID_ARG.  The request shares the queue and the memory budget
+ * (footprint about 32 bytes a vertex) with BC requests; sp_bc_poll,
+ * sp_bc_wait, sp_bc_cancel and sp_request_times serve every kind of request.
+ * sp_request_stats of a PageRank request gives kernel_ms, launches and
+ * traversed_arcs = arcs x iterations.
+ */
+SP_API sp_status sp_pagerank_submit(sp_server s, int32_t graph_id, double damping, double tol, int32_t max_iter,
+                                    double* pr_out, sp_request* req);
+/* Iterations run and last L1 change of a finished PageRank request; SP_NOT_READY while it runs, its
+   error if it failed, SP_ERR_INVALID_ARG for a BC request. */
+SP_API sp_status sp_request_pagerank(sp_server s, sp_request req, int32_t* iterations, double* change);
+/* Requests of either kind: */
 SP_API sp_status sp_bc_poll(sp_server s, sp_request req);                     /* SP_OK, SP_NOT_READY or the error */
 SP_API sp_status sp_bc_wait(sp_server s, sp_request req, int64_t timeout_ns); /* SP_NOT_READY on timeout */
 SP_API sp_status sp_bc_cancel(sp_server s, sp_request req);

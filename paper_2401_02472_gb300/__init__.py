@@ -98,6 +98,8 @@ SIGNATURES = {
     "sp_server_create": ([_SZ, _I32, _P], ctypes.c_int),
     "sp_server_add_graph": ([_P, _P, _P], ctypes.c_int),
     "sp_bc_submit": ([_P, _I32, _P, _I32, _P, _P, _P], ctypes.c_int),
+    "sp_pagerank_submit": ([_P, _I32, ctypes.c_double, ctypes.c_double, _I32, _P, _P], ctypes.c_int),
+    "sp_request_pagerank": ([_P, _I64, _P, _P], ctypes.c_int),
     "sp_bc_poll": ([_P, _I64], ctypes.c_int),
     "sp_bc_wait": ([_P, _I64, _I64], ctypes.c_int),
     "sp_bc_cancel": ([_P, _I64], ctypes.c_int),
@@ -325,6 +327,24 @@ def sp_bc_submit(s: int, graph_id: int, sources, bc_out, opts: sp_bc_opts | None
                             ctypes.byref(opts) if opts is not None else None, _ptr(bc_out), ctypes.byref(req)),
            "sp_bc_submit")
     return req.value
+
+
+def sp_pagerank_submit(s: int, graph_id: int, pr_out, damping: float = 0.85, tol: float = 1e-10,
+                       max_iter: int = 100) -> int:
+    _check_dtype(pr_out, "float64", "pr_out")
+    req = ctypes.c_int64()
+    _check(lib.sp_pagerank_submit(s, graph_id, float(damping), float(tol), int(max_iter), _ptr(pr_out),
+                                  ctypes.byref(req)), "sp_pagerank_submit")
+    return req.value
+
+
+def sp_request_pagerank(s: int, req: int):
+    """(status, iterations, last change) of a PageRank request; status SP_NOT_READY while it runs."""
+    it, ch = ctypes.c_int32(), ctypes.c_double()
+    rc = lib.sp_request_pagerank(s, req, ctypes.byref(it), ctypes.byref(ch))
+    if rc not in (SP_OK, SP_NOT_READY):
+        _check(rc, "sp_request_pagerank")
+    return rc, it.value, ch.value
 
 
 def sp_bc_poll(s: int, req: int) -> int:

@@ -1416,6 +1416,25 @@ sp_status bc_device_entry(Graph* g, const int32_t* d_src, int32_t nsrc, const sp
     return bc_device(g, d_src, nsrc, o, d_bc, stats, st);
 }
 
+// PageRank into device memory, waiting for the result (serving requests).
+sp_status pagerank_device_entry(Graph* g, double damping, double tol, int32_t max_iter, double* d_pr,
+                                PrResult* result, cudaStream_t st) {
+    if (g->n == 0) return SP_OK;
+    PrLaunch L{};
+    L.g = g;
+    L.damping = damping;
+    L.tol = tol;
+    L.max_iter = max_iter;
+    L.timeout_ns = bfs_timeout_ns();
+    L.stream = st;
+    L.d_pr = d_pr;
+    sp_status rc = run_pagerank(L, result);
+    if (rc == SP_OK) rc = map_device_error(result->err, "pagerank", result->diag);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == SP_OK && e != cudaSuccess) rc = cuda_fail(e, "pagerank request");
+    return rc;
+}
+
 // The graph's mapped flags (error and hint words of asynchronous calls).
 static sp_status alloc_flags(Graph* g) {
     void* hp = nullptr;

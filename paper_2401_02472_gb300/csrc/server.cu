@@ -24,6 +24,10 @@
 // A request's words, the order of their lanes and the order in which its BC
 // is added depend only on the request, so its result is bit-identical alone
 // or in any mix of other requests.
+//
+// PageRank requests (the paper's second resident-graph workload, Section
+// 3.3) share the queue, the admission budget and the slots; each runs alone
+// in one persistent launch on its slot's stream.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -42,6 +46,8 @@ namespace sp {
 // Defined in api.cu.
 sp_status bc_device_entry(Graph* g, const int32_t* d_src, int32_t nsrc, const sp_bc_opts& o, double* d_bc,
                           sp_bc_stats* stats, cudaStream_t st);
+sp_status pagerank_device_entry(Graph* g, double damping, double tol, int32_t max_iter, double* d_pr,
+                                PrResult* result, cudaStream_t st);
 int default_batch_width(int32_t nsrc);
 size_t batched_workspace_bytes(const Graph* g, int width, bool theta_f32);
 
@@ -50,9 +56,17 @@ static int64_t now_ns() {
         .count();
 }
 
+enum class ReqKind : int { BC = 0, PAGERANK = 1 };
+
 struct Request {
     sp_request id = 0;
+    ReqKind kind = ReqKind::BC;
     Graph* g = nullptr;
+    // PageRank requests: parameters and result
+    double damping = 0.85, tol = 0.0;
+    int32_t max_iter = 0;
+    int32_t pr_iterations = 0;
+    double pr_change = 0.0;
     std::vector<int32_t> sources;
     sp_bc_opts opts{};
     double* bc_out = nullptr;
@@ -112,7 +126,8 @@ struct Server {
 
     // Requests that can share r's launch: same graph, same options, batched.
     static bool compatible(const Request& r, const Request& x) {
-        return x.g == r.g && !x.cancelled && x.sources.size() >= 2 && x.opts.precision == r.opts.precision &&
+        return x.kind == ReqKind::BC && r.kind == ReqKind::BC && x.g == r.g && !x.cancelled &&
+               x.sources.size() >= 2 && x.opts.precision == r.opts.precision &&
                x.opts.form == r.opts.form && x.opts.flags == r.opts.flags && x.opts.max_ctas == r.opts.max_ctas &&
                x.opts.batch == r.opts.batch && x.opts.debug_flags == 0 && r.opts.debug_flags == 0;
     }
@@ -133,7 +148,8 @@ struct Server {
             lk.unlock();
             sp_bc_opts o = r->opts;
 
-            const bool batched = !r->cancelled && request_is_batched(r->g, (int32_t)r->sources.size(), o, st);
+            const bool batched = !r->cancelled && r->kind == ReqKind::BC &&
+                                 request_is_batched(r->g, (int32_t)r->sources.size(), o, st);
             std::vector<std::shared_ptr<Request>> group{r};
             if (batched) {
                 // continuous batching: admitted requests on the same graph join
@@ -167,6 +183,16 @@ struct Server {
                 for (size_t i = 0; i < group.size(); ++i) {
                     rcs[i] = rc;
                     sts[i] = parts[i].stats;
+                }
+            } else if (!r->cancelled && r->kind == ReqKind::PAGERANK) {
+                PrResult pr;
+                rcs[0] = pagerank_device_entry(r->g, r->damping, r->tol, r->max_iter, r->bc_out, &pr, st);
+                if (rcs[0] == SP_OK) {
+                    r->pr_iterations = pr.iterations;
+                    r->pr_change = pr.change;
+                    sts[0].kernel_ms = pr.kernel_ms;
+                    sts[0].launches = pr.launches;
+                    sts[0].traversed_arcs = (int64_t)r->g->nnz * (int64_t)pr.iterations;
                 }
             } else if (!r->cancelled) {
                 const int cnt = (int)r->sources.size();
@@ -300,6 +326,67 @@ sp_status sp_bc_submit(sp_server sh, int32_t graph_id, const int32_t* sources, i
     }
     *req = r->id;
     return SP_OK;
+}
+
+sp_status sp_pagerank_submit(sp_server sh, int32_t graph_id, double damping, double tol, int32_t max_iter,
+                             double* pr_out, sp_request* req) {
+    set_last_error("");
+    if (!sh || !req) return fail(SP_ERR_INVALID_ARG, "NULL argument");
+    Server* s = reinterpret_cast<Server*>(sh);
+    Graph* g = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size()) return fail(SP_ERR_INVALID_ARG, "graph_id");
+        g = s->graphs[graph_id];
+    }
+    if (!(damping >= 0.0 && damping <= 1.0)) return fail(SP_ERR_INVALID_ARG, "damping must be in [0, 1]");
+    if (max_iter < 0) return fail(SP_ERR_INVALID_ARG, "max_iter < 0");
+    if (g->n > 0) {
+        if (!pr_out) return fail(SP_ERR_INVALID_ARG, "pr_out is NULL");
+        cudaPointerAttributes at{};
+        const bool ok = cudaPointerGetAttributes(&at, pr_out) == cudaSuccess &&
+                        (at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == g->device));
+        cudaGetLastError();
+        if (!ok) return fail(SP_ERR_INVALID_ARG, "pr_out must be device memory of the graph's GPU");
+    }
+    auto r = std::make_shared<Request>();
+    r->kind = ReqKind::PAGERANK;
+    r->g = g;
+    r->bc_out = pr_out;
+    sp_bc_opts_default(&r->opts);
+    r->damping = damping;
+    r->tol = tol;
+    r->max_iter = max_iter;
+    // the launch's own vectors (two rank vectors, rank / out-degree, changes) and the hub plan
+    r->footprint = (size_t)g->n * 32 + (size_t)g->knnz() / 64 + 4096;
+    r->t_submit = now_ns();
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    s->reqs[r->id] = r;
+    if (g->n == 0) {
+        r->status = SP_OK;
+        r->finished = true;
+        r->t_start = r->t_done = now_ns();
+    } else {
+        s->waiting.push_back(r);
+        s->admit_locked();
+        s->cv_work.notify_all();
+    }
+    *req = r->id;
+    return SP_OK;
+}
+
+sp_status sp_request_pagerank(sp_server sh, sp_request req, int32_t* iterations, double* change) {
+    if (!sh) return fail(SP_ERR_INVALID_ARG, "server is NULL");
+    Server* s = reinterpret_cast<Server*>(sh);
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(req);
+    if (it == s->reqs.end()) return fail(SP_ERR_INVALID_ARG, "unknown request");
+    if (it->second->kind != ReqKind::PAGERANK) return fail(SP_ERR_INVALID_ARG, "not a PageRank request");
+    if (!it->second->finished) return SP_NOT_READY;
+    if (iterations) *iterations = it->second->pr_iterations;
+    if (change) *change = it->second->pr_change;
+    return it->second->status;
 }
 
 sp_status sp_bc_poll(sp_server sh, sp_request req) {

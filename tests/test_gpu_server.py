@@ -145,3 +145,44 @@ def test_requests_on_one_graph_share_launches():
         assert st["form"] == sp.SP_FORM_BATCHED
         alone, _, _ = serve(Gs, [(gi, srcs, prec)], slots=1)
         assert np.array_equal(alone[0], got), (gi, len(srcs))
+
+
+def test_pagerank_requests_share_the_server_with_bc(graphs):
+    # PageRank requests (the paper's second workload on resident graphs) run
+    # through the same queue and slots as BC requests: each result equals the
+    # oracle's and, bit for bit, a direct sp_pagerank call on the same graph.
+    gs, Gs = graphs
+    s = sp.sp_server_create(8 << 30, 2)
+    ids = [sp.sp_server_add_graph(s, G.handle) for G in Gs]
+    jobs = []
+    for i, gi in enumerate([0, 1, 2, 0]):
+        srcs = gen.sources(gs[gi], 40, 300 + i)
+        bc = torch.full((Gs[gi].n,), -1.0, dtype=torch.float64, device=DEV)
+        hb = sp.sp_bc_submit(s, ids[gi], srcs, bc, sp.make_opts(precision=sp.SP_FP64))
+        pr = torch.full((Gs[gi].n,), -1.0, dtype=torch.float64, device=DEV)
+        iters = 5 + 3 * i
+        hp = sp.sp_pagerank_submit(s, ids[gi], pr, 0.85, -1.0, iters)
+        jobs.append((gi, srcs, bc, hb, pr, hp, iters))
+    for gi, srcs, bc, hb, pr, hp, iters in jobs:
+        assert sp.sp_bc_wait(s, hb) == sp.SP_OK
+        assert sp.sp_bc_wait(s, hp) == sp.SP_OK
+        rc, it, ch = sp.sp_request_pagerank(s, hp)
+        assert rc == sp.SP_OK and it == iters
+        st = sp.sp_request_stats(s, hp)
+        assert st["traversed_arcs"] == gs[gi].nnz * iters and st["kernel_ms"] > 0
+        want, wit, wch = oracle.pagerank(gs[gi], 0.85, -1.0, iters)
+        got = pr.cpu().numpy()
+        assert np.all(np.abs(got - want) <= 1e-10 * np.abs(want))
+        direct = torch.empty(Gs[gi].n, dtype=torch.float64, device=DEV)
+        dit, dch = sp.sp_pagerank(Gs[gi].handle, direct, 0.85, -1.0, iters)
+        assert np.array_equal(direct.cpu().numpy(), got) and dit == it and dch == ch
+        assert close(bc.cpu().numpy(), oracle.bc(gs[gi], srcs)[0], RTOL[sp.SP_FP64])
+    # a BC handle is not a PageRank request; bad arguments are refused at submission
+    with pytest.raises(sp.StarbcError):
+        sp.sp_request_pagerank(s, jobs[0][3])
+    bad = torch.empty(Gs[0].n, dtype=torch.float64, device=DEV)
+    with pytest.raises(sp.StarbcError):
+        sp.sp_pagerank_submit(s, ids[0], bad, 1.5, -1.0, 3)
+    with pytest.raises(sp.StarbcError):
+        sp.sp_pagerank_submit(s, ids[0], np.empty(Gs[0].n), 0.85, -1.0, 3)
+    sp.sp_server_destroy(s)
