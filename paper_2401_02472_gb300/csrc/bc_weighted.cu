@@ -39,6 +39,7 @@ namespace {
 
 constexpr int kWThreads = 512;
 constexpr int kWLane = 16;  // rows of at most this many arcs are walked by one lane
+constexpr int kG = 4;       // arcs of a lane's row whose loads are in flight together
 constexpr int kUnreached = INT_MAX;
 
 struct WArgs {
@@ -160,8 +161,42 @@ __global__ void __launch_bounds__(kWThreads, 2) weighted_kernel(WArgs a) {
                         if (atomicExch(&stamp[x], round) != round) nxt[atomicAdd(&s_cnt[0], 1)] = x;
                     }
                 };
-                if (deg <= kWLane)
-                    for (int k = 0; k < deg; ++k) relax(beg + k, du);
+                if (deg <= kWLane) {
+                    // a lane's row, kG arcs at a time: their ids and weights,
+                    // then their atomicMin, then the frontier updates, each
+                    // issued for all kG arcs before any result is used
+                    for (int k0 = 0; k0 < deg; k0 += kG) {
+                        int x[kG], nd[kG], old[kG];
+#pragma unroll
+                        for (int q = 0; q < kG; ++q) {
+                            const bool ok = k0 + q < deg;
+                            x[q] = ok ? __ldg(&a.ci[beg + k0 + q]) : -1;
+                            nd[q] = ok ? du + __ldg(&a.w[beg + k0 + q]) : 0;
+                        }
+#pragma unroll
+                        for (int q = 0; q < kG; ++q) {
+                            old[q] = kUnreached;
+                            if (x[q] >= 0) {
+                                if (nd[q] >= a.hcap) {
+                                    atomicCAS(&s_err, 0, kErrCapLevels);
+                                    x[q] = -1;
+                                } else {
+                                    old[q] = atomicMin(&dist[x[q]], nd[q]);
+                                }
+                            }
+                        }
+                        int ts[kG];
+#pragma unroll
+                        for (int q = 0; q < kG; ++q) {
+                            const bool better = x[q] >= 0 && nd[q] < old[q];
+                            if (better && old[q] == kUnreached) reach[atomicAdd(&s_cnt[1], 1)] = x[q];
+                            ts[q] = better ? atomicExch(&stamp[x[q]], round) : round;
+                        }
+#pragma unroll
+                        for (int q = 0; q < kG; ++q)
+                            if (ts[q] != round) nxt[atomicAdd(&s_cnt[0], 1)] = x[q];
+                    }
+                }
                 unsigned wide = __ballot_sync(kFull, i < fsize && deg > kWLane);
                 while (wide) {
                     const int j = __ffs(wide) - 1;
@@ -236,10 +271,23 @@ __global__ void __launch_bounds__(kWThreads, 2) weighted_kernel(WArgs a) {
                     }
                     double acc = 0.0;
                     if (deg <= kWLane)
-                        for (int k = 0; k < deg; ++k) {
-                            const int u = __ldg(&a.ci[beg + k]);
-                            const int du = dist[u];
-                            if (du != kUnreached && du + __ldg(&a.w[beg + k]) == dv) acc += sig[u];
+                        for (int k0 = 0; k0 < deg; k0 += kG) {  // kG arcs in flight, summed in CSR order
+                            int u[kG], wt[kG], du[kG];
+                            double c[kG];
+#pragma unroll
+                            for (int q = 0; q < kG; ++q) {
+                                const bool ok = k0 + q < deg;
+                                u[q] = ok ? __ldg(&a.ci[beg + k0 + q]) : -1;
+                                wt[q] = ok ? __ldg(&a.w[beg + k0 + q]) : 0;
+                            }
+#pragma unroll
+                            for (int q = 0; q < kG; ++q) du[q] = u[q] >= 0 ? dist[u[q]] : kUnreached;
+#pragma unroll
+                            for (int q = 0; q < kG; ++q)
+                                c[q] = du[q] != kUnreached && du[q] + wt[q] == dv ? sig[u[q]] : 0.0;
+#pragma unroll
+                            for (int q = 0; q < kG; ++q)
+                                if (k0 + q < deg && du[q] != kUnreached && du[q] + wt[q] == dv) acc += c[q];
                         }
                     unsigned wide = __ballot_sync(kFull, i < e && deg > kWLane);
                     while (wide) {
@@ -280,10 +328,23 @@ __global__ void __launch_bounds__(kWThreads, 2) weighted_kernel(WArgs a) {
                     }
                     double acc = 0.0;
                     if (deg <= kWLane)
-                        for (int k = 0; k < deg; ++k) {
-                            const int x = __ldg(&a.ci[beg + k]);
-                            const int dx = dist[x];
-                            if (dx != kUnreached && dx == dv + __ldg(&a.w[beg + k])) acc += th[x];
+                        for (int k0 = 0; k0 < deg; k0 += kG) {  // kG arcs in flight, summed in CSR order
+                            int x[kG], wt[kG], dx[kG];
+                            double c[kG];
+#pragma unroll
+                            for (int q = 0; q < kG; ++q) {
+                                const bool ok = k0 + q < deg;
+                                x[q] = ok ? __ldg(&a.ci[beg + k0 + q]) : -1;
+                                wt[q] = ok ? __ldg(&a.w[beg + k0 + q]) : 0;
+                            }
+#pragma unroll
+                            for (int q = 0; q < kG; ++q) dx[q] = x[q] >= 0 ? dist[x[q]] : kUnreached;
+#pragma unroll
+                            for (int q = 0; q < kG; ++q)
+                                c[q] = dx[q] != kUnreached && dx[q] == dv + wt[q] ? th[x[q]] : 0.0;
+#pragma unroll
+                            for (int q = 0; q < kG; ++q)
+                                if (x[q] >= 0 && dx[q] != kUnreached && dx[q] == dv + wt[q]) acc += c[q];
                         }
                     unsigned wide = __ballot_sync(kFull, i < e && deg > kWLane);
                     while (wide) {
