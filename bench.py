@@ -617,6 +617,102 @@ def run_approx(args, rank, world, dist):
                    "rounds": [s["rounds"] for s in sts], "kernel_ms": [s["kernel_ms"] for s in sts]}}), flush=True)
 
 
+# Configurations beside the default one, measured in the same run after its
+# timed region (N=1 only), so that every configuration has a number taken in
+# the same process under the same clocks: a resident graph, CUDA events on the
+# launching stream around each step, inputs larger than L2 except the small
+# ER graph (L2-resident by size).
+OTHER_CONFIGS = [
+    ("er2000_all", None, 0),
+    ("rmat20_64src_batched", None, 0),
+    ("rmat20_64src_batched", "plain", 0),
+    ("knn4_1m_256src", None, 0),
+    ("rmat22_1024src_batched", "plain", 128),
+    ("drmat22_1024src_batched", None, 0),
+    ("rmat20_weighted_256src", None, 0),
+]
+
+
+def measure_other_configs(sp, torch, dev, graphs, steps=3, warmup=2):
+    """One record per configuration (GTEPS, ms per step, kernel ms, form), then
+    PageRank on the default graph; a configuration that fails records its error."""
+    out = []
+    stream = torch.cuda.current_stream()
+    forms = {"auto": sp.SP_FORM_AUTO, "plain": sp.SP_FORM_PLAIN, "batched": sp.SP_FORM_BATCHED,
+             "small": sp.SP_FORM_SMALL}
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        last = None
+        for a, b in ev:
+            a.record(stream)
+            last = fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], last
+
+    for name, form_override, nsrc in OTHER_CONFIGS:
+        t0 = time.perf_counter()
+        rec = {"workload": name + (f"/{form_override}" if form_override else "") + (f"/{nsrc}src" if nsrc else "")}
+        G = None
+        try:
+            w = dict(WORKLOADS[name])
+            if form_override:
+                w["form"] = form_override
+            if w["graph"] not in graphs:
+                graphs[w["graph"]] = gen.workload_graph(w["graph"])
+            g = graphs[w["graph"]]
+            srcs = np.arange(min(w["nsrc"], g.n), dtype=np.int32) if w["seed"] is None \
+                else gen.sources(g, w["nsrc"], w["seed"])
+            if nsrc:
+                srcs = srcs[:nsrc]
+            prec = sp.SP_FP32_DELTA if w["precision"] == "fp32_delta" else sp.SP_FP64
+            opts = sp.make_opts(precision=prec, form=forms[w["form"]])
+            G = make_graph(sp, w, g, torch.as_tensor(g.row_ptr, device=dev), torch.as_tensor(g.col_idx, device=dev))
+            d_src = torch.as_tensor(srcs, device=dev)
+            d_bc = torch.empty(g.n, dtype=torch.float64, device=dev)
+            ms, st = timed(lambda: sp.sp_bc_ex(G, d_src, d_bc, opts))
+            mean = sum(ms) / len(ms)
+            rec.update({"metric": "BC GTEPS (fwd+bwd)", "value": st["traversed_arcs"] / (mean / 1e3) / 1e9,
+                        "unit": "GTEPS", "ms_per_step": mean, "kernel_ms": st["kernel_ms"], "step_ms": ms,
+                        "sources": int(len(srcs)),
+                        "form": {1: "plain", 2: "batched", 3: "small", 4: "weighted"}.get(st["form"], st["form"]),
+                        "batch": st["batch"], "max_levels": st["max_levels"], "promoted": st["promoted"]})
+        except Exception as e:  # recorded, not fatal: the default line stands on its own
+            rec["error"] = str(e)[:300]
+        finally:
+            if G is not None:
+                sp.sp_graph_destroy(G)
+        rec["wall_s"] = time.perf_counter() - t0
+        out.append(rec)
+    # PageRank, 20 iterations, on the default graph
+    t0 = time.perf_counter()
+    rec = {"workload": "pagerank_rmat22"}
+    G = None
+    try:
+        w = WORKLOADS["pagerank_rmat22"]
+        g = graphs[w["graph"]] if w["graph"] in graphs else gen.workload_graph(w["graph"])
+        G = make_graph(sp, w, g, torch.as_tensor(g.row_ptr, device=dev), torch.as_tensor(g.col_idx, device=dev))
+        pr = torch.empty(g.n, dtype=torch.float64, device=dev)
+        ms, _ = timed(lambda: sp.sp_pagerank(G, pr, 0.85, -1.0, w["iterations"], want_result=False))
+        sp.sp_graph_sync(G)
+        mean = sum(ms) / len(ms)
+        rec.update({"metric": "PageRank GTEPS (arcs x iterations / s)", "unit": "GTEPS",
+                    "value": float(g.nnz) * w["iterations"] / (mean / 1e3) / 1e9, "ms_per_step": mean,
+                    "step_ms": ms, "iterations": w["iterations"]})
+    except Exception as e:
+        rec["error"] = str(e)[:300]
+    finally:
+        if G is not None:
+            sp.sp_graph_destroy(G)
+    rec["wall_s"] = time.perf_counter() - t0
+    out.append(rec)
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -733,6 +829,12 @@ def run_ours(args, rank, world, dist):
     pair_alg = pair_model_bytes(s, g.n, theta_bytes, s["batch"], s["batches"])
     pair_achieved = pair_alg / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0
     launches_per_step = s["launches"]
+    others, clk_others = None, None
+    if world == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_other_configs:
+        clocks_o = ClockSampler(local)
+        clocks_o.start()
+        others = measure_other_configs(sp, torch, dev, {w["graph"]: g})
+        clk_others = clocks_o.stop()
     base = cpu_baseline(g, srcs, args.cpu_budget) if not args.no_cpu_baseline else None
     line = {
         "metric": "BC GTEPS (fwd+bwd)",
@@ -778,6 +880,10 @@ def run_ours(args, rank, world, dist):
                    # the other TEPS convention: every arc of the graph once per source
                    "gteps_arcs_x_sources": g.nnz * len(srcs) * args.steps / (total_ms_max / 1e3) / 1e9 * world},
     }
+    if others is not None:
+        line["other_configs"] = {"note": "measured after the timed region, same run: resident graph, 2 warm-up "
+                                         "and 3 timed steps each, CUDA events", "clocks": clk_others,
+                                 "results": others}
     print(json.dumps(line), flush=True)
 
 
@@ -798,6 +904,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="default workload: skip the other configurations measured after its timed region")
     ap.add_argument("--ref-sources", type=int, default=0,
                     help="reference arm: oracle sources per step (0 = one per host thread)")
     ap.add_argument("--duration", type=float, default=30.0, help="serving: measured stream length (s)")

@@ -1508,16 +1508,21 @@ sp_status sp_graph_create(const int32_t* row_ptr, const int32_t* col_idx, int32_
     g->n = n;
     g->nnz = nnz;
     auto cleanup = [&](sp_status s) {
-        if (g->d_rp) cudaFree(g->d_rp);
-        if (g->d_ci) cudaFree(g->d_ci);
+        cudaStreamSynchronize(st);
+        if (g->d_rp) cudaFreeAsync(g->d_rp, st);
+        if (g->d_ci) cudaFreeAsync(g->d_ci, st);
         if (g->d_crp) cudaFree(g->d_crp);
         if (g->d_cci) cudaFree(g->d_cci);
         if (g->d_odeg) cudaFree(g->d_odeg);
+        cudaStreamSynchronize(st);
         delete g;
         return s;
     };
-    if (cudaMalloc((void**)&g->d_rp, sizeof(int32_t) * ((size_t)n + 1)) != cudaSuccess ||
-        cudaMalloc((void**)&g->d_ci, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)) != cudaSuccess) {
+    // the CSR from the library's memory pool: creating a graph after another
+    // was destroyed reuses memory that is already mapped
+    g->pooled_csr = true;
+    if (workspace_alloc((void**)&g->d_rp, sizeof(int32_t) * ((size_t)n + 1), st) != cudaSuccess ||
+        workspace_alloc((void**)&g->d_ci, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1), st) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(fail(SP_ERR_OOM, "graph arrays"));
     }
@@ -1637,8 +1642,15 @@ sp_status sp_graph_destroy(sp_graph gh) {
     if (g->d_land_dist) cudaFree(g->d_land_dist);
     destroy_step_cache(g);
     destroy_pr_plan(g);
-    cudaFree(g->d_rp);  // waits for work still running on the graph
-    cudaFree(g->d_ci);
+    cudaDeviceSynchronize();  // waits for work still running on the graph
+    if (g->pooled_csr) {
+        cudaFreeAsync(g->d_rp, 0);
+        cudaFreeAsync(g->d_ci, 0);
+        cudaStreamSynchronize(0);
+    } else {
+        cudaFree(g->d_rp);
+        cudaFree(g->d_ci);
+    }
     if (g->d_crp) cudaFree(g->d_crp);
     if (g->d_cci) cudaFree(g->d_cci);
     if (g->d_odeg) cudaFree(g->d_odeg);

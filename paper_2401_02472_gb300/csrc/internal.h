@@ -51,6 +51,9 @@ struct Graph {
     int64_t nnz = 0;
     int32_t* d_rp = nullptr;  // [n+1]
     int32_t* d_ci = nullptr;  // [max(nnz,1)]
+    // d_rp / d_ci come from the library's memory pool (sp_graph_create: a
+    // destroyed graph's arrays stay mapped for the next one) rather than cudaMalloc
+    bool pooled_csr = false;
     sp_graph_info info{};
     // Directed graphs: the kernels read combined rows (out-arcs, then in-arcs
     // tagged with the top bit) and count traversed arcs by out-degree.  For an
