@@ -366,7 +366,7 @@ SP_API sp_status sp_pagerank(sp_graph g, double damping, double tol, int32_t max
  *   bc_out is overwritten.  The call is synchronous: it returns after its
  *   kernels have finished and the result is complete.
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call uses
+ * device).  Every call uses
  * the same array, so calls that overlap on the GPU (other streams or host
  * threads) race and must be serialised by the caller.
  */
