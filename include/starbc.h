@@ -170,7 +170,7 @@ SP_API sp_status sp_graph_from_edges(const int32_t* src, const int32_t* dst, int
  * with the arc in sp_last_error(); directed graphs: SP_ERR_INVALID_ARG).  From
  * then on sp_bc / sp_bc_ex compute BC with shortest paths by total weight in
  * the weighted form (SP_FORM_WEIGHTED, one block per source: distances by
- * Bellman-Ford frontier rounds with atomicMin, path counts and dependencies
+ * near-far frontier rounds with atomicMin, path counts and dependencies
  * in FP64 over the weighted shortest-path DAG, level by level in distance
  * order); those calls return when the result is complete, and the precision
  * option does not apply (FP64).  sp_bfs still gives hop distances.

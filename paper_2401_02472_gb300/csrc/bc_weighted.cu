@@ -6,10 +6,16 @@
 // dist[v] + weight with atomicMin and mark the neighbour modified).  Per
 // source a block runs, with __syncthreads as its only barrier:
 //
-//   distances  Bellman-Ford frontier rounds: the vertices whose distance fell
-//              in the last round relax their arcs with atomicMin; a vertex
-//              joins the next frontier once per round (a round stamp); the
-//              first arrival at a vertex lists it as reached
+//   distances  near-far frontier rounds (Davidson et al., IPDPS 2014): the
+//              vertices whose distance fell below a threshold T in the last
+//              round relax their arcs with atomicMin and join the next round
+//              once (a round stamp); a vertex whose new distance is at least T
+//              goes to a far pile instead (once, a flag).  When no near vertex
+//              is left, T moves to the smallest far distance + delta (the
+//              mean arc weight) and the far vertices below it become the
+//              next near frontier.  A vertex is expanded at most once per
+//              distance it takes; the first arrival at a vertex lists it as
+//              reached
 //   order      a counting sort of the reached vertices by distance, then the
 //              boundaries of the runs of equal distance (the "levels")
 //   sigma      level by level in increasing distance: sigma(v) = sum over
@@ -63,6 +69,11 @@ struct WArgs {
     int32_t hcap;     // distances must stay below this
     Ctl* ctl;
     int32_t* dist_out;  // SSSP mode: [nsrc][n] distances (-1 unreachable), else null
+    int32_t* far0;      // [n] far pile, two buffers
+    int32_t* far1;      // [n]
+    int32_t* infar;     // [n] 1 while the vertex is in the far pile
+    int32_t* expd;      // [n] distance at which the vertex was last expanded (-1: never)
+    int32_t delta;      // near-far step
 };
 
 // Block-wide exclusive scan of cnt[0..m) in place (cnt[m] receives the total);
@@ -99,6 +110,7 @@ __global__ void __launch_bounds__(kWThreads, 2) weighted_kernel(WArgs a) {
     __shared__ int s_cnt[2];  // frontier fill (next), reached fill
     __shared__ int s_err;
     __shared__ int s_max;
+    __shared__ int s_far, s_far2, s_min;  // far pile fill (current, next), its smallest distance
     __shared__ unsigned long long s_st[3];
     const int n = a.n;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid / kWarp, nwarps = blockDim.x / kWarp;
@@ -114,12 +126,18 @@ __global__ void __launch_bounds__(kWThreads, 2) weighted_kernel(WArgs a) {
     double* sig = a.sig + off;
     double* th = a.th + off;
     double* bcp = a.bcpart + off;
+    int32_t* fcur = a.far0 + off;
+    int32_t* fnxt = a.far1 + off;
+    int32_t* infar = a.infar + off;
+    int32_t* expd = a.expd + off;
     unsigned long long st_arcs = 0, st_reached = 0, st_scanned = 0;
     int levels_max = 0;
     if (tid == 0) s_err = 0;
     for (int v = tid; v < n; v += blockDim.x) {
         dist[v] = kUnreached;
         stamp[v] = -1;
+        infar[v] = 0;
+        expd[v] = -1;
         if (a.dist_out == nullptr) bcp[v] = 0.0;
     }
     __syncthreads();
@@ -133,85 +151,125 @@ __global__ void __launch_bounds__(kWThreads, 2) weighted_kernel(WArgs a) {
             reach[0] = s;
             s_cnt[0] = 0;
             s_cnt[1] = 1;
+            s_far = 0;
         }
         __syncthreads();
-        // ---- distances: frontier rounds ----
+        // ---- distances: near-far frontier rounds ----
         int fsize = 1;
         int32_t* cur = f0;
         int32_t* nxt = f1;
-        while (fsize > 0) {
-            ++round;
-            for (int i0 = warp * 32; i0 < fsize; i0 += nwarps * 32) {
-                const int i = i0 + lane;
-                int u = 0, beg = 0, deg = 0, du = 0;
-                if (i < fsize) {
-                    u = cur[i];
-                    beg = __ldg(&a.rp[u]);
-                    deg = __ldg(&a.rp[u + 1]) - beg;
-                    du = ld_volatile(&dist[u]);
-                    st_scanned += (unsigned long long)deg;
-                }
-                auto relax = [&](int e, int d0) {
-                    const int x = __ldg(&a.ci[e]);
-                    const int nd = d0 + __ldg(&a.w[e]);
-                    if (nd >= a.hcap) { atomicCAS(&s_err, 0, kErrCapLevels); return; }
-                    const int old = atomicMin(&dist[x], nd);
-                    if (nd < old) {
-                        if (old == kUnreached) reach[atomicAdd(&s_cnt[1], 1)] = x;
-                        if (atomicExch(&stamp[x], round) != round) nxt[atomicAdd(&s_cnt[0], 1)] = x;
-                    }
-                };
-                if (deg <= kWLane) {
-                    // a lane's row, kG arcs at a time: their ids and weights,
-                    // then their atomicMin, then the frontier updates, each
-                    // issued for all kG arcs before any result is used
-                    for (int k0 = 0; k0 < deg; k0 += kG) {
-                        int x[kG], nd[kG], old[kG];
-#pragma unroll
-                        for (int q = 0; q < kG; ++q) {
-                            const bool ok = k0 + q < deg;
-                            x[q] = ok ? __ldg(&a.ci[beg + k0 + q]) : -1;
-                            nd[q] = ok ? du + __ldg(&a.w[beg + k0 + q]) : 0;
+        int thr = a.delta;  // near: distance below thr
+        int splits = 0;
+        while (true) {
+            while (fsize > 0) {
+                ++round;
+                for (int i0 = warp * 32; i0 < fsize; i0 += nwarps * 32) {
+                    const int i = i0 + lane;
+                    int u = 0, beg = 0, deg = 0, du = 0;
+                    if (i < fsize) {
+                        u = cur[i];
+                        du = ld_volatile(&dist[u]);
+                        if (expd[u] != du) {  // not yet expanded at this distance
+                            expd[u] = du;
+                            beg = __ldg(&a.rp[u]);
+                            deg = __ldg(&a.rp[u + 1]) - beg;
+                            st_scanned += (unsigned long long)deg;
                         }
+                    }
+                    // a vertex whose distance fell: the next near round, or the far pile
+                    auto improved = [&](int x, int nd, int old) {
+                        if (old == kUnreached) reach[atomicAdd(&s_cnt[1], 1)] = x;
+                        if (nd < thr) {
+                            if (atomicExch(&stamp[x], round) != round) nxt[atomicAdd(&s_cnt[0], 1)] = x;
+                        } else if (atomicExch(&infar[x], 1) == 0) {
+                            fcur[atomicAdd(&s_far, 1)] = x;
+                        }
+                    };
+                    auto relax = [&](int e, int d0) {
+                        const int x = __ldg(&a.ci[e]);
+                        const int nd = d0 + __ldg(&a.w[e]);
+                        if (nd >= a.hcap) { atomicCAS(&s_err, 0, kErrCapLevels); return; }
+                        const int old = atomicMin(&dist[x], nd);
+                        if (nd < old) improved(x, nd, old);
+                    };
+                    if (deg <= kWLane) {
+                        // a lane's row, kG arcs at a time: their ids and weights,
+                        // then their atomicMin, then the frontier updates, each
+                        // issued for all kG arcs before any result is used
+                        for (int k0 = 0; k0 < deg; k0 += kG) {
+                            int x[kG], nd[kG], old[kG];
 #pragma unroll
-                        for (int q = 0; q < kG; ++q) {
-                            old[q] = kUnreached;
-                            if (x[q] >= 0) {
-                                if (nd[q] >= a.hcap) {
-                                    atomicCAS(&s_err, 0, kErrCapLevels);
-                                    x[q] = -1;
-                                } else {
-                                    old[q] = atomicMin(&dist[x[q]], nd[q]);
+                            for (int q = 0; q < kG; ++q) {
+                                const bool ok = k0 + q < deg;
+                                x[q] = ok ? __ldg(&a.ci[beg + k0 + q]) : -1;
+                                nd[q] = ok ? du + __ldg(&a.w[beg + k0 + q]) : 0;
+                            }
+#pragma unroll
+                            for (int q = 0; q < kG; ++q) {
+                                old[q] = kUnreached;
+                                if (x[q] >= 0) {
+                                    if (nd[q] >= a.hcap) {
+                                        atomicCAS(&s_err, 0, kErrCapLevels);
+                                        x[q] = -1;
+                                    } else {
+                                        old[q] = atomicMin(&dist[x[q]], nd[q]);
+                                    }
                                 }
                             }
-                        }
-                        int ts[kG];
 #pragma unroll
-                        for (int q = 0; q < kG; ++q) {
-                            const bool better = x[q] >= 0 && nd[q] < old[q];
-                            if (better && old[q] == kUnreached) reach[atomicAdd(&s_cnt[1], 1)] = x[q];
-                            ts[q] = better ? atomicExch(&stamp[x[q]], round) : round;
+                            for (int q = 0; q < kG; ++q)
+                                if (x[q] >= 0 && nd[q] < old[q]) improved(x[q], nd[q], old[q]);
                         }
-#pragma unroll
-                        for (int q = 0; q < kG; ++q)
-                            if (ts[q] != round) nxt[atomicAdd(&s_cnt[0], 1)] = x[q];
+                    }
+                    unsigned wide = __ballot_sync(kFull, i < fsize && deg > kWLane);
+                    while (wide) {
+                        const int j = __ffs(wide) - 1;
+                        wide &= wide - 1;
+                        const int bj = __shfl_sync(kFull, beg, j), dj = __shfl_sync(kFull, deg, j);
+                        const int dj0 = __shfl_sync(kFull, du, j);
+                        for (int k = lane; k < dj; k += kWarp) relax(bj + k, dj0);
                     }
                 }
-                unsigned wide = __ballot_sync(kFull, i < fsize && deg > kWLane);
-                while (wide) {
-                    const int j = __ffs(wide) - 1;
-                    wide &= wide - 1;
-                    const int bj = __shfl_sync(kFull, beg, j), dj = __shfl_sync(kFull, deg, j);
-                    const int dj0 = __shfl_sync(kFull, du, j);
-                    for (int k = lane; k < dj; k += kWarp) relax(bj + k, dj0);
+                __syncthreads();
+                fsize = s_cnt[0];
+                __syncthreads();
+                if (tid == 0) s_cnt[0] = 0;
+                int32_t* t = cur; cur = nxt; nxt = t;
+                if (s_err != 0) break;
+                __syncthreads();
+            }
+            if (s_err != 0) break;
+            // no near vertex left: move the threshold to the far pile
+            const int nf = s_far;
+            if (nf == 0) break;
+            if (++splits > n + 1) {  // each split takes at least one vertex out of the pile
+                if (tid == 0) atomicCAS(&s_err, 0, kErrCorrupt);
+                break;
+            }
+            if (tid == 0) { s_min = INT_MAX; s_far2 = 0; }
+            __syncthreads();
+            int mn = INT_MAX;
+            for (int i = tid; i < nf; i += blockDim.x) mn = min(mn, dist[fcur[i]]);
+            mn = warp_min_i32(mn);
+            if (lane == 0) atomicMin(&s_min, mn);
+            __syncthreads();
+            thr = s_min + a.delta;
+            ++round;
+            for (int i = tid; i < nf; i += blockDim.x) {
+                const int x = fcur[i];
+                const int dx = dist[x];
+                if (dx < thr) {
+                    infar[x] = 0;
+                    if (expd[x] != dx && atomicExch(&stamp[x], round) != round) cur[atomicAdd(&s_cnt[0], 1)] = x;
+                } else {
+                    fnxt[atomicAdd(&s_far2, 1)] = x;
                 }
             }
             __syncthreads();
             fsize = s_cnt[0];
             __syncthreads();
-            if (tid == 0) s_cnt[0] = 0;
-            int32_t* t = cur; cur = nxt; nxt = t;
-            if (s_err != 0) break;
+            if (tid == 0) { s_cnt[0] = 0; s_far = s_far2; }
+            int32_t* t = fcur; fcur = fnxt; fnxt = t;
             __syncthreads();
         }
         if (s_err != 0) break;
@@ -378,7 +436,11 @@ __global__ void __launch_bounds__(kWThreads, 2) weighted_kernel(WArgs a) {
         // order in BC mode (reach[] then holds level ends), by arrival in SSSP mode ----
         __syncthreads();
         const int32_t* reached_list = a.dist_out != nullptr ? reach : order;
-        for (int i = tid; i < nr; i += blockDim.x) dist[reached_list[i]] = kUnreached;
+        for (int i = tid; i < nr; i += blockDim.x) {
+            const int v = reached_list[i];
+            dist[v] = kUnreached;
+            expd[v] = -1;
+        }
         __syncthreads();
     }
     if (tid == 0) { s_st[0] = 0; s_st[1] = 0; s_st[2] = 0; }
@@ -409,13 +471,16 @@ __global__ void weighted_sum_kernel(const double* __restrict__ part, int nparts,
 // Arc weights: each in [1, kMaxWeight]; undirected graphs: the reverse arc
 // carries the same weight (rows sorted, found by binary search).
 __global__ void weights_check_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                     const int32_t* __restrict__ w, int32_t n, int32_t max_w, int* bad) {
+                                     const int32_t* __restrict__ w, int32_t n, int32_t max_w, int* bad,
+                                     unsigned long long* wsum) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long sum = 0;
     for (int v = warp; v < n; v += nwarp) {
         for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
             const int x = ci[e], wt = w[e];
+            sum += (unsigned long long)(unsigned)wt;
             if (wt < 1 || wt > max_w) { atomicMin(bad, e); continue; }
             int lo = rp[x], hi = rp[x + 1];
             while (lo < hi) {
@@ -425,6 +490,8 @@ __global__ void weights_check_kernel(const int32_t* __restrict__ rp, const int32
             if (!(lo < rp[x + 1] && ci[lo] == v && w[lo] == wt)) atomicMin(bad, e);
         }
     }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0 && sum != 0) atomicAdd(wsum, sum);
 }
 
 }  // namespace
@@ -435,20 +502,25 @@ sp_status set_weights(Graph* g, const int32_t* weights, bool device_src, cudaStr
         return fail(SP_ERR_INVALID_ARG, "weighted graphs need sorted rows without repeated arcs (SP_GRAPH_SORT_ROWS)");
     int32_t* d_w = nullptr;
     SP_CUDA(cudaMalloc((void**)&d_w, sizeof(int32_t) * (size_t)std::max<int64_t>(g->nnz, 1)));
-    int* d_bad = nullptr;
+    int* d_bad = nullptr;  // [0] the first bad arc (0x7F7F7F7F: none); then the weight sum (u64) at byte 8
     cudaError_t e = cudaSuccess;
     if (g->nnz > 0)
         e = cudaMemcpyAsync(d_w, weights, sizeof(int32_t) * (size_t)g->nnz,
                             device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_bad, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_bad, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0x7F, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(reinterpret_cast<char*>(d_bad) + 8, 0, 8, st);
     int bad = 0x7F7F7F7F;
+    unsigned long long wsum = 0;
     if (e == cudaSuccess && g->n > 0) {
-        weights_check_kernel<<<device_sm_count(g->device) * 8, 256, 0, st>>>(g->d_rp, g->d_ci, d_w, g->n,
-                                                                             kMaxWeight, d_bad);
+        weights_check_kernel<<<device_sm_count(g->device) * 8, 256, 0, st>>>(
+            g->d_rp, g->d_ci, d_w, g->n, kMaxWeight, d_bad,
+            reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(d_bad) + 8));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&wsum, reinterpret_cast<char*>(d_bad) + 8, 8, cudaMemcpyDeviceToHost, st);
     if (d_bad) cudaFreeAsync(d_bad, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -463,6 +535,10 @@ sp_status set_weights(Graph* g, const int32_t* weights, bool device_src, cudaStr
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->d_w) cudaFree(g->d_w);
     g->d_w = d_w;
+    // near-far step of the weighted form: the mean arc weight
+    g->w_delta = g->nnz > 0 ? (int32_t)std::max<unsigned long long>(1, (wsum + (unsigned long long)g->nnz / 2) /
+                                                                       (unsigned long long)g->nnz)
+                            : 1;
     return SP_OK;
 }
 
@@ -473,14 +549,14 @@ sp_status run_weighted(const WeightedLaunch& L, LaunchResult* result) {
     int per_sm = 0;
     SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)&weighted_kernel, kWThreads, 0));
     if (per_sm < 1) return fail(SP_ERR_CUDA, "weighted kernel cannot be resident");
-    // one block per source at a time; per-block state of 48 bytes a vertex,
-    // so the grid is also capped by a state budget (16 GiB)
+    // one block per source at a time; per-block state of 64 bytes a vertex,
+    // so the grid is also capped by a state budget (32 GiB)
     int grid = per_sm * device_sm_count(g->device);
     if (L.max_ctas > 0 && L.max_ctas < grid) grid = L.max_ctas;
     const int64_t hcap = L.dist_cap;
-    const double per_block = 48.0 * (double)n + 8.0 * (double)(hcap + 2);
+    const double per_block = 64.0 * (double)n + 8.0 * (double)(hcap + 2);
     grid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)grid, (int64_t)L.nsrc,
-                                                         (int64_t)((16.0 * (1ull << 30)) / per_block)}));
+                                                         (int64_t)((32.0 * (1ull << 30)) / per_block)}));
     size_t bytes = 0;
     auto take = [&](size_t b) { size_t o = bytes; bytes += (b + 255) & ~(size_t)255; return o; };
     const size_t G = (size_t)grid, N = (size_t)n;
@@ -490,6 +566,8 @@ sp_status run_weighted(const WeightedLaunch& L, LaunchResult* result) {
     const size_t o_lstart = take(4 * (size_t)(hcap + 1) * G);
     const size_t o_hist = take(4 * (size_t)(hcap + 1) * G);
     const size_t o_sig = take(8 * N * G), o_th = take(8 * N * G), o_part = take(8 * N * G);
+    const size_t o_far0 = take(4 * N * G), o_far1 = take(4 * N * G), o_infar = take(4 * N * G),
+                 o_expd = take(4 * N * G);
     char* ws = nullptr;
     if (workspace_alloc((void**)&ws, bytes, st) != cudaSuccess) {
         cudaGetLastError();
@@ -521,6 +599,11 @@ sp_status run_weighted(const WeightedLaunch& L, LaunchResult* result) {
     a.hcap = (int32_t)hcap;
     a.ctl = reinterpret_cast<Ctl*>(ws + o_ctl);
     a.dist_out = L.d_dist;
+    a.far0 = reinterpret_cast<int32_t*>(ws + o_far0);
+    a.far1 = reinterpret_cast<int32_t*>(ws + o_far1);
+    a.infar = reinterpret_cast<int32_t*>(ws + o_infar);
+    a.expd = reinterpret_cast<int32_t*>(ws + o_expd);
+    a.delta = std::max(1, g->w_delta);
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);

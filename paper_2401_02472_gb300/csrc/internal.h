@@ -66,6 +66,7 @@ struct Graph {
     const int32_t* kci() const { return directed ? d_cci : d_ci; }
     int64_t knnz() const { return directed ? 2 * nnz : nnz; }
     int32_t* d_w = nullptr;     // arc weights [nnz] (sp_graph_set_weights): BC under these weights
+    int32_t w_delta = 1;        // near-far step of the weighted form: the mean arc weight
     DevFlags* flags_host = nullptr;  // mapped pinned: errors and hints of asynchronous calls
     DevFlags* flags_dev = nullptr;   // the same words, as the device addresses them
     int ecap_mult = 1, hcap_mult = 1;  // batched capacities learnt from asynchronous calls
