@@ -140,6 +140,7 @@ def run_serving(args, world):
         return times, stats, kept
 
     server = sp.sp_server_create(args.serve_budget << 30, args.slots)
+    sp.sp_server_set_live(server, not args.no_live)
     clocks = ClockSampler(0)
     clocks.start()
     times, stats, kept = one_stream(server)
@@ -150,7 +151,7 @@ def run_serving(args, world):
     sub0 = times[0][0]
     lat, arcs = [], 0
     first_sub, last_done = None, 0
-    service, kernel, per_graph, shared = [], [], {}, []
+    service, kernel, per_graph, shared, joined = [], [], {}, [], 0
     for (ta, gi, srcs), (ts, tb, td), st in zip(reqs, times, stats):
         if ta < warm:
             continue
@@ -158,6 +159,7 @@ def run_serving(args, world):
         service.append((td - tb) / 1e6)
         kernel.append(st["kernel_ms"])
         shared.append(st["shared"])
+        joined += st["joined"]
         per_graph.setdefault(gi, []).append((td - tb) / 1e6)
         arcs += st["traversed_arcs"]
         first_sub = ts if first_sub is None else min(first_sub, ts)
@@ -187,6 +189,7 @@ def run_serving(args, world):
     for i, out in kept.items():
         _, gi, srcs = reqs[i]
         s1 = sp.sp_server_create(args.serve_budget << 30, args.slots)
+        sp.sp_server_set_live(s1, not args.no_live)
         gid = [sp.sp_server_add_graph(s1, G.handle) for G in Gs][gi]
         alone = torch.empty(gs[gi].n, dtype=torch.float64, device=dev)
         sp.sp_bc_wait(s1, sp.sp_bc_submit(s1, gid, srcs, alone, opts))
@@ -207,6 +210,8 @@ def run_serving(args, world):
                     "kernel_ms_mean": float(np.mean(kernel)) if kernel else None,
                     # requests per launch, seen from each request (1 = ran alone)
                     "shared_launch_mean": float(np.mean(shared)) if shared else None,
+                    # requests that entered a batched launch already running (live launches)
+                    "joined_running_launch": joined, "live_launches": not args.no_live,
                     "service_ms_mean_per_graph": {str(k): round(float(np.mean(v)), 3) for k, v in sorted(per_graph.items())},
                     "one_at_a_time_plain": {"p50_ms": pct(base_lat, 50), "p99_ms": pct(base_lat, 99),
                                             "gteps": base_arcs / max(base_window, 1e-9) / 1e9,
@@ -912,6 +917,8 @@ def main():
     ap.add_argument("--serve-warmup", type=float, default=5.0, help="serving: warm-up part of the stream (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
+    ap.add_argument("--no-live", action="store_true",
+                    help="serving: batched launches run only the requests they started with")
     ap.add_argument("--serve-budget", type=int, default=64, help="serving: device memory budget (GiB)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -265,6 +265,9 @@ typedef struct {
     int32_t shared;         /* serving: requests that shared this request's launch (itself included) */
     int32_t recentred;      /* (level, source) pairs whose FP64 path counts were recentred by a power of
                                two (X6 of the readings; 0 unless sigma_float) */
+    int32_t joined;         /* serving: 1 when the request entered a batched launch that was already
+                               running, between two of its batches; 0 otherwise */
+    int32_t reserved;
 } sp_bc_stats;
 
 SP_API void sp_bc_opts_default(sp_bc_opts* o);
@@ -384,13 +387,22 @@ SP_API sp_status sp_bc_noalloc(const int32_t* row_ptr, const int32_t* col_idx, i
  * takes the oldest admitted request and runs it in one persistent launch;
  * when the batched form serves it, every other admitted request on the same
  * graph with the same options joins that launch (continuous batching, up to
- * 1,024 sources), each in 32-source words of its own.  With several slots,
- * launches of different slots are sized for the whole GPU and overlap on the
- * device as SMs free up.  A request's result does not depend on what else
- * runs: its words and the order in which their BC is added are fixed by the
- * request alone.
+ * 1,024 sources at the start), each in 32-source words of its own.  The
+ * launch is live: between two of its batches it takes the words of requests
+ * on the same graph with the same options admitted since it started (while
+ * no other admitted request has waited more than 10 ms), and each request
+ * completes as soon as its own words are done, not when the launch ends.
+ * With several slots, launches of different slots are sized for the whole
+ * GPU and overlap on the device as SMs free up.  A request's result does not
+ * depend on what else runs: its words and the order in which their BC is
+ * added are fixed by the request alone.  sp_server_add_graph computes the
+ * graph's source ordering keys once (a BFS per landmark if not yet done) and
+ * keeps a host copy (8 bytes a vertex).
  */
 SP_API sp_status sp_server_create(size_t hbm_budget_bytes, int32_t max_slots, sp_server* out);
+/* Live launches on (on != 0, the default) or off: off, a batched launch runs
+   the requests it started with and later ones wait for the next launch. */
+SP_API sp_status sp_server_set_live(sp_server s, int32_t on);
 SP_API sp_status sp_server_add_graph(sp_server s, sp_graph g, int32_t* graph_id);
 /* bc_out: device double[n] (n of the graph) on the graph's GPU, else SP_ERR_INVALID_ARG;
    sources (host or device) copied before return. */
@@ -421,7 +433,11 @@ SP_API sp_status sp_request_times(sp_server s, sp_request req, int64_t* submit_n
 /* Statistics of a request (valid once it is done).  traversed_arcs and reached
    are the request's own; when requests shared a launch (shared > 1), entries,
    scanned_arcs and dag_arcs are the launch's, split in proportion to
-   traversed_arcs, and kernel_ms is the launch's time. */
+   traversed_arcs, and kernel_ms is the launch's time.  A request finished by
+   a live launch has shared = requests the launch had taken by then, joined =
+   1 if it entered the launch while it ran, kernel_ms = time from its entry
+   into the launch to its completion, and entries, scanned_arcs, dag_arcs and
+   max_levels = 0 (kept per launch, not per request). */
 SP_API sp_status sp_request_stats(sp_server s, sp_request req, sp_bc_stats* out);
 SP_API sp_status sp_server_destroy(sp_server s); /* waits for running requests */
 

@@ -45,7 +45,8 @@ class sp_bc_stats(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("batches", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("promoted", ctypes.c_int32), ("sigma_float", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("tuned", ctypes.c_int32), ("driver", ctypes.c_int32),
-                ("bottom_up", ctypes.c_int32), ("shared", ctypes.c_int32), ("recentred", ctypes.c_int32)]
+                ("bottom_up", ctypes.c_int32), ("shared", ctypes.c_int32), ("recentred", ctypes.c_int32),
+                ("joined", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +98,7 @@ SIGNATURES = {
     "sp_bc_noalloc": ([_P, _P, _I32, _I64, _P, _I32, _P, _P], ctypes.c_int),
     "sp_server_create": ([_SZ, _I32, _P], ctypes.c_int),
     "sp_server_add_graph": ([_P, _P, _P], ctypes.c_int),
+    "sp_server_set_live": ([_P, _I32], ctypes.c_int),
     "sp_bc_submit": ([_P, _I32, _P, _I32, _P, _P, _P], ctypes.c_int),
     "sp_pagerank_submit": ([_P, _I32, ctypes.c_double, ctypes.c_double, _I32, _P, _P], ctypes.c_int),
     "sp_request_pagerank": ([_P, _I64, _P, _P], ctypes.c_int),
@@ -311,6 +313,10 @@ def sp_server_create(hbm_budget_bytes: int, max_slots: int) -> int:
     h = ctypes.c_void_p()
     _check(lib.sp_server_create(hbm_budget_bytes, max_slots, ctypes.byref(h)), "sp_server_create")
     return h.value
+
+
+def sp_server_set_live(s: int, on: bool) -> None:
+    _check(lib.sp_server_set_live(s, 1 if on else 0), "sp_server_set_live")
 
 
 def sp_server_add_graph(s: int, g: int) -> int:

@@ -335,7 +335,7 @@ __global__ void source_keys_kernel(const int32_t* __restrict__ src, int32_t nsrc
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
     auto clamp8 = [](int d) -> unsigned long long { return d < 0 || d > 255 ? 255ull : (unsigned long long)d; };
     for (int i = warp; i < nsrc; i += nwarp) {
-        const int s = src[i];
+        const int s = src != nullptr ? src[i] : i;  // no list: the keys of vertices 0 .. nsrc-1
         if (s < 0 || s >= n) {  // not a vertex: an asynchronous call's check reports it; read nothing
             if (lane == 0) keys[i] = ~0ull;
             continue;
@@ -906,6 +906,7 @@ __global__ void sum_words_kernel(const double* __restrict__ word_bc, int64_t w0,
 }
 
 bool request_is_batched(Graph* g, int32_t nsrc, const sp_bc_opts& o, cudaStream_t st) {
+    if (g->d_w != nullptr) return false;  // weighted graphs: the weighted form, request by request
     if (o.form == SP_FORM_BATCHED) return true;
     if (o.form != SP_FORM_AUTO || nsrc < 2 || o.debug_flags != 0) return false;
     bool sigma_float;
@@ -971,26 +972,41 @@ sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts
             at += parts[p].nsrc;
         }
     }
-    int32_t* d_all = nullptr;
-    unsigned long long* d_keys = nullptr;
-    SP_CUDA(cudaMallocAsync((void**)&d_all, sizeof(int32_t) * (size_t)total, st));
-    SP_CUDA(cudaMallocAsync((void**)&d_keys, sizeof(unsigned long long) * (size_t)total, st));
-    SP_CUDA(cudaMemcpyAsync(d_all, all.data(), sizeof(int32_t) * (size_t)total, cudaMemcpyHostToDevice, st));
-    {
-        sp_status rc = check_sources(d_all, (int32_t)total, g->n, st);
-        if (rc != SP_OK) { cudaFreeAsync(d_all, st); cudaFreeAsync(d_keys, st); return rc; }
-    }
-    const int32_t* d2 = g->d_land_dist;
-    source_keys_kernel<<<std::min<int64_t>(1024, (total + 7) / 8), 256, 0, st>>>(
-        d_all, (int32_t)total, g->n, g->d_rp, g->d_ci, g->d_top_dist, d2, d2 ? d2 + g->n : nullptr, d_keys);
     std::vector<unsigned long long> keys((size_t)total);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned long long) * (size_t)total, cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(d_keys, st);
-    cudaFreeAsync(d_all, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "request source ordering");
+    bool have_keys = false;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        if ((int64_t)g->h_keys.size() == n) {  // the graph's host copy (the server makes one per graph)
+            for (int64_t i = 0; i < total; ++i) {
+                const int32_t x = all[(size_t)i];
+                if (x < 0 || x >= n) return fail(SP_ERR_INVALID_ARG, "request source out of range");
+                keys[(size_t)i] = g->h_keys[(size_t)x];
+            }
+            have_keys = true;
+        }
+    }
+    if (!have_keys) {
+        int32_t* d_all = nullptr;
+        unsigned long long* d_keys = nullptr;
+        SP_CUDA(cudaMallocAsync((void**)&d_all, sizeof(int32_t) * (size_t)total, st));
+        SP_CUDA(cudaMallocAsync((void**)&d_keys, sizeof(unsigned long long) * (size_t)total, st));
+        SP_CUDA(cudaMemcpyAsync(d_all, all.data(), sizeof(int32_t) * (size_t)total, cudaMemcpyHostToDevice, st));
+        {
+            sp_status rc = check_sources(d_all, (int32_t)total, g->n, st);
+            if (rc != SP_OK) { cudaFreeAsync(d_all, st); cudaFreeAsync(d_keys, st); return rc; }
+        }
+        const int32_t* d2 = g->d_land_dist;
+        source_keys_kernel<<<std::min<int64_t>(1024, (total + 7) / 8), 256, 0, st>>>(
+            d_all, (int32_t)total, g->n, g->d_rp, g->d_ci, g->d_top_dist, d2, d2 ? d2 + g->n : nullptr, d_keys);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned long long) * (size_t)total, cudaMemcpyDeviceToHost,
+                                st);
+        cudaFreeAsync(d_keys, st);
+        cudaFreeAsync(d_all, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "request source ordering");
+    }
     std::vector<int64_t> wfirst(nparts), wcount(nparts);
     int64_t words = 0;
     for (int p = 0; p < nparts; ++p) {
@@ -1054,6 +1070,7 @@ sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts
         L.level_cap = lcap;
         L.d_word_bc = d_wbc;
         L.d_word_stats = d_wst;
+        L.word_cap = (int32_t)words_pad;
         L.bottom_up_den = batch_bu;
         r = LaunchResult{};
         sp_status rc = run_batched(L, &r);
@@ -1117,6 +1134,295 @@ sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts
         st_p.launches = launches + nparts;
     }
     return SP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: a batched launch that takes requests between its batches (live
+// feed).  The host side of the protocol described with FeedCtl / FeedReq.
+
+sp_status graph_host_keys(Graph* g, cudaStream_t st) {
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        if ((int64_t)g->h_keys.size() == g->n) return SP_OK;
+    }
+    if (g->n == 0) return SP_OK;
+    sp_status rc = ensure_top_bfs(g, st);
+    if (rc == SP_OK) rc = ensure_landmarks(g, st);
+    if (rc != SP_OK) return rc;
+    std::vector<unsigned long long> keys((size_t)g->n);
+    unsigned long long* d_keys = nullptr;
+    SP_CUDA(cudaMallocAsync((void**)&d_keys, sizeof(unsigned long long) * (size_t)g->n, st));
+    const int32_t* d2 = g->d_land_dist;
+    const int grid = (int)std::min<int64_t>((g->n + 7) / 8, (int64_t)device_sm_count(g->device) * 8);
+    source_keys_kernel<<<std::max(grid, 1), 256, 0, st>>>(nullptr, g->n, g->n, g->d_rp, g->d_ci, g->d_top_dist, d2,
+                                                          d2 ? d2 + g->n : nullptr, d_keys);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(keys.data(), d_keys, sizeof(unsigned long long) * (size_t)g->n, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d_keys, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "source keys of the graph");
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->h_keys.swap(keys);
+    return SP_OK;
+}
+
+constexpr int32_t kLiveReqs = 256;                 // request slots of a feed
+constexpr int32_t kLiveMaxWords = 256;            // word slots of a feed, at most
+constexpr size_t kLiveWordBytes = size_t(1) << 30;  // per-word BC vectors of a feed, at most (soft)
+
+sp_status live_open(Graph* g, const sp_bc_opts& o, int64_t nsrc, LiveFeed* lf, cudaStream_t st) {
+    const int64_t n = g->n;
+    if (n == 0) return fail(SP_ERR_INVALID_ARG, "live feed on an empty graph");
+    {
+        sp_status rc = graph_host_keys(g, st);
+        if (rc != SP_OK) return rc;
+    }
+    absorb_hints(g);
+    bool theta_f32 = o.precision == SP_FP32_DELTA, sigma_float;
+    {
+        const int hints = range_hints(g);
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (hints & 1) g->sigma_float = true;
+        if (hints & 2) g->theta_f64 = true;
+        if (g->theta_f64) theta_f32 = false;
+        sigma_float = g->sigma_float;
+    }
+    int width = 0;
+    int batch_bu = batched_bottom_up(g, o.bottom_up);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key(g, o.precision));
+        if (it != g_tuned.end()) {
+            width = it->second.width;
+            if (o.bottom_up == 0) batch_bu = batched_bottom_up(g, it->second.bottom_up);
+        }
+    }
+    if (width == 0) width = nsrc >= 128 ? 128 : default_batch_width((int32_t)std::max<int64_t>(nsrc, 1));
+    // word slots: room for the largest request plus a batch, more while the
+    // vectors stay within about 1 GiB
+    const int64_t min_words = (int64_t)(1024 / 32) + width / 32;
+    const int64_t by_bytes = (int64_t)(kLiveWordBytes / (sizeof(double) * (size_t)n));
+    const int32_t word_cap = (int32_t)std::max<int64_t>(min_words, std::min<int64_t>(by_bytes, kLiveMaxWords));
+    if (lf->ctl == nullptr) {  // first use: the mapped feed, sized for the largest feed
+        void* hp = nullptr;
+        const size_t o_req = 64, o_lanes = o_req + sizeof(FeedReq) * (size_t)kLiveReqs;
+        const size_t bytes = o_lanes + sizeof(int32_t) * 32 * (size_t)kLiveMaxWords;
+        cudaError_t e = cudaHostAlloc(&hp, bytes, cudaHostAllocMapped);
+        if (e != cudaSuccess) return cuda_fail(e, "live feed");
+        std::memset(hp, 0, bytes);
+        void* dp = nullptr;
+        e = cudaHostGetDevicePointer(&dp, hp, 0);
+        if (e != cudaSuccess) {
+            cudaFreeHost(hp);
+            return cuda_fail(e, "live feed");
+        }
+        char* h = static_cast<char*>(hp);
+        char* d = static_cast<char*>(dp);
+        lf->ctl = reinterpret_cast<FeedCtl*>(h);
+        lf->req = reinterpret_cast<FeedReq*>(h + o_req);
+        lf->lanes = reinterpret_cast<int32_t*>(h + o_lanes);
+        lf->ctl_d = reinterpret_cast<FeedCtl*>(d);
+        lf->req_d = reinterpret_cast<FeedReq*>(d + o_req);
+        lf->lanes_d = reinterpret_cast<int32_t*>(d + o_lanes);
+    }
+    if (lf->d_lanes == nullptr) {  // the launch's device copies of lanes and records
+        cudaError_t e = cudaMallocAsync((void**)&lf->d_lanes, sizeof(int32_t) * 32 * (size_t)kLiveMaxWords, st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&lf->d_req, sizeof(FeedReq) * (size_t)kLiveReqs, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SP_ERR_OOM, "live feed: device copies");
+        }
+    }
+    const size_t wbytes = sizeof(double) * (size_t)word_cap * (size_t)n;
+    if (lf->wbc_bytes < wbytes || lf->d_wst == nullptr) {  // zeroed once; launches leave them zero
+        if (lf->d_wbc) cudaFreeAsync(lf->d_wbc, st);
+        lf->d_wbc = nullptr;
+        lf->wbc_bytes = 0;
+        if (cudaMallocAsync((void**)&lf->d_wbc, wbytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            lf->d_wbc = nullptr;
+            return fail(SP_ERR_OOM, "live feed: per-word BC vectors");
+        }
+        cudaError_t e = cudaSuccess;
+        if (lf->d_wst == nullptr)
+            e = cudaMallocAsync((void**)&lf->d_wst, sizeof(unsigned long long) * 2 * (size_t)kLiveMaxWords, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(lf->d_wbc, 0, wbytes, st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(lf->d_wst, 0, sizeof(unsigned long long) * 2 * (size_t)kLiveMaxWords, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "live feed");
+        lf->wbc_bytes = wbytes;
+    }
+    lf->g = g;
+    lf->word_cap = word_cap;
+    lf->req_cap = kLiveReqs;
+    lf->width = width;
+    lf->bottom_up = batch_bu;
+    lf->sigma_float = sigma_float;
+    lf->theta_f32 = theta_f32;
+    lf->words = lf->nreq = lf->first_open_word = lf->first_open_req = 0;
+    lf->pub_words = lf->pub_nreq = 0;
+    lf->ctl->words = 0;
+    lf->ctl->nreq = 0;
+    lf->ctl->ran_words = 0;
+    lf->ctl->closed = 0;
+    return SP_OK;
+}
+
+int64_t live_append(LiveFeed* lf, const int32_t* h_sources, int32_t nsrc, double* d_out) {
+    if (nsrc <= 0 || __atomic_load_n(&lf->ctl->closed, __ATOMIC_ACQUIRE) != 0) return -1;
+    const int64_t nw = (nsrc + 31) / 32;
+    if (lf->words + nw - lf->first_open_word > lf->word_cap) return -1;  // word slots still in use
+    if (lf->nreq + 1 - lf->first_open_req > lf->req_cap) return -1;
+    if (lf->words + nw > (int64_t(1) << 25)) return -1;  // lane indices stay within int32
+    // the request's sources regrouped among themselves, as bc_requests does
+    std::vector<int32_t> idx((size_t)nsrc);
+    {
+        Graph* g = lf->g;
+        std::lock_guard<std::mutex> lk(g->mu);
+        if ((int64_t)g->h_keys.size() != g->n) return -1;
+        for (int32_t i = 0; i < nsrc; ++i) {
+            if (h_sources[i] < 0 || h_sources[i] >= g->n) return -1;
+            idx[(size_t)i] = i;
+        }
+        std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+            return g->h_keys[(size_t)h_sources[x]] < g->h_keys[(size_t)h_sources[y]];
+        });
+    }
+    for (int64_t j = 0; j < nw; ++j) {
+        int32_t* lane = lf->lanes + (size_t)((lf->words + j) % lf->word_cap) * 32;
+        for (int l = 0; l < 32; ++l) {
+            const int64_t i = j * 32 + l;
+            lane[l] = i < nsrc ? h_sources[idx[(size_t)i]] : -1;
+        }
+    }
+    const int64_t r = lf->nreq;
+    FeedReq& fr = lf->req[r % lf->req_cap];
+    fr.first_word = (int32_t)lf->words;
+    fr.nwords = (int32_t)nw;
+    fr.out = d_out;
+    fr.traversed = 0;
+    fr.reached = 0;
+    fr.done = 0;
+    lf->nreq += 1;
+    lf->words += nw;
+    return r;
+}
+
+void live_publish(LiveFeed* lf) {
+    if (lf->pub_words == lf->words) return;
+    __atomic_store_n(&lf->ctl->nreq, (int32_t)lf->nreq, __ATOMIC_RELEASE);
+    __atomic_store_n(&lf->ctl->words, (int32_t)lf->words, __ATOMIC_RELEASE);
+    lf->pub_words = lf->words;
+    lf->pub_nreq = lf->nreq;
+}
+
+bool live_done(const LiveFeed* lf, int64_t r) {
+    return __atomic_load_n(&lf->req[r % lf->req_cap].done, __ATOMIC_ACQUIRE) != 0;
+}
+
+void live_retire(LiveFeed* lf) {
+    while (lf->first_open_req < lf->nreq && live_done(lf, lf->first_open_req)) ++lf->first_open_req;
+    lf->first_open_word =
+        lf->first_open_req < lf->nreq ? lf->req[lf->first_open_req % lf->req_cap].first_word : lf->words;
+}
+
+int64_t live_ran_words(const LiveFeed* lf) { return __atomic_load_n(&lf->ctl->ran_words, __ATOMIC_ACQUIRE); }
+
+sp_status live_start(LiveFeed* lf, const sp_bc_opts& o, cudaStream_t st, cudaHostFn_t on_done, void* on_done_arg) {
+    if (lf->h_ctl == nullptr) {
+        void* hp = nullptr;
+        cudaError_t e = cudaHostAlloc(&hp, sizeof(Ctl), cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(e, "live feed control block");
+        lf->h_ctl = static_cast<Ctl*>(hp);
+    }
+    if (lf->ev == nullptr) {
+        cudaError_t e = cudaEventCreateWithFlags(&lf->ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            lf->ev = nullptr;
+            return cuda_fail(e, "live feed event");
+        }
+    }
+    std::memset(lf->h_ctl, 0, sizeof(Ctl));
+    BatchedLaunch L{};
+    L.g = lf->g;
+    L.d_sources = lf->d_lanes;
+    L.nsrc = 0;
+    L.d_bc = nullptr;
+    L.width = lf->width;
+    L.sigma_float = lf->sigma_float;
+    L.theta_f32 = lf->theta_f32;
+    L.max_ctas = o.max_ctas;
+    L.timeout_ns = timeout_of(o);
+    L.stream = st;
+    L.d_word_bc = lf->d_wbc;
+    L.d_word_stats = lf->d_wst;
+    L.word_cap = lf->word_cap;
+    L.bottom_up_den = lf->bottom_up;
+    L.feed = lf->ctl_d;
+    L.feed_req = lf->req_d;
+    L.feed_lanes = lf->lanes_d;
+    L.req_dev = lf->d_req;
+    L.req_cap = lf->req_cap;
+    L.ctl_out = lf->h_ctl;
+    L.done_ev = lf->ev;
+    L.on_done = on_done;
+    L.on_done_arg = on_done_arg;
+    LaunchResult r;
+    return run_batched(L, &r);
+}
+
+bool live_ended(LiveFeed* lf, LaunchResult* result) {
+    const cudaError_t q = cudaEventQuery(lf->ev);
+    if (q == cudaErrorNotReady) return false;
+    *result = LaunchResult{};
+    if (q != cudaSuccess) {  // the launch failed as a CUDA call: report it as an error of the launch
+        cudaGetLastError();
+        result->err = SP_ERR_CUDA;
+        return true;
+    }
+    const Ctl& h = *lf->h_ctl;
+    result->err = h.err;
+    result->levels = h.max_levels;
+    result->traversed_arcs = h.traversed_arcs;
+    result->reached = h.reached;
+    result->entries = h.entries;
+    result->scanned_arcs = h.scanned_arcs;
+    result->dag_arcs = h.dag_arcs;
+    result->recentred = h.recentred;
+    // what a failed launch learnt about the graph, as bc_requests records it
+    if (h.err == kErrSigmaOverflow && !lf->sigma_float) {
+        add_range_hint(lf->g, 1);
+        std::lock_guard<std::mutex> lk(lf->g->mu);
+        lf->g->sigma_float = true;
+    }
+    if (h.err == kErrThetaRange32 && lf->theta_f32) {
+        add_range_hint(lf->g, 2);
+        std::lock_guard<std::mutex> lk(lf->g->mu);
+        lf->g->theta_f64 = true;
+    }
+    return true;
+}
+
+void live_scrub(LiveFeed* lf, cudaStream_t st) {
+    if (lf->d_wbc) cudaMemsetAsync(lf->d_wbc, 0, lf->wbc_bytes, st);
+    if (lf->d_wst) cudaMemsetAsync(lf->d_wst, 0, sizeof(unsigned long long) * 2 * (size_t)kLiveMaxWords, st);
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+}
+
+void live_close(LiveFeed* lf, cudaStream_t st) {
+    if (lf->d_wbc) cudaFreeAsync(lf->d_wbc, st);
+    if (lf->d_wst) cudaFreeAsync(lf->d_wst, st);
+    if (lf->d_lanes) cudaFreeAsync(lf->d_lanes, st);
+    if (lf->d_req) cudaFreeAsync(lf->d_req, st);
+    cudaStreamSynchronize(st);
+    if (lf->ctl) cudaFreeHost(lf->ctl);
+    if (lf->h_ctl) cudaFreeHost(lf->h_ctl);
+    if (lf->ev) cudaEventDestroy(lf->ev);
+    cudaGetLastError();
+    *lf = LiveFeed{};
 }
 
 // ---------------------------------------------------------------------------

@@ -87,6 +87,16 @@ struct BatchArgs {
     int directed;      // rp/ci: combined out- and in-arc rows (arc_in / arc_out); odeg: out-degrees
     const int32_t* odeg;
     double* sq;        // optional [n]: sum over the call's sources of delta_s(v)^2 (sampling bounds)
+    // Request mode: word_bc and word_stats hold word_cap word slots; word w
+    // uses slot w % word_cap.  Live feed (serving): feed non-null; the words,
+    // their lanes (sources, slot-indexed like word_bc) and the requests come
+    // from the feed between batches instead of from nsrc.
+    int32_t word_cap;
+    FeedCtl* feed;
+    FeedReq* feed_req;        // the feed's request records (host memory): done and counts are written here
+    const int32_t* feed_lanes;  // the feed's lanes (host memory), copied into `sources` (device) as published
+    FeedReq* req_dev;         // device copy of the published request records
+    int32_t req_cap;
 };
 
 template <int W>
@@ -144,7 +154,7 @@ struct BatchKernel {
     Ctl* ctl;
     int lane;
     int d = 0;
-    int word0 = 0;  // request mode: global index of the current batch's first word
+    int word0 = 0;  // request mode: word slot of the current batch's first word
     bool discover_on = true;  // top-down discovery by the level's entries (off on bottom-up levels)
     uint32_t active[W];       // bits of the batch's sources (lanes with a source)
     unsigned long long* wst = nullptr;  // request mode: the block's per-word counts [W][2]
@@ -363,7 +373,9 @@ struct BatchKernel {
                 if (F[k] == 0u) continue;  // the entry's mask: the same in every lane
                 const double x = warp_sum_f64((double)dk[k]);
                 if (lane == 0) {
-                    double* p = a.word_bc + (size_t)(word0 + k) * (size_t)a.n + v;
+                    int ws = word0 + k;  // word0 is already a slot index
+                    if (ws >= a.word_cap) ws -= a.word_cap;
+                    double* p = a.word_bc + (size_t)ws * (size_t)a.n + v;
                     *p = __ldcg(p) + x;
                 }
             }
@@ -844,6 +856,91 @@ struct BatchKernel {
     }
 };
 
+// Live feed (serving), kept out of line so that the batched kernel's register
+// allocation does not see them.  live_ready: the requests from r0 on whose
+// words all lie below word wend, [r0, result).  live_sum: each such request's
+// BC as its words' partial vectors summed in word order, the slots cleared for
+// the words that reuse them.  live_mark (one thread, after a grid barrier):
+// the requests' counts, then done, and the launch's finished-request count.
+// live_snapshot (every thread of block 0): the words and requests published
+// since the last look, their lanes and records copied to device memory (so
+// that the other blocks read no host memory), then the counts.
+static __device__ __noinline__ void live_snapshot(const FeedCtl* feed, const int32_t* h_lanes, const FeedReq* h_req,
+                                                  int32_t* lanes, FeedReq* req, int word_cap, int req_cap, Ctl* ctl) {
+    __shared__ int s_w[2];
+    if (threadIdx.x == 0) {
+        s_w[0] = ld_acquire_sys_i32(&feed->words);
+        s_w[1] = ld_volatile(&feed->nreq);
+    }
+    __syncthreads();
+    const int w1 = s_w[0], r1 = s_w[1];
+    const int w0 = ld_volatile(&ctl->live_words), r0 = ld_volatile(&ctl->live_nreq);
+    for (int i = threadIdx.x; i < (w1 - w0) * 32; i += blockDim.x) {
+        const size_t at = (size_t)((w0 + i / 32) % word_cap) * 32 + (size_t)(i & 31);
+        lanes[at] = ld_volatile(&h_lanes[at]);
+    }
+    for (int r = r0 + (int)threadIdx.x; r < r1; r += blockDim.x) {
+        const FeedReq* src = h_req + (r % req_cap);
+        FeedReq* dst = req + (r % req_cap);
+        dst->first_word = ld_volatile(&src->first_word);
+        dst->nwords = ld_volatile(&src->nwords);
+        dst->out = ld_volatile(&src->out);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->live_words = w1;
+        ctl->live_nreq = r1;
+    }
+}
+static __device__ __noinline__ int live_ready(const FeedReq* req, int req_cap, int r0, int nreq, int wend) {
+    int r1 = r0;
+    while (r1 < nreq) {
+        const FeedReq* fr = req + (r1 % req_cap);
+        if (ld_volatile(&fr->first_word) + ld_volatile(&fr->nwords) > wend) break;
+        ++r1;
+    }
+    return r1;
+}
+static __device__ __noinline__ void live_sum(const FeedReq* req, int req_cap, double* word_bc, int word_cap, int n,
+                                             int r0, int r1, int tid, int nthr) {
+    for (int r = r0; r < r1; ++r) {
+        const FeedReq* fr = req + (r % req_cap);
+        const int fw = ld_volatile(&fr->first_word), nw = ld_volatile(&fr->nwords);
+        double* out = ld_volatile(&fr->out);
+        const int s0 = fw % word_cap;
+        for (int v = tid; v < n; v += nthr) {
+            double sum = 0.0;
+            for (int k = 0, ws = s0; k < nw; ++k, ws = ws + 1 == word_cap ? 0 : ws + 1) {
+                double* p = word_bc + (size_t)ws * (size_t)n + v;
+                sum += __ldcg(p);
+                *p = 0.0;
+            }
+            out[v] = sum;
+        }
+    }
+}
+static __device__ __noinline__ void live_mark(const FeedReq* req, FeedReq* h_req, int req_cap,
+                                              unsigned long long* word_stats, int word_cap, Ctl* ctl, int r0, int r1) {
+    for (int r = r0; r < r1; ++r) {
+        const FeedReq* dr = req + (r % req_cap);
+        FeedReq* fr = h_req + (r % req_cap);
+        const int fw = ld_volatile(&dr->first_word), nw = ld_volatile(&dr->nwords);
+        unsigned long long tr = 0, re = 0;
+        for (int k = 0; k < nw; ++k) {
+            unsigned long long* q = word_stats + 2 * (size_t)((fw + k) % word_cap);
+            tr += q[0];
+            re += q[1];
+            q[0] = 0ull;
+            q[1] = 0ull;
+        }
+        fr->traversed = tr;
+        fr->reached = re;
+        __threadfence_system();
+        st_release_sys_i32(&fr->done, 1);
+    }
+    ctl->live_req_done = r1;
+}
+
 template <int W, typename SigT, typename ThT, bool kDir>
 __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(BatchArgs a) {
     if (a.pre_err != nullptr) {  // the same word for every block: all return, nothing is touched
@@ -923,10 +1020,27 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
         for (int i = tid; i < n; i += nthr) a.bc[i] = 0.0;
     if (a.sq != nullptr)
         for (int i = tid; i < n; i += nthr) a.sq[i] = 0.0;
+    if (a.feed != nullptr && blockIdx.x == 0)  // live feed: the words and requests there are now
+        live_snapshot(a.feed, a.feed_lanes, a.feed_req, const_cast<int32_t*>(a.sources), a.req_dev, a.word_cap,
+                      a.req_cap, ctl);
     if (!sync()) goto out;
 
-    for (int b0 = 0; b0 < a.nsrc; b0 += B) {
-        const int nb = min(B, a.nsrc - b0);
+    for (int b0 = 0, nb = 0;; b0 += nb) {
+        if (a.feed != nullptr) {  // the next min(W, available) words
+            const int avail = ld_volatile(&ctl->live_words);
+            if ((b0 >> 5) >= avail) break;
+            nb = min(W, avail - (b0 >> 5)) * 32;
+        } else {
+            if (b0 >= a.nsrc) break;
+            nb = min(B, a.nsrc - b0);
+        }
+        // source of lane sl of this batch (-1: none); live feeds keep their
+        // lanes in word slots that the host refills
+        auto source_of = [&](int sl) -> int {
+            if (a.feed == nullptr) return __ldg(&a.sources[b0 + sl]);
+            const int w = (b0 + sl) >> 5;
+            return __ldcg(&a.sources[(size_t)(w % a.word_cap) * 32 + (sl & 31)]);
+        };
         // ---- init: sources of this batch at level 0 ----
         K.hoff_next = 0;
         K.soff_next = 0;
@@ -946,15 +1060,15 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
                 a.emin[B + i] = INT_MAX;
             }
         }
-        K.word0 = b0 / 32;
+        K.word0 = a.word_cap > 0 ? (b0 >> 5) % a.word_cap : 0;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
             const int sl = k * 32 + lane;
-            K.active[k] = __ballot_sync(kFull, sl < nb && __ldg(&a.sources[b0 + sl]) >= 0);
+            K.active[k] = __ballot_sync(kFull, sl < nb && source_of(sl) >= 0);
         }
-        if (tid < nb && __ldg(&a.sources[b0 + tid]) >= 0) {  // request mode leaves empty lanes (-1)
+        if (tid < nb && source_of(tid) >= 0) {  // request mode leaves empty lanes (-1)
             const int s = tid;
-            const int x = __ldg(&a.sources[b0 + s]);
+            const int x = source_of(s);
             const uint32_t bit = 1u << (s & 31);
             atomicOr(&a.seen[(size_t)x * W + (s >> 5)], bit);
             atomicOr(&a.dense[(size_t)x * W + (s >> 5)], bit);  // ring 0 = F_0
@@ -1081,11 +1195,16 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
         if (a.word_stats != nullptr) {  // this batch's per-word counts
             __syncthreads();
             if (threadIdx.x < 2 * W) {
-                if (s_wst[threadIdx.x]) atomicAdd(&a.word_stats[2 * (size_t)K.word0 + threadIdx.x], s_wst[threadIdx.x]);
+                int ws = K.word0 + (int)(threadIdx.x >> 1);
+                if (ws >= a.word_cap) ws -= a.word_cap;
+                if (s_wst[threadIdx.x]) atomicAdd(&a.word_stats[2 * (size_t)ws + (threadIdx.x & 1)], s_wst[threadIdx.x]);
                 s_wst[threadIdx.x] = 0ull;
             }
             __syncthreads();
         }
+        if (a.feed != nullptr && blockIdx.x == 0)  // what the feed holds now, for the next batch
+            live_snapshot(a.feed, a.feed_lanes, a.feed_req, const_cast<int32_t*>(a.sources), a.req_dev, a.word_cap,
+                          a.req_cap, ctl);
         // ---- cleanup: dense levels 0..2, seen of the sources; reset the stack ----
         for (int j = 0; j < 3 && j < L; ++j) {
             const int cb = ld_volatile(&a.eoff[j]), ce = ld_volatile(&a.eoff[j + 1]);
@@ -1102,7 +1221,20 @@ __global__ void __launch_bounds__(kBatchThreads, SP_BATCH_MINB) batched_kernel(B
         }
         stamp_base += L + 1;
         if (!sync()) goto out;
+        if (a.feed != nullptr) {
+            // ---- live feed: finish the requests whose words are all done ----
+            const int wend = (b0 + nb) >> 5;
+            const int r0 = ld_volatile(&ctl->live_req_done);
+            const int r1 = live_ready(a.req_dev, a.req_cap, r0, ld_volatile(&ctl->live_nreq), wend);
+            if (r1 > r0) {
+                live_sum(a.req_dev, a.req_cap, a.word_bc, a.word_cap, n, r0, r1, tid, nthr);
+                if (!sync()) goto out;
+                if (tid == 0) live_mark(a.req_dev, a.feed_req, a.req_cap, a.word_stats, a.word_cap, ctl, r0, r1);
+            }
+            if (tid == 0) st_release_sys_i32(&a.feed->ran_words, wend);
+        }
     }
+    if (a.feed != nullptr && tid == 0 && ld_volatile(&ctl->err) == 0) st_release_sys_i32(&a.feed->closed, 1);
 
 out:
     {

@@ -122,6 +122,12 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     a.word_stats = L.d_word_stats;
     a.centre_bound = sigma_centre_bound(L.sigma_float, L.theta_f32, PlainMode::BC);
     a.sq = L.d_sq;
+    a.word_cap = L.word_cap;
+    a.feed = L.feed;
+    a.feed_req = L.feed_req;
+    a.feed_lanes = L.feed_lanes;
+    a.req_dev = L.req_dev;
+    a.req_cap = L.req_cap;
 
     void* args[] = {&a};
     if (L.async.flags != nullptr) {  // enqueue only: the finish step moves the error word on
@@ -138,6 +144,20 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
         result->hcap = hcap;
         result->lcap = lcap;
         return frc;
+    }
+    if (L.ctl_out != nullptr) {  // enqueue only: the control block comes back with an event
+        ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBatchThreads), args, 0, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(L.ctl_out, ws + o_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(ws, st);
+        if (ce == cudaSuccess && L.on_done != nullptr) ce = cudaLaunchHostFunc(st, L.on_done, L.on_done_arg);
+        if (ce == cudaSuccess && L.done_ev != nullptr) ce = cudaEventRecord(L.done_ev, st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaLaunchCooperativeKernel (batched form, live)");
+        result->launches = 1;
+        result->grid = grid;
+        result->ecap = ecap;
+        result->hcap = hcap;
+        result->lcap = lcap;
+        return SP_OK;
     }
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);

@@ -49,7 +49,42 @@ struct Ctl {
     unsigned long long prof[8];      // SP_PROFILE builds: SM cycles by kind of work, summed over warps
     unsigned long long phase_ns[256];  // SP_PROFILE builds: %globaltimer at each of the first barriers
     int block_phase[1024];           // last barrier each block arrived at (diagnostics)
+    // live feed (serving): the words and requests the launch may take, as
+    // block 0 last read them from the feed; requests finished so far
+    int live_words, live_nreq, live_req_done, pad2;
 };
+
+// Serving: a batched launch that keeps taking requests on its graph between
+// batches.  Both structs live in mapped pinned host memory.  The host writes
+// a request's lanes (one source per lane, -1 for empty lanes, in word slots
+// word % word_cap) and its FeedReq (slot r % req_cap), then nreq, then words
+// (release); the kernel reads words (acquire) and nreq at the end of each
+// batch, runs the next batch of words, and finishes every request whose words
+// are all done: its BC vector is the sum of its words' partial vectors in
+// word order, written to out, and then done is set (release).
+struct FeedReq {
+    int32_t first_word;                 // host: global index of the request's first word
+    int32_t nwords;                     // host
+    double* out;                        // host: the request's BC vector (device memory, n doubles)
+    unsigned long long traversed;       // device: (arc, source) pairs of the request's words
+    unsigned long long reached;         // device: (vertex, source) pairs
+    int32_t done;                       // device: 1 once out and the counts are complete
+    int32_t pad;
+};
+struct FeedCtl {
+    int32_t words;      // host: words appended so far
+    int32_t nreq;       // host: requests appended so far (written before words)
+    int32_t ran_words;  // device: words of the batches finished so far
+    int32_t closed;     // device: 1 once the launch has taken its last batch
+};
+__device__ __forceinline__ int ld_acquire_sys_i32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys_i32(int* p, int v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // Directed graphs: the kernels read a combined CSR whose row v lists v's
 // out-arcs and then its in-arcs, an in-arc's column id tagged with the top

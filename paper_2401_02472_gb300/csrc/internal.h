@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "starbc.h"
 
@@ -15,6 +16,8 @@ namespace sp {
 
 struct Ctl;
 struct HubRec;
+struct FeedCtl;
+struct FeedReq;
 
 // Per-graph words that the device writes and the host reads without a CUDA
 // call (mapped pinned host memory): the first error of an asynchronous call,
@@ -65,6 +68,7 @@ struct Graph {
     const int32_t* krp() const { return directed ? d_crp : d_rp; }
     const int32_t* kci() const { return directed ? d_cci : d_ci; }
     int64_t knnz() const { return directed ? 2 * nnz : nnz; }
+    std::vector<unsigned long long> h_keys;  // source ordering key per vertex (graph_host_keys), or empty
     int32_t* d_w = nullptr;     // arc weights [nnz] (sp_graph_set_weights): BC under these weights
     int32_t w_delta = 1;        // near-far step of the weighted form: the mean arc weight
     DevFlags* flags_host = nullptr;  // mapped pinned: errors and hints of asynchronous calls
@@ -193,6 +197,21 @@ struct BatchedLaunch {
     unsigned long long* d_word_stats;  // request mode: [nsrc/32][2]
     double* d_sq = nullptr;            // optional: sum over the sources of delta^2 per vertex
     AsyncHooks async;
+    // live feed (serving): d_sources are the feed's lanes (word slots), nsrc is
+    // unused, d_word_bc / d_word_stats have word_cap slots
+    FeedCtl* feed = nullptr;
+    FeedReq* feed_req = nullptr;
+    const int32_t* feed_lanes = nullptr;  // live feed: its lanes in host memory (d_sources: device copy)
+    FeedReq* req_dev = nullptr;           // live feed: device copy of its request records
+    int32_t word_cap = 0;              // request mode: word slots (word index modulo this)
+    int32_t req_cap = 0;               // live feed: request slots
+    // enqueue only (live feeds): the launch's control block is copied to
+    // ctl_out (pinned host) and done_ev recorded after it; the call returns
+    // without waiting and `result` gets only the launch shape
+    Ctl* ctl_out = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    cudaHostFn_t on_done = nullptr;    // host function enqueued before done_ev (no CUDA calls in it)
+    void* on_done_arg = nullptr;
 };
 
 // Serving: several requests on one graph in one batched launch, each
@@ -207,6 +226,58 @@ struct RequestPart {
 sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts& o, cudaStream_t st);
 // Whether a request of nsrc sources with these options runs in the batched form.
 bool request_is_batched(Graph* g, int32_t nsrc, const sp_bc_opts& o, cudaStream_t st);
+
+// Serving: one batched launch that keeps taking requests on its graph (with
+// the same options) between batches.  open sets the feed up for a launch
+// (allocating on first use, reusing the buffers of earlier launches after);
+// append adds a request (host sources, regrouped by the graph's source keys)
+// unless the feed is full or closed; start enqueues the launch and returns,
+// the caller then polls done, appends, and polls ended; scrub clears the per-word vectors after a launch that stopped on
+// an error (a finished launch leaves them zero); close frees.
+struct LiveFeed {
+    Graph* g = nullptr;
+    FeedCtl* ctl = nullptr;     // mapped pinned host memory: host addresses
+    FeedReq* req = nullptr;     // [req_cap]
+    int32_t* lanes = nullptr;   // [word_cap * 32]
+    FeedCtl* ctl_d = nullptr;   // the same memory as the device addresses it
+    FeedReq* req_d = nullptr;
+    int32_t* lanes_d = nullptr;
+    int32_t word_cap = 0, req_cap = 0;
+    double* d_wbc = nullptr;                 // [word_cap][n], all zero between launches
+    size_t wbc_bytes = 0;                    // its allocated size
+    unsigned long long* d_wst = nullptr;     // [word_cap][2], all zero between launches
+    int32_t* d_lanes = nullptr;              // device copies the launch makes of the lanes and records
+    FeedReq* d_req = nullptr;
+    int width = 0, bottom_up = 0;
+    bool sigma_float = false, theta_f32 = false;
+    Ctl* h_ctl = nullptr;                    // pinned host: the last launch's control block
+    cudaEvent_t ev = nullptr;                // recorded after it
+    int64_t words = 0, nreq = 0;             // appended so far
+    int64_t pub_words = 0, pub_nreq = 0;     // of which published to the launch (live_publish)
+    int64_t first_open_word = 0, first_open_req = 0;  // oldest request not yet seen done
+};
+// nsrc: the sources the launch starts with (they pick the batch width when no tuned width is known)
+sp_status live_open(Graph* g, const sp_bc_opts& o, int64_t nsrc, LiveFeed* lf, cudaStream_t st);
+// Returns the request's index in the feed (>= 0), or -1 when it does not fit
+// now (slots of unfinished requests), a source is out of range, or the launch
+// has closed.
+int64_t live_append(LiveFeed* lf, const int32_t* h_sources, int32_t nsrc, double* d_out);
+// Whether request r is finished (its done flag, read with acquire ordering).
+bool live_done(const LiveFeed* lf, int64_t r);
+// Publish the appended requests to the launch (release): until then it does not see them.
+void live_publish(LiveFeed* lf);
+void live_retire(LiveFeed* lf);  // advance past the finished requests at the front
+int64_t live_ran_words(const LiveFeed* lf);  // words of the batches the launch finished
+// Enqueue the live launch on st and return; live_ended polls its end and then
+// fills `result` from its control block.
+sp_status live_start(LiveFeed* lf, const sp_bc_opts& o, cudaStream_t st, cudaHostFn_t on_done = nullptr,
+                     void* on_done_arg = nullptr);
+bool live_ended(LiveFeed* lf, LaunchResult* result);
+void live_scrub(LiveFeed* lf, cudaStream_t st);
+void live_close(LiveFeed* lf, cudaStream_t st);
+// Host copy of the per-vertex source ordering keys (live feeds order a
+// request's sources with it while the GPU is busy).
+sp_status graph_host_keys(Graph* g, cudaStream_t st);
 
 sp_status run_batched(const BatchedLaunch& L, LaunchResult* result);
 template <int W>

@@ -92,6 +92,7 @@ struct Server {
     std::deque<std::shared_ptr<Request>> admitted;  // admitted, not yet taken by a slot, arrival order
     std::vector<std::thread> workers;
     bool stopping = false;
+    bool live = true;  // batched requests run in live launches (sp_server_set_live)
     sp_request next_id = 1;
 
     void admit_locked() {
@@ -132,11 +133,42 @@ struct Server {
                x.opts.batch == r.opts.batch && x.opts.debug_flags == 0 && r.opts.debug_flags == 0;
     }
 
+    // Host function enqueued after a live launch: wakes the slots.
+    static void CUDART_CB wake(void* p) {
+        Server* s = static_cast<Server*>(p);
+        std::lock_guard<std::mutex> g(s->mu);
+        s->cv_work.notify_all();
+    }
+
+    // Runs a group of compatible batched BC requests as one ordinary launch
+    // (bc_requests) and finishes them.  Called and returns with lk unlocked.
+    void run_group(const std::vector<std::shared_ptr<Request>>& group, const sp_bc_opts& o, cudaStream_t st,
+                   std::unique_lock<std::mutex>& lk) {
+        std::vector<RequestPart> parts(group.size());
+        for (size_t i = 0; i < group.size(); ++i) {
+            parts[i].h_sources = group[i]->sources.data();
+            parts[i].nsrc = (int32_t)group[i]->sources.size();
+            parts[i].d_out = group[i]->bc_out;
+        }
+        const sp_status rc = bc_requests(group[0]->g, parts.data(), (int)parts.size(), o, st);
+        cudaStreamSynchronize(st);
+        lk.lock();
+        for (size_t i = 0; i < group.size(); ++i) {
+            if (rc == SP_OK) {
+                group[i]->stats = parts[i].stats;
+                group[i]->stats.shared = (int32_t)group.size();
+            }
+            finish_locked(group[i], rc);
+        }
+        lk.unlock();
+    }
+
     void worker(int slot) {
         (void)slot;
         cudaSetDevice(device);
         cudaStream_t st;
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        LiveFeed lf;  // this slot's live feed, reused launch after launch
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
             cv_work.wait(lk, [&] { return stopping || !admitted.empty(); });
@@ -150,10 +182,10 @@ struct Server {
 
             const bool batched = !r->cancelled && r->kind == ReqKind::BC &&
                                  request_is_batched(r->g, (int32_t)r->sources.size(), o, st);
-            std::vector<std::shared_ptr<Request>> group{r};
             if (batched) {
                 // continuous batching: admitted requests on the same graph join
                 // this launch, each in words of its own
+                std::vector<std::shared_ptr<Request>> group{r};
                 lk.lock();
                 size_t total = r->sources.size();
                 for (auto it = admitted.begin(); it != admitted.end();) {
@@ -167,61 +199,153 @@ struct Server {
                         ++it;
                     }
                 }
+                const bool use_live = live;
                 lk.unlock();
+                // a live launch keeps taking requests between its batches;
+                // without a live feed, one ordinary launch
+                if (!(o.debug_flags == 0 && use_live && serve_live(group, o, st, lf, lk))) run_group(group, o, st, lk);
+                lk.lock();
+                continue;
             }
 
-            std::vector<sp_status> rcs(group.size(), SP_OK);
-            std::vector<sp_bc_stats> sts(group.size());
-            if (!r->cancelled && batched) {
-                std::vector<RequestPart> parts(group.size());
-                for (size_t i = 0; i < group.size(); ++i) {
-                    parts[i].h_sources = group[i]->sources.data();
-                    parts[i].nsrc = (int32_t)group[i]->sources.size();
-                    parts[i].d_out = group[i]->bc_out;
-                }
-                sp_status rc = bc_requests(r->g, parts.data(), (int)parts.size(), o, st);
-                for (size_t i = 0; i < group.size(); ++i) {
-                    rcs[i] = rc;
-                    sts[i] = parts[i].stats;
-                }
-            } else if (!r->cancelled && r->kind == ReqKind::PAGERANK) {
+            sp_status rc = SP_OK;
+            sp_bc_stats sts{};
+            if (!r->cancelled && r->kind == ReqKind::PAGERANK) {
                 PrResult pr;
-                rcs[0] = pagerank_device_entry(r->g, r->damping, r->tol, r->max_iter, r->bc_out, &pr, st);
-                if (rcs[0] == SP_OK) {
+                rc = pagerank_device_entry(r->g, r->damping, r->tol, r->max_iter, r->bc_out, &pr, st);
+                if (rc == SP_OK) {
                     r->pr_iterations = pr.iterations;
                     r->pr_change = pr.change;
-                    sts[0].kernel_ms = pr.kernel_ms;
-                    sts[0].launches = pr.launches;
-                    sts[0].traversed_arcs = (int64_t)r->g->nnz * (int64_t)pr.iterations;
+                    sts.kernel_ms = pr.kernel_ms;
+                    sts.launches = pr.launches;
+                    sts.traversed_arcs = (int64_t)r->g->nnz * (int64_t)pr.iterations;
                 }
             } else if (!r->cancelled) {
                 const int cnt = (int)r->sources.size();
                 int32_t* d_src = nullptr;
-                sp_status rc = SP_OK;
                 cudaError_t e = cudaMallocAsync((void**)&d_src, sizeof(int32_t) * cnt, st);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(d_src, r->sources.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st);
                 if (e != cudaSuccess) rc = cuda_fail(e, "server request sources");
-                if (rc == SP_OK) rc = bc_device_entry(r->g, d_src, cnt, o, r->bc_out, &sts[0], st);
+                if (rc == SP_OK) rc = bc_device_entry(r->g, d_src, cnt, o, r->bc_out, &sts, st);
                 if (d_src) cudaFreeAsync(d_src, st);
-                rcs[0] = rc;
             }
             cudaStreamSynchronize(st);
 
             lk.lock();
-            for (size_t i = 0; i < group.size(); ++i) {
-                auto& x = group[i];
-                const bool skip = x->cancelled && i == 0;
-                if (rcs[i] == SP_OK && !skip) {
-                    x->stats = sts[i];
-                    x->stats.shared = (int32_t)group.size();
-                }
-                finish_locked(x, skip ? SP_ERR_CANCELLED : rcs[i]);
+            if (rc == SP_OK && !r->cancelled) {
+                r->stats = sts;
+                r->stats.shared = 1;
             }
+            finish_locked(r, r->cancelled ? SP_ERR_CANCELLED : rc);
         }
         lk.unlock();
+        live_close(&lf, st);
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
+    }
+
+    // Runs `group` (compatible BC requests of the batched form, already taken)
+    // in one live launch on stream st, admitting further compatible requests
+    // between its batches, and finishes each request as soon as its words are
+    // done.  Returns false, having changed nothing, when no live feed could be
+    // set up (the caller then runs the group as one ordinary launch).  Called
+    // and returns with lk unlocked.
+    bool serve_live(const std::vector<std::shared_ptr<Request>>& group, const sp_bc_opts& o, cudaStream_t st,
+                    LiveFeed& lf, std::unique_lock<std::mutex>& lk) {
+        Graph* g = group[0]->g;
+        size_t total = 0;
+        for (auto& x : group) total += x->sources.size();
+        if (live_open(g, o, (int64_t)total, &lf, st) != SP_OK) return false;
+        struct Member {
+            std::shared_ptr<Request> x;
+            int64_t idx;
+            bool joined, done;
+        };
+        std::vector<Member> mem;
+        std::vector<std::shared_ptr<Request>> unplaced;
+        for (auto& x : group) {
+            const int64_t idx = live_append(&lf, x->sources.data(), (int32_t)x->sources.size(), x->bc_out);
+            if (idx < 0) unplaced.push_back(x);
+            else mem.push_back({x, idx, false, false});
+        }
+        if (mem.empty()) return false;
+        live_publish(&lf);
+        const int64_t t_launch = now_ns();
+        // enqueued: the loop below polls the requests' done flags; the end of
+        // the launch wakes it at once (a host function after the kernel)
+        const sp_status run_rc = live_start(&lf, o, st, &Server::wake, this);
+        LaunchResult res;
+        bool ended = run_rc != SP_OK;
+        auto finish_done = [&]() {  // with lk held
+            for (auto& m : mem) {
+                if (m.done || !live_done(&lf, m.idx)) continue;
+                m.done = true;
+                const FeedReq& fr = lf.req[m.idx % lf.req_cap];
+                sp_bc_stats s{};
+                s.traversed_arcs = (int64_t)fr.traversed;
+                s.reached = (int64_t)fr.reached;
+                s.kernel_ms = 1e-6 * (double)(now_ns() - std::max(t_launch, m.x->t_start));
+                s.batch = lf.width;
+                s.batches = (int32_t)((fr.nwords + lf.width / 32 - 1) / (lf.width / 32));
+                s.form = SP_FORM_BATCHED;
+                s.promoted = o.precision == SP_FP32_DELTA && !lf.theta_f32;
+                s.sigma_float = lf.sigma_float ? 1 : 0;
+                s.launches = 1;
+                s.shared = (int32_t)lf.nreq;
+                s.joined = m.joined ? 1 : 0;
+                m.x->stats = s;
+                finish_locked(m.x, SP_OK);
+            }
+            live_retire(&lf);
+        };
+        lk.lock();
+        while (!ended) {
+            finish_done();
+            if (__atomic_load_n(&lf.ctl->closed, __ATOMIC_ACQUIRE) == 0) {
+                // joins: the oldest admitted requests while they are compatible
+                // (no request overtakes an older one on another graph)
+                while (!admitted.empty() && compatible(*group[0], *admitted.front())) {
+                    auto x = admitted.front();
+                    const int64_t idx = live_append(&lf, x->sources.data(), (int32_t)x->sources.size(), x->bc_out);
+                    if (idx < 0) break;  // full for now
+                    x->taken = true;
+                    x->t_start = now_ns();
+                    mem.push_back({x, idx, true, false});
+                    admitted.pop_front();
+                }
+                // joiners are published a whole batch of words at a time, so
+                // that a join never adds a batch the launch would run part
+                // empty; what is still held when the launch ends goes to the next
+                if (lf.words - lf.pub_words >= lf.width / 32) live_publish(&lf);
+            }
+            cv_work.wait_for(lk, std::chrono::microseconds(50));
+            ended = live_ended(&lf, &res);
+        }
+        finish_done();
+        std::vector<std::shared_ptr<Request>> left;
+        for (auto& m : mem)
+            if (!m.done) left.push_back(m.x);
+        const bool failed = run_rc != SP_OK || res.err != 0;
+        if (!failed) {
+            // requests the launch never reached (appended after its last look
+            // at the feed) go back to the front of the queue, in order
+            for (auto it = unplaced.rbegin(); it != unplaced.rend(); ++it) left.insert(left.begin(), *it);
+            for (auto it = left.rbegin(); it != left.rend(); ++it) {
+                (*it)->taken = false;
+                admitted.push_front(*it);
+            }
+            if (!left.empty()) cv_work.notify_all();
+            lk.unlock();
+            return true;
+        }
+        lk.unlock();
+        live_scrub(&lf, st);
+        // the launch stopped on an error: the unfinished requests run as one
+        // ordinary launch, which reruns with wider representations as needed
+        for (auto& x : unplaced) left.push_back(x);
+        if (!left.empty()) run_group(left, o, st, lk);
+        return true;
     }
 };
 
@@ -251,9 +375,26 @@ sp_status sp_server_create(size_t hbm_budget_bytes, int32_t max_slots, sp_server
     return SP_OK;
 }
 
+sp_status sp_server_set_live(sp_server sh, int32_t on) {
+    if (!sh) return fail(SP_ERR_INVALID_ARG, "server is NULL");
+    Server* s = reinterpret_cast<Server*>(sh);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->live = on != 0;
+    return SP_OK;
+}
+
 sp_status sp_server_add_graph(sp_server sh, sp_graph gh, int32_t* graph_id) {
     if (!sh || !gh || !graph_id) return fail(SP_ERR_INVALID_ARG, "NULL argument");
     Server* s = reinterpret_cast<Server*>(sh);
+    {
+        // the source keys live launches order requests with, made once per graph
+        Graph* g = reinterpret_cast<Graph*>(gh);
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(cudaGetLastError(), "stream");
+        const sp_status rc = graph_host_keys(g, st);
+        cudaStreamDestroy(st);
+        if (rc != SP_OK) return rc;
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     s->graphs.push_back(reinterpret_cast<Graph*>(gh));
     *graph_id = (int32_t)s->graphs.size() - 1;

@@ -42,7 +42,7 @@ def test_status_strings_and_defaults():
     assert sp.sp_status_string(12345) == "SP_ERR_UNKNOWN"
     o = sp.make_opts()
     assert (o.precision, o.form, o.batch, o.debug_flags) == (sp.SP_FP64, sp.SP_FORM_AUTO, 0, 0)
-    assert ctypes.sizeof(sp.sp_bc_opts) == 40 and ctypes.sizeof(sp.sp_bc_stats) == 96
+    assert ctypes.sizeof(sp.sp_bc_opts) == 40 and ctypes.sizeof(sp.sp_bc_stats) == 104
     assert ctypes.sizeof(sp.sp_graph_info) == 48
 
 

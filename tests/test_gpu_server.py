@@ -3,6 +3,8 @@
 Each request's result must equal the oracle within the tolerance and be
 bit-identical whether it ran alone or mixed with other requests.
 """
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -40,8 +42,9 @@ def requests(gs, count, seed):
     return out
 
 
-def serve(Gs, reqs, slots=4, budget=8 << 30):
+def serve(Gs, reqs, slots=4, budget=8 << 30, live=True):
     s = sp.sp_server_create(budget, slots)
+    sp.sp_server_set_live(s, live)
     ids = [sp.sp_server_add_graph(s, G.handle) for G in Gs]
     outs, handles = [], []
     for gi, srcs, prec in reqs:
@@ -71,6 +74,69 @@ def test_mixed_requests_match_oracle_and_run_alone(graphs):
     for i in range(0, len(reqs), 3):
         alone, _, _ = serve(Gs, [reqs[i]])
         assert np.array_equal(alone[0], mixed[i]), i
+
+
+def test_launches_without_live_feeds_give_the_same_results(graphs):
+    # With live launches off, each batched launch runs only the requests it
+    # started with; results are bit-identical to those of live launches.
+    gs, Gs = graphs
+    reqs = requests(gs, 8, 13)
+    live, _, _ = serve(Gs, reqs, slots=1)
+    fixed, _, stats = serve(Gs, reqs, slots=1, live=False)
+    for i, (a, b) in enumerate(zip(live, fixed)):
+        assert np.array_equal(a, b), i
+    assert all(st["joined"] == 0 for st in stats)
+
+
+def test_requests_join_a_running_launch():
+    # A long request on one graph runs as a live launch; requests on the same
+    # graph submitted while it runs enter it between its batches (their words
+    # run after the words already there).  Each matches the oracle and is
+    # bit-identical to the request served alone; traversal counts are the
+    # request's own.
+    g = gen.rmat(17, 16, 7)
+    G = sp.Graph(g.row_ptr, g.col_idx)
+    opts = sp.make_opts(precision=sp.SP_FP64)
+    big_srcs = gen.sources(g, 1024, 11)
+    small = [gen.sources(g, k, 20 + i) for i, k in enumerate([40, 7, 64])]
+    joined_any = False
+    for attempt in range(3):
+        s = sp.sp_server_create(8 << 30, 1)
+        gid = sp.sp_server_add_graph(s, G.handle)
+        big_out = torch.full((g.n,), -1.0, dtype=torch.float64, device=DEV)
+        hb = sp.sp_bc_submit(s, gid, big_srcs, big_out, opts)
+        t_end = time.monotonic() + 30.0
+        while sp.sp_request_times(s, hb)[1] == 0:  # taken by the slot
+            assert time.monotonic() < t_end
+        outs, hs = [], []
+        for srcs in small:
+            out = torch.full((g.n,), -1.0, dtype=torch.float64, device=DEV)
+            hs.append(sp.sp_bc_submit(s, gid, srcs, out, opts))
+            outs.append(out)
+        for h in hs + [hb]:
+            assert sp.sp_bc_wait(s, h) == sp.SP_OK
+        stats = [sp.sp_request_stats(s, h) for h in hs]
+        times = [sp.sp_request_times(s, h) for h in hs + [hb]]
+        sp.sp_server_destroy(s)
+        torch.cuda.synchronize()
+        joined = [st["joined"] == 1 for st in stats]
+        if any(joined):
+            joined_any = True
+            for i in range(len(hs)):
+                if joined[i]:  # entered the launch before its first request was done, finished after it
+                    assert times[i][1] < times[-1][2] <= times[i][2]
+                    assert stats[i]["shared"] > 1
+            break
+    assert joined_any, "no request joined the running launch in three attempts"
+    for srcs, out, st in zip(small, outs, stats):
+        got = out.cpu().numpy()
+        want, ost = oracle.bc(g, srcs)
+        assert close(got, want, RTOL[sp.SP_FP64]), len(srcs)
+        assert st["traversed_arcs"] == int(ost["arcs"].sum())
+        alone, _, _ = serve([G], [(0, srcs, sp.SP_FP64)], slots=1)
+        assert np.array_equal(alone[0], got), len(srcs)
+    alone, _, _ = serve([G], [(0, big_srcs, sp.SP_FP64)], slots=1)
+    assert np.array_equal(alone[0], big_out.cpu().numpy())
 
 
 def test_budget_smaller_than_a_request_still_runs(graphs):
@@ -185,4 +251,26 @@ def test_pagerank_requests_share_the_server_with_bc(graphs):
         sp.sp_pagerank_submit(s, ids[0], bad, 1.5, -1.0, 3)
     with pytest.raises(sp.StarbcError):
         sp.sp_pagerank_submit(s, ids[0], np.empty(Gs[0].n), 0.85, -1.0, 3)
+    sp.sp_server_destroy(s)
+
+
+def test_requests_on_a_weighted_graph_run_the_weighted_form():
+    # A graph with weights is served in the weighted form, request by
+    # request, never in (unweighted) batched launches.
+    g = gen.rmat(15, 8, 3)
+    w = gen.edge_weights(g, 5, 1, 20)
+    G = sp.Graph(g.row_ptr, g.col_idx)
+    sp.sp_graph_set_weights(G.handle, w)
+    s = sp.sp_server_create(8 << 30, 1)
+    gid = sp.sp_server_add_graph(s, G.handle)
+    jobs = []
+    for i, k in enumerate([30, 2]):
+        srcs = gen.sources(g, k, 70 + i)
+        out = torch.full((g.n,), -1.0, dtype=torch.float64, device=DEV)
+        jobs.append((srcs, out, sp.sp_bc_submit(s, gid, srcs, out)))
+    for srcs, out, h in jobs:
+        assert sp.sp_bc_wait(s, h) == sp.SP_OK
+        assert sp.sp_request_stats(s, h)["form"] == sp.SP_FORM_WEIGHTED
+        want, _ = oracle.bc_weighted(g, w, srcs)
+        assert close(out.cpu().numpy(), want, RTOL[sp.SP_FP64]), len(srcs)
     sp.sp_server_destroy(s)
