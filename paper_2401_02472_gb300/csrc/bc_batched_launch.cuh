@@ -8,6 +8,13 @@
 
 #include "bc_batched.cuh"
 
+#ifndef SP_T_HUB
+#define SP_T_HUB 64
+#endif
+#ifndef SP_SEG
+#define SP_SEG 512
+#endif
+
 namespace sp {
 
 template <int W>
@@ -16,7 +23,7 @@ sp_status launch_batched_w(const BatchedLaunch& L, LaunchResult* result) {
     const Graph* g = L.g;
     const int64_t n = g->n;
     cudaStream_t st = L.stream;
-    const int t_hub = 64, seg = 256;
+    const int t_hub = SP_T_HUB, seg = SP_SEG;  // rows above t_hub arcs run in segments of seg arcs
 
     // path-count rows: exact u32 counts, or FP64 with per-level exponents once
     // a count passes 2^32
