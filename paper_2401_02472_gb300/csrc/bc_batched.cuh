@@ -34,7 +34,10 @@
 
 namespace sp {
 
-constexpr int kBatchThreads = 256;
+#ifndef SP_BATCH_THREADS
+#define SP_BATCH_THREADS 256  // threads per block
+#endif
+constexpr int kBatchThreads = SP_BATCH_THREADS;
 
 #ifndef SP_BATCH_MINB
 #define SP_BATCH_MINB 4  // resident blocks per SM the register budget is sized for
