@@ -43,7 +43,13 @@
 namespace sp {
 namespace {
 
-constexpr int kWThreads = 512;
+#ifndef SP_W_THREADS
+#define SP_W_THREADS 1024  // threads per block (one source per block)
+#endif
+constexpr int kWThreads = SP_W_THREADS;
+#ifndef SP_W_PER_SM
+#define SP_W_PER_SM 2  // resident blocks per SM the registers are sized for (32 registers)
+#endif
 constexpr int kWLane = 16;  // rows of at most this many arcs are walked by one lane
 constexpr int kG = 4;       // arcs of a lane's row whose loads are in flight together
 constexpr int kUnreached = INT_MAX;
@@ -106,7 +112,7 @@ __device__ void block_exclusive_scan(int32_t* cnt, int m) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kWThreads, 2) weighted_kernel(WArgs a) {
+__global__ void __launch_bounds__(kWThreads, SP_W_PER_SM) weighted_kernel(WArgs a) {
     __shared__ int s_cnt[2];  // frontier fill (next), reached fill
     __shared__ int s_err;
     __shared__ int s_max;
