@@ -639,7 +639,10 @@ static __device__ __forceinline__ bool plain_skip(const PlainArgs& a) {
 }
 
 template <typename SigT, typename ThT, bool kRec, bool kDir>
-__global__ void __launch_bounds__(kPlainThreads, 2) plain_kernel(PlainArgs a) {
+#ifndef SP_PLAIN_PER_SM
+#define SP_PLAIN_PER_SM 2  // resident blocks per SM the registers are sized for
+#endif
+__global__ void __launch_bounds__(kPlainThreads, SP_PLAIN_PER_SM) plain_kernel(PlainArgs a) {
     if (plain_skip(a)) return;
     constexpr bool kFloatSig = !std::is_integral<SigT>::value;
     const int g = blockIdx.x / a.gblocks;

@@ -153,7 +153,10 @@ __device__ void hub_item(const PrArgs& a, int g, int iter, const double* contrib
     if (lane == 0) settle(a, v, re - rb, t, pr_cur, pr_nxt, contrib_nxt);
 }
 
-__global__ void __launch_bounds__(kPrThreads, 2) pagerank_kernel(PrArgs a) {
+#ifndef SP_PR_PER_SM
+#define SP_PR_PER_SM 2  // resident blocks per SM the registers are sized for
+#endif
+__global__ void __launch_bounds__(kPrThreads, SP_PR_PER_SM) pagerank_kernel(PrArgs a) {
     if (a.pre_err != nullptr && ld_volatile(a.pre_err) != 0) return;
     Ctl* ctl = a.ctl;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
