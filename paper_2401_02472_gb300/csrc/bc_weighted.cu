@@ -11,8 +11,8 @@
 //              round relax their arcs with atomicMin and join the next round
 //              once (a round stamp); a vertex whose new distance is at least T
 //              goes to a far pile instead (once, a flag).  When no near vertex
-//              is left, T moves to the smallest far distance + delta (the
-//              mean arc weight) and the far vertices below it become the
+//              is left, T moves to the smallest far distance + delta (see
+//              set_weights) and the far vertices below it become the
 //              next near frontier.  A vertex is expanded at most once per
 //              distance it takes; the first arrival at a vertex lists it as
 //              reached
@@ -34,6 +34,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <string>
 
@@ -47,6 +48,7 @@ namespace {
 #define SP_W_THREADS 1024  // threads per block (one source per block)
 #endif
 constexpr int kWThreads = SP_W_THREADS;
+
 #ifndef SP_W_PER_SM
 #define SP_W_PER_SM 2  // resident blocks per SM the registers are sized for (32 registers)
 #endif
@@ -541,10 +543,16 @@ sp_status set_weights(Graph* g, const int32_t* weights, bool device_src, cudaStr
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->d_w) cudaFree(g->d_w);
     g->d_w = d_w;
-    // near-far step of the weighted form: the mean arc weight
-    g->w_delta = g->nnz > 0 ? (int32_t)std::max<unsigned long long>(1, (wsum + (unsigned long long)g->nnz / 2) /
-                                                                       (unsigned long long)g->nnz)
-                            : 1;
+    // near-far step of the weighted form: Delta ~ (largest weight) / (average
+    // degree), the delta-stepping rule of Meyer and Sanders (2003), with the
+    // largest weight of a uniform draw taken as twice the mean: 4 x mean
+    // weight x n / nnz (about 7 for weights U[1, 100] at average degree 30)
+    double delta = 1.0;
+    if (g->nnz > 0 && g->n > 0) {
+        const double mean_w = (double)wsum / (double)g->nnz;
+        delta = std::floor(4.0 * mean_w * (double)g->n / (double)g->nnz + 0.5);
+    }
+    g->w_delta = (int32_t)std::min(std::max(delta, 1.0), (double)kMaxWeight);
     return SP_OK;
 }
 

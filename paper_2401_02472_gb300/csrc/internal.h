@@ -70,7 +70,7 @@ struct Graph {
     int64_t knnz() const { return directed ? 2 * nnz : nnz; }
     std::vector<unsigned long long> h_keys;  // source ordering key per vertex (graph_host_keys), or empty
     int32_t* d_w = nullptr;     // arc weights [nnz] (sp_graph_set_weights): BC under these weights
-    int32_t w_delta = 1;        // near-far step of the weighted form: the mean arc weight
+    int32_t w_delta = 1;        // near-far step of the weighted form (sp_graph_set_weights)
     DevFlags* flags_host = nullptr;  // mapped pinned: errors and hints of asynchronous calls
     DevFlags* flags_dev = nullptr;   // the same words, as the device addresses them
     int ecap_mult = 1, hcap_mult = 1;  // batched capacities learnt from asynchronous calls
