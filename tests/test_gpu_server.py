@@ -274,3 +274,26 @@ def test_requests_on_a_weighted_graph_run_the_weighted_form():
         want, _ = oracle.bc_weighted(g, w, srcs)
         assert close(out.cpu().numpy(), want, RTOL[sp.SP_FP64]), len(srcs)
     sp.sp_server_destroy(s)
+
+
+def test_live_launch_that_overflows_its_counts_reruns_its_requests():
+    # Path counts on a 200 x 200 grid pass 2^32, so a live batched launch in
+    # exact u32 counts stops on the overflow; its unfinished requests rerun as
+    # one ordinary launch with FP64 counts, and later requests on the graph
+    # start in FP64.  Every result matches the oracle.
+    g = gen.grid(200, 200)
+    G = sp.Graph(g.row_ptr, g.col_idx)
+    opts = sp.make_opts(precision=sp.SP_FP64, form=sp.SP_FORM_BATCHED)
+    s = sp.sp_server_create(8 << 30, 1)
+    gid = sp.sp_server_add_graph(s, G.handle)
+    jobs = []
+    for srcs in [np.array([0, 199, 200 * 200 - 1], np.int32), np.array([100 * 200 + 100, 5], np.int32)]:
+        out = torch.full((g.n,), -1.0, dtype=torch.float64, device=DEV)
+        jobs.append((srcs, out, sp.sp_bc_submit(s, gid, srcs, out, opts)))
+    for srcs, out, h in jobs:
+        assert sp.sp_bc_wait(s, h) == sp.SP_OK
+        st = sp.sp_request_stats(s, h)
+        assert st["sigma_float"] == 1 and st["form"] == sp.SP_FORM_BATCHED
+        want, _ = oracle.bc(g, srcs)
+        assert close(out.cpu().numpy(), want, RTOL[sp.SP_FP64]), srcs
+    sp.sp_server_destroy(s)
