@@ -919,6 +919,46 @@ bool request_is_batched(Graph* g, int32_t nsrc, const sp_bc_opts& o, cudaStream_
     return g->top_levels <= 64;
 }
 
+// Representation and shape of a request-mode launch on g: path counts exact
+// or FP64 and dependencies FP32 or FP64 as the graph's earlier calls found
+// necessary; the graph's tuned width, else one by the launch's size (a
+// request's result does not depend on it: per-word partial vectors); the
+// bottom-up threshold.  Makes sure the regrouping BFS distances exist.
+struct RequestShape {
+    bool sigma_float = false, theta_f32 = false;
+    int width = 0, bottom_up = 0;
+};
+static sp_status request_shape(Graph* g, const sp_bc_opts& o, int64_t nsrc, cudaStream_t st, RequestShape* out) {
+    absorb_hints(g);
+    out->theta_f32 = o.precision == SP_FP32_DELTA;
+    {
+        const int hints = range_hints(g);
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (hints & 1) g->sigma_float = true;
+        if (hints & 2) g->theta_f64 = true;
+        if (g->theta_f64) out->theta_f32 = false;
+        out->sigma_float = g->sigma_float;
+    }
+    {
+        sp_status rc = ensure_top_bfs(g, st);
+        if (rc == SP_OK) rc = ensure_landmarks(g, st);
+        if (rc != SP_OK) return rc;
+    }
+    int width = 0;
+    out->bottom_up = batched_bottom_up(g, o.bottom_up);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key(g, o.precision));
+        if (it != g_tuned.end()) {
+            width = it->second.width;
+            if (o.bottom_up == 0) out->bottom_up = batched_bottom_up(g, it->second.bottom_up);
+        }
+    }
+    if (width == 0) width = nsrc >= 128 ? 128 : default_batch_width((int32_t)std::max<int64_t>(nsrc, 1));
+    out->width = width;
+    return SP_OK;
+}
+
 sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts& o, cudaStream_t st) {
     const int64_t n = g->n;
     int64_t total = 0;
@@ -932,34 +972,13 @@ sp_status bc_requests(Graph* g, RequestPart* parts, int nparts, const sp_bc_opts
         SP_CUDA(cudaStreamSynchronize(st));
         return SP_OK;
     }
-    absorb_hints(g);
-    bool sigma_float, theta_f32 = o.precision == SP_FP32_DELTA;
+    RequestShape shape;
     {
-        const int hints = range_hints(g);
-        std::lock_guard<std::mutex> lk(g->mu);
-        if (hints & 1) g->sigma_float = true;
-        if (hints & 2) g->theta_f64 = true;
-        if (g->theta_f64) theta_f32 = false;
-        sigma_float = g->sigma_float;
-    }
-    {
-        sp_status rc = ensure_top_bfs(g, st);
-        if (rc == SP_OK) rc = ensure_landmarks(g, st);
+        sp_status rc = request_shape(g, o, total, st, &shape);
         if (rc != SP_OK) return rc;
     }
-    // Width: the one tuned for the graph, else by the launch's size.  A
-    // request's result does not depend on it (per-word partial vectors).
-    int width = 0;
-    int batch_bu = batched_bottom_up(g, o.bottom_up);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tuned.find(tune_key(g, o.precision));
-        if (it != g_tuned.end()) {
-            width = it->second.width;
-            if (o.bottom_up == 0) batch_bu = batched_bottom_up(g, it->second.bottom_up);
-        }
-    }
-    if (width == 0) width = total >= 128 ? 128 : default_batch_width((int32_t)total);
+    bool sigma_float = shape.sigma_float, theta_f32 = shape.theta_f32;
+    const int width = shape.width, batch_bu = shape.bottom_up;
     const int W = width / 32;
 
     // Each request's sources regrouped among themselves (same keys as a
@@ -1178,27 +1197,13 @@ sp_status live_open(Graph* g, const sp_bc_opts& o, int64_t nsrc, LiveFeed* lf, c
         sp_status rc = graph_host_keys(g, st);
         if (rc != SP_OK) return rc;
     }
-    absorb_hints(g);
-    bool theta_f32 = o.precision == SP_FP32_DELTA, sigma_float;
+    RequestShape shape;
     {
-        const int hints = range_hints(g);
-        std::lock_guard<std::mutex> lk(g->mu);
-        if (hints & 1) g->sigma_float = true;
-        if (hints & 2) g->theta_f64 = true;
-        if (g->theta_f64) theta_f32 = false;
-        sigma_float = g->sigma_float;
+        sp_status rc = request_shape(g, o, nsrc, st, &shape);
+        if (rc != SP_OK) return rc;
     }
-    int width = 0;
-    int batch_bu = batched_bottom_up(g, o.bottom_up);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tuned.find(tune_key(g, o.precision));
-        if (it != g_tuned.end()) {
-            width = it->second.width;
-            if (o.bottom_up == 0) batch_bu = batched_bottom_up(g, it->second.bottom_up);
-        }
-    }
-    if (width == 0) width = nsrc >= 128 ? 128 : default_batch_width((int32_t)std::max<int64_t>(nsrc, 1));
+    const int width = shape.width, batch_bu = shape.bottom_up;
+    const bool sigma_float = shape.sigma_float, theta_f32 = shape.theta_f32;
     // word slots: room for the largest request plus a batch, more while the
     // vectors stay within about 1 GiB
     const int64_t min_words = (int64_t)(1024 / 32) + width / 32;
