@@ -81,6 +81,8 @@ struct WArgs {
     int32_t* far1;      // [n]
     int32_t* infar;     // [n] 1 while the vertex is in the far pile
     int32_t* expd;      // [n] distance at which the vertex was last expanded (-1: never)
+    int4* kids;         // [n] up to three shortest-path-DAG children in CSR order (x, y, z)
+                        // and their count (w; -1: more than three), found by the sigma pass
     int32_t delta;      // near-far step
 };
 
@@ -138,6 +140,7 @@ __global__ void __launch_bounds__(kWThreads, SP_W_PER_SM) weighted_kernel(WArgs 
     int32_t* fnxt = a.far1 + off;
     int32_t* infar = a.infar + off;
     int32_t* expd = a.expd + off;
+    int4* kids = a.kids + off;
     unsigned long long st_arcs = 0, st_reached = 0, st_scanned = 0;
     int levels_max = 0;
     if (tid == 0) s_err = 0;
@@ -336,6 +339,10 @@ __global__ void __launch_bounds__(kWThreads, SP_W_PER_SM) weighted_kernel(WArgs 
                         st_scanned += (unsigned long long)deg;
                     }
                     double acc = 0.0;
+                    // the row's arcs into the next distances are v's DAG children:
+                    // the first three (CSR order) and their count are kept for
+                    // the dependency pass
+                    int kid[3] = {0, 0, 0}, nkid = 0;
                     if (deg <= kWLane)
                         for (int k0 = 0; k0 < deg; k0 += kG) {  // kG arcs in flight, summed in CSR order
                             int u[kG], wt[kG], du[kG];
@@ -352,21 +359,43 @@ __global__ void __launch_bounds__(kWThreads, SP_W_PER_SM) weighted_kernel(WArgs 
                             for (int q = 0; q < kG; ++q)
                                 c[q] = du[q] != kUnreached && du[q] + wt[q] == dv ? sig[u[q]] : 0.0;
 #pragma unroll
-                            for (int q = 0; q < kG; ++q)
+                            for (int q = 0; q < kG; ++q) {
                                 if (k0 + q < deg && du[q] != kUnreached && du[q] + wt[q] == dv) acc += c[q];
+                                if (u[q] >= 0 && du[q] != kUnreached && du[q] == dv + wt[q]) {
+                                    if (nkid < 3) kid[nkid] = u[q];
+                                    ++nkid;
+                                }
+                            }
                         }
+                    if (i < e && deg <= kWLane) kids[v] = make_int4(kid[0], kid[1], kid[2], nkid > 3 ? -1 : nkid);
                     unsigned wide = __ballot_sync(kFull, i < e && deg > kWLane);
                     while (wide) {
                         const int j = __ffs(wide) - 1;
                         wide &= wide - 1;
                         const int bj = __shfl_sync(kFull, beg, j), dj = __shfl_sync(kFull, deg, j);
                         const int dvj = __shfl_sync(kFull, dv, j);
+                        const int vj = __shfl_sync(kFull, v, j);
+                        int* kj = reinterpret_cast<int*>(&kids[vj]);
+                        int nk = 0;  // children so far (the same in every lane)
                         double p = 0.0;
-                        for (int k = lane; k < dj; k += kWarp) {
-                            const int u = __ldg(&a.ci[bj + k]);
-                            const int du = dist[u];
-                            if (du != kUnreached && du + __ldg(&a.w[bj + k]) == dvj) p += sig[u];
+                        for (int k0 = 0; k0 < dj; k0 += kWarp) {
+                            const int k = k0 + lane;
+                            bool child = false;
+                            if (k < dj) {
+                                const int u = __ldg(&a.ci[bj + k]);
+                                const int du = dist[u];
+                                const int wk = __ldg(&a.w[bj + k]);
+                                if (du != kUnreached && du + wk == dvj) p += sig[u];
+                                child = du != kUnreached && du == dvj + wk;
+                            }
+                            const unsigned cb = __ballot_sync(kFull, child);
+                            if (child) {
+                                const int rank = nk + __popc(cb & ((1u << lane) - 1u));
+                                if (rank < 3) kj[rank] = __ldg(&a.ci[bj + k]);
+                            }
+                            nk += __popc(cb);
                         }
+                        if (lane == 0) kj[3] = nk > 3 ? -1 : nk;
                         p = warp_sum_f64(p);
                         if (lane == j) acc = p;
                     }
@@ -385,14 +414,28 @@ __global__ void __launch_bounds__(kWThreads, SP_W_PER_SM) weighted_kernel(WArgs 
                 for (int i0 = b + warp * 32; i0 < e; i0 += nwarps * 32) {
                     const int i = i0 + lane;
                     int v = 0, beg = 0, deg = 0, dv = 0;
+                    int4 kd = make_int4(0, 0, 0, 0);
                     if (i < e) {
                         v = order[i];
+                        kd = kids[v];
                         beg = __ldg(&a.rp[v]);
                         deg = __ldg(&a.rp[v + 1]) - beg;
                         dv = dist[v];
-                        st_scanned += (unsigned long long)deg;
                     }
+                    // at most three children: their slots, summed in CSR order;
+                    // else the row is scanned again
+                    const bool slots = kd.w >= 0;
+                    if (slots) deg = 0;
+                    if (i < e && !slots) st_scanned += (unsigned long long)deg;
                     double acc = 0.0;
+                    if (i < e && slots && kd.w > 0) {
+                        const double t0 = th[kd.x];
+                        const double t1 = kd.w > 1 ? th[kd.y] : 0.0;
+                        const double t2 = kd.w > 2 ? th[kd.z] : 0.0;
+                        acc += t0;
+                        if (kd.w > 1) acc += t1;
+                        if (kd.w > 2) acc += t2;
+                    }
                     if (deg <= kWLane)
                         for (int k0 = 0; k0 < deg; k0 += kG) {  // kG arcs in flight, summed in CSR order
                             int x[kG], wt[kG], dx[kG];
@@ -563,12 +606,12 @@ sp_status run_weighted(const WeightedLaunch& L, LaunchResult* result) {
     int per_sm = 0;
     SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)&weighted_kernel, kWThreads, 0));
     if (per_sm < 1) return fail(SP_ERR_CUDA, "weighted kernel cannot be resident");
-    // one block per source at a time; per-block state of 64 bytes a vertex,
+    // one block per source at a time; per-block state of 80 bytes a vertex,
     // so the grid is also capped by a state budget (32 GiB)
     int grid = per_sm * device_sm_count(g->device);
     if (L.max_ctas > 0 && L.max_ctas < grid) grid = L.max_ctas;
     const int64_t hcap = L.dist_cap;
-    const double per_block = 64.0 * (double)n + 8.0 * (double)(hcap + 2);
+    const double per_block = 80.0 * (double)n + 8.0 * (double)(hcap + 2);
     grid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)grid, (int64_t)L.nsrc,
                                                          (int64_t)((32.0 * (1ull << 30)) / per_block)}));
     size_t bytes = 0;
@@ -581,7 +624,7 @@ sp_status run_weighted(const WeightedLaunch& L, LaunchResult* result) {
     const size_t o_hist = take(4 * (size_t)(hcap + 1) * G);
     const size_t o_sig = take(8 * N * G), o_th = take(8 * N * G), o_part = take(8 * N * G);
     const size_t o_far0 = take(4 * N * G), o_far1 = take(4 * N * G), o_infar = take(4 * N * G),
-                 o_expd = take(4 * N * G);
+                 o_expd = take(4 * N * G), o_kids = take(16 * N * G);
     char* ws = nullptr;
     if (workspace_alloc((void**)&ws, bytes, st) != cudaSuccess) {
         cudaGetLastError();
@@ -617,6 +660,7 @@ sp_status run_weighted(const WeightedLaunch& L, LaunchResult* result) {
     a.far1 = reinterpret_cast<int32_t*>(ws + o_far1);
     a.infar = reinterpret_cast<int32_t*>(ws + o_infar);
     a.expd = reinterpret_cast<int32_t*>(ws + o_expd);
+    a.kids = reinterpret_cast<int4*>(ws + o_kids);
     a.delta = std::max(1, g->w_delta);
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
