@@ -196,10 +196,13 @@ __global__ void __launch_bounds__(kWThreads, SP_W_PER_SM) weighted_kernel(WArgs 
                             fcur[atomicAdd(&s_far, 1)] = x;
                         }
                     };
+                    // distances only fall, so a read that is not below the
+                    // candidate proves the atomicMin would change nothing
                     auto relax = [&](int e, int d0) {
                         const int x = __ldg(&a.ci[e]);
                         const int nd = d0 + __ldg(&a.w[e]);
                         if (nd >= a.hcap) { atomicCAS(&s_err, 0, kErrCapLevels); return; }
+                        if (__ldcg(&dist[x]) <= nd) return;
                         const int old = atomicMin(&dist[x], nd);
                         if (nd < old) improved(x, nd, old);
                     };
@@ -215,6 +218,9 @@ __global__ void __launch_bounds__(kWThreads, SP_W_PER_SM) weighted_kernel(WArgs 
                                 x[q] = ok ? __ldg(&a.ci[beg + k0 + q]) : -1;
                                 nd[q] = ok ? du + __ldg(&a.w[beg + k0 + q]) : 0;
                             }
+                            int dc[kG];
+#pragma unroll
+                            for (int q = 0; q < kG; ++q) dc[q] = x[q] >= 0 ? __ldcg(&dist[x[q]]) : 0;
 #pragma unroll
                             for (int q = 0; q < kG; ++q) {
                                 old[q] = kUnreached;
@@ -222,8 +228,10 @@ __global__ void __launch_bounds__(kWThreads, SP_W_PER_SM) weighted_kernel(WArgs 
                                     if (nd[q] >= a.hcap) {
                                         atomicCAS(&s_err, 0, kErrCapLevels);
                                         x[q] = -1;
-                                    } else {
+                                    } else if (nd[q] < dc[q]) {
                                         old[q] = atomicMin(&dist[x[q]], nd[q]);
+                                    } else {
+                                        x[q] = -1;  // no improvement possible
                                     }
                                 }
                             }
