@@ -48,6 +48,9 @@ namespace {
 #define SP_W_THREADS 1024  // threads per block (one source per block)
 #endif
 constexpr int kWThreads = SP_W_THREADS;
+#ifndef SP_W_DELTA_K
+#define SP_W_DELTA_K 4.0  // near-far step = K x mean weight x n / nnz (sp_graph_set_weights)
+#endif
 
 #ifndef SP_W_PER_SM
 #define SP_W_PER_SM 2  // resident blocks per SM the registers are sized for (32 registers)
@@ -601,7 +604,7 @@ sp_status set_weights(Graph* g, const int32_t* weights, bool device_src, cudaStr
     double delta = 1.0;
     if (g->nnz > 0 && g->n > 0) {
         const double mean_w = (double)wsum / (double)g->nnz;
-        delta = std::floor(4.0 * mean_w * (double)g->n / (double)g->nnz + 0.5);
+        delta = std::floor(SP_W_DELTA_K * mean_w * (double)g->n / (double)g->nnz + 0.5);
     }
     g->w_delta = (int32_t)std::min(std::max(delta, 1.0), (double)kMaxWeight);
     return SP_OK;
